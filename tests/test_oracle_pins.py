@@ -1,0 +1,334 @@
+"""Pins of the RPIM oracle against facts fixed by the mathematics.
+
+Each test checks the oracle (``oracle/oracle.c``) against something other than
+itself: closed forms (quadrature of cubics, Timoshenko's cantilever deflection,
+the weight carried by a column), identities that exact RPIM shape functions
+satisfy (partition of unity, linear reproduction, the Kronecker property,
+reproduction of any constrained RBF combination), special cases that reduce to
+textbook formulas (barycentric interpolation from four nodes), brute force,
+and an extended-precision rerun. A plausible slip anywhere in the oracle (a
+dropped term, a wrong sign, index or factor, a transposed operand) breaks at
+least one of them; ``test_oracle_mutations.py`` plants such slips to show it.
+"""
+import mpmath as mp
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+KINDS = ["f64", "ld"]
+
+
+@pytest.fixture(scope="module")
+def cube_j():
+    return gen.cube_config(jitter=0.2, seed=7)
+
+
+def _points(p):
+    return oracle.gauss_points(p.cell_lo, p.cell_hi)
+
+
+# ---------------------------------------------------------------- quadrature
+def test_gauss_rule_integrates_cubics_exactly(cube_j):
+    """2x2x2 Gauss-Legendre on the node cells integrates any polynomial of
+    degree <= 3 per axis exactly over the domain (cells tile the box)."""
+    pts, wj = _points(cube_j)
+    x, y, z = pts.T
+    f = x**3 + 2 * x**2 * y - y * z**3 + x * y * z + 5.0
+    exact = 1 / 4 + 2 * (1 / 3) * (1 / 2) - (1 / 2) * (1 / 4) + 1 / 8 + 5.0
+    assert abs(np.dot(wj, f) - exact) < 1e-14
+    assert abs(wj.sum() - 1.0) < 1e-15
+
+
+def test_gauss_points_of_rectangular_cells():
+    p = gen.cantilever_config(shape=(9, 3, 3), length=2.0, jitter=0.0)
+    pts, wj = _points(p)
+    assert abs(wj.sum() - 2.0) < 1e-14
+    # every point lies inside its own cell
+    c = np.repeat(np.arange(p.n_nodes), 8)
+    assert np.all(pts >= p.cell_lo[c]) and np.all(pts <= p.cell_hi[c])
+
+
+# ---------------------------------------------------------------- support
+def test_support_matches_brute_force(cube_j):
+    p = cube_j
+    pts, _ = _points(p)
+    rs2 = oracle.support_radius2(p.alpha_s, p.h)
+    assert rs2 == pytest.approx((2.5 * 0.2) ** 2, rel=1e-15)
+    for g in range(0, len(pts), 37):
+        s = oracle.support(p.xyz, pts[g], rs2)
+        d2 = ((p.xyz - pts[g]) ** 2).sum(1)
+        sure_in = set(np.nonzero(d2 < rs2 * (1 - 1e-12))[0])
+        maybe = set(np.nonzero(d2 <= rs2 * (1 + 1e-12))[0])
+        assert sure_in <= set(s) <= maybe
+        assert np.all(np.diff(s) > 0)
+
+
+# ---------------------------------------------------------------- shape functions
+def _some_points(p, stride=61):
+    pts, _ = _points(p)
+    return pts[::stride]
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_partition_of_unity_and_linear_reproduction(cube_j, kind):
+    p = cube_j
+    rs2 = oracle.support_radius2(p.alpha_s, p.h)
+    for x in _some_points(p):
+        s = oracle.support(p.xyz, x, rs2)
+        ph = oracle.shape(p.xyz, s, x, p.h, kind=kind)
+        X = p.xyz[s]
+        assert abs(ph[0].sum() - 1.0) < 1e-10
+        assert np.abs(ph[0] @ X - x).max() < 1e-10
+        for k in range(3):
+            assert abs(ph[1 + k].sum()) < 1e-10 / p.h
+            assert np.abs(ph[1 + k] @ X - np.eye(3)[k]).max() < 1e-10
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_kronecker_delta_at_nodes(cube_j, kind):
+    p = cube_j
+    rs2 = oracle.support_radius2(p.alpha_s, p.h)
+    for j in np.linspace(0, p.n_nodes - 1, 7).astype(int):
+        x = p.xyz[j]
+        s = oracle.support(p.xyz, x, rs2)
+        ph = oracle.shape(p.xyz, s, x, p.h, kind=kind)
+        e = (s == j).astype(float)
+        assert np.abs(ph[0] - e).max() < (1e-10 if kind == "f64" else 1e-13)
+
+
+def _mq(r2, c2, q):
+    return (r2 + c2) ** q
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_reproduces_constrained_rbf_combinations(cube_j, kind):
+    """Any f(y) = sum_j c_j R(|y - x_j|/h) with sum_j c_j p(x_j) = 0 lies in
+    the RPIM interpolation space, so sum_i phi_i(x) f(x_i) = f(x) and the same
+    for the gradient. f and grad f are evaluated independently in 40-digit
+    arithmetic (gradient by numerical differentiation)."""
+    p = cube_j
+    mp.mp.dps = 40
+    rs2 = oracle.support_radius2(p.alpha_s, p.h)
+    rng = np.random.default_rng(3)
+    tol = 2e-7 if kind == "f64" else 1e-10
+    for x in _some_points(p, 211):
+        s = oracle.support(p.xyz, x, rs2)
+        X = p.xyz[s]
+        P = np.concatenate([np.ones((len(s), 1)), X], 1)
+        c = rng.standard_normal(len(s))
+        c -= P @ np.linalg.lstsq(P, c, rcond=None)[0]
+        cm = [mp.mpf(float(v)) for v in c]
+        Xm = [[mp.mpf(float(v)) for v in row] for row in X]
+        hm, c2, qm = mp.mpf(p.h), mp.mpf(p.alpha_c) ** 2, mp.mpf(p.q)
+
+        def f(y):
+            return sum(cj * _mq(sum((y[k] - xj[k]) ** 2 for k in range(3)) / hm**2, c2, qm)
+                       for cj, xj in zip(cm, Xm))
+
+        fx = [float(f(row)) for row in Xm]
+        xm = [mp.mpf(float(v)) for v in x]
+        ph = oracle.shape(p.xyz, s, x, p.h, kind=kind)
+        scale = sum(abs(v) for v in fx) / len(fx)
+        assert abs(ph[0] @ fx - float(f(xm))) < tol * scale * 10
+        for k in range(3):
+            g = mp.diff(lambda t: f([xm[a] + (t if a == k else 0) for a in range(3)]), 0)
+            assert abs(ph[1 + k] @ fx - float(g)) < tol * scale * 10 / p.h
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_gradients_match_central_differences(cube_j, kind):
+    p = cube_j
+    rs2 = oracle.support_radius2(p.alpha_s, p.h)
+    d = 1e-5 * p.h
+    for x in _some_points(p, 173):
+        s = oracle.support(p.xyz, x, rs2)
+        ph = oracle.shape(p.xyz, s, x, p.h, kind=kind)
+        for k in range(3):
+            e = np.eye(3)[k] * d
+            fd = (oracle.shape(p.xyz, s, x + e, p.h, kind=kind)[0] -
+                  oracle.shape(p.xyz, s, x - e, p.h, kind=kind)[0]) / (2 * d)
+            tol = 1e-3 if kind == "f64" else 1e-6
+            assert np.abs(fd - ph[1 + k]).max() < tol / p.h
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_four_nodes_reduce_to_barycentric_interpolation(kind):
+    """With n = m = 4 the polynomial constraints fix phi completely: the shape
+    functions are the barycentric coordinates of x in the tetrahedron and the
+    gradients are constant, whatever the radial basis."""
+    xyz = np.array([[0.0, 0.0, 0.0], [1.0, 0.1, 0.0], [0.2, 0.9, 0.1], [0.1, 0.2, 1.1]])
+    x = np.array([0.3, 0.25, 0.2])
+    s = np.arange(4, dtype=np.int32)
+    ph = oracle.shape(xyz, s, x, 0.5, kind=kind)
+    A = np.vstack([np.ones(4), xyz.T])
+    lam = np.linalg.solve(A, np.concatenate([[1.0], x]))
+    grads = np.linalg.inv(A)[:, 1:]
+    assert np.abs(ph[0] - lam).max() < 1e-12
+    assert np.abs(ph[1:].T - grads).max() < 1e-11
+
+
+def test_fp64_floor_against_extended_precision(cube_j):
+    """The plain FP64 solve of the MQ moment matrix (alpha_c = 4, q = 1.03)
+    loses about log10(cond G) ~ 9-10 digits: it agrees with the
+    extended-precision oracle only to a few 1e-9 (h units)."""
+    p = cube_j
+    rs2 = oracle.support_radius2(p.alpha_s, p.h)
+    worst = 0.0
+    for x in _some_points(p, 97):
+        s = oracle.support(p.xyz, x, rs2)
+        a = oracle.shape(p.xyz, s, x, p.h, kind="f64")
+        b = oracle.shape(p.xyz, s, x, p.h, kind="ld")
+        worst = max(worst, np.abs(a - b).max() * p.h)
+    assert worst < 5e-8
+
+
+# ---------------------------------------------------------------- stiffness
+@pytest.fixture(scope="module", params=KINDS)
+def cube_model(request, cube_j):
+    return oracle.assemble_problem(cube_j, request.param)
+
+
+def _strain_fields(xyz):
+    """Six displacement fields with unit engineering strain in Voigt order."""
+    out = []
+    for k in range(6):
+        A = np.zeros((3, 3))
+        if k < 3:
+            A[k, k] = 1.0
+        else:
+            a, b = [(1, 2), (0, 2), (0, 1)][k - 3]
+            A[a, b] = A[b, a] = 0.5
+        out.append(((xyz @ A.T).ravel(), A))
+    return out
+
+
+def test_K_symmetric(cube_model):
+    K = cube_model.dense()
+    assert np.abs(K - K.T).max() <= 1e-14 * np.abs(K).max()
+
+
+def test_K_rigid_body_modes(cube_model, cube_j):
+    K = cube_model.dense()
+    X = cube_j.xyz
+    modes = [np.tile(np.eye(3)[k], len(X)) for k in range(3)]
+    for k in range(3):
+        w = np.eye(3)[k]
+        modes.append(np.cross(w, X).ravel())
+    kf = np.linalg.norm(K)
+    for u in modes:
+        assert np.linalg.norm(K @ u) / (kf * np.linalg.norm(u)) < 1e-10
+
+
+def test_K_energy_of_linear_fields(cube_model, cube_j):
+    """For u = A x, B u is the constant strain of A at every point, so
+    u_a^T K u_b = V (lambda tr e_a tr e_b + 2 mu e_a : e_b): pins D, B and the
+    quadrature weights through Hooke's law in tensor form."""
+    K = cube_model.dense()
+    E, nu = 1.0e4, 0.3
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    fields = _strain_fields(cube_j.xyz)
+    V = cube_j.volume
+    for ua, Aa in fields:
+        for ub, Ab in fields:
+            want = V * (lam * np.trace(Aa) * np.trace(Ab) + 2 * mu * np.sum(Aa * Ab))
+            assert abs(ua @ K @ ub - want) < 1e-9 * (lam + 2 * mu) * V
+
+
+def test_K_positive_diagonal(cube_model):
+    K = cube_model.dense()
+    assert np.all(np.diag(K) > 0)
+
+
+def test_K_ld_matches_f64_to_fp64_floor(cube_j):
+    a = oracle.assemble_problem(cube_j, "f64")
+    b = oracle.assemble_problem(cube_j, "ld")
+    assert np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.cols, b.cols)
+    assert np.abs(a.vals - b.vals).max() / np.abs(b.vals).max() < 2e-8
+
+
+def test_body_force_moments():
+    """f_I = sum_g phi_I b w: sum_I f_I = b V (partition of unity) and
+    sum_I f_I x_I = b (first moment of the domain)."""
+    p = gen.gravity_column(shape=(4, 4, 6), height=1.0, width=0.6, gamma=3.0)
+    m = oracle.assemble_problem(p)
+    F = m.f.reshape(-1, 3)
+    V = p.volume
+    assert np.abs(F.sum(0) - p.body * V).max() < 1e-12 * 3.0 * V
+    mom = F[:, 2] @ p.xyz
+    centroid = np.array([0.3, 0.3, 0.5])
+    assert np.abs(mom - (-3.0) * V * centroid).max() < 1e-10
+
+
+def test_point_loads_force_and_moment(cube_j):
+    p = cube_j
+    f = np.zeros(3 * p.n_nodes)
+    oracle.point_loads(p.xyz, p.load_xyz, p.load_force, p.alpha_s, p.alpha_c, p.q, p.h, f)
+    F = f.reshape(-1, 3)
+    assert np.abs(F.sum(0) - p.load_force.sum(0)).max() < 1e-10
+    M = np.cross(p.xyz, F).sum(0)
+    Mp = np.cross(p.load_xyz, p.load_force).sum(0)
+    assert np.abs(M - Mp).max() < 1e-10
+
+
+# ---------------------------------------------------------------- penalty and solve
+def test_penalty_adds_alpha_on_listed_dofs(cube_j):
+    m = oracle.assemble_problem(cube_j)
+    vals = m.vals.ravel().copy()
+    f = m.f.copy()
+    dofs = np.array([2, 5, 300], np.int64)
+    vv = np.array([0.0, 0.5, -1.0])
+    diag0 = np.diag(m.dense()).copy()
+    a = oracle.penalty(cube_j.n_nodes, m.rowptr, m.cols, vals, f, dofs, vv, 1e8)
+    assert a == 1e8 * diag0.max()
+    m2 = oracle.Model(m.n_nodes, m.rowptr, m.cols, vals.reshape(-1, 9), f, None, None)
+    d = np.diag(m2.dense()) - diag0
+    want = np.zeros_like(d)
+    want[dofs] = a
+    assert np.array_equal(d, want)
+    assert np.array_equal(f - m.f, np.where(np.isin(np.arange(len(f)), dofs), 0, 0) +
+                          np.bincount(dofs, a * vv, len(f)))
+
+
+def test_pcg_matches_dense_solve(cube_j):
+    m = oracle.assemble_problem(cube_j)
+    vals = m.vals.ravel().copy()
+    f = m.f.copy()
+    oracle.penalty(cube_j.n_nodes, m.rowptr, m.cols, vals, f, cube_j.fixed_dofs,
+                   cube_j.fixed_vals, 1e8)
+    u, it, rr, st = oracle.pcg(cube_j.n_nodes, m.rowptr, m.cols, vals, f, rtol=1e-13)
+    assert st == 0 and rr <= 1e-13
+    K = oracle.Model(m.n_nodes, m.rowptr, m.cols, vals.reshape(-1, 9), f, None, None).dense()
+    ud = np.linalg.solve(K, f)
+    assert np.linalg.norm(u - ud) / np.linalg.norm(ud) < 1e-8
+
+
+def test_cantilever_tip_deflection_timoshenko():
+    """Tip deflection of the end-loaded cantilever against Timoshenko's
+    closed form PL^3/(3EI) + (4 + 5 nu) P D^2 L / (24 E I) = 0.2070 for
+    L = 8, D = 1, E = 1e4, nu = 0.3, P = 1 (coarse 33x5x5 cloud)."""
+    oracle.set_threads(4)
+    p = gen.cantilever_config(shape=(33, 5, 5))
+    m, u, it, rr, a = oracle.solve_problem(p)
+    I = 1.0 / 12.0
+    ref = 1.0 * 8**3 / (3 * 1e4 * I) + (4 + 5 * 0.3) * 1.0 * 1.0 * 8 / (24 * 1e4 * I)
+    tip = np.nonzero(np.all(np.abs(p.nominal - [8.0, 0.5, 0.5]) < 1e-9, axis=1))[0][0]
+    assert abs(-u[3 * tip + 2] - ref) / ref < 0.02
+
+
+def test_gravity_column_reaction_and_stress():
+    """Column under self weight, base fixed, sides on rollers: the penalty
+    reactions at the base carry exactly the weight gamma V, and the
+    volume-average vertical stress is -gamma H / 2 (uniaxial strain)."""
+    oracle.set_threads(4)
+    gam, H = 20.0, 2.0
+    p = gen.gravity_column(shape=(5, 5, 9), height=H, width=1.0, gamma=gam)
+    m, u, it, rr, a = oracle.solve_problem(p, rtol=1e-12)
+    base = p.fixed_dofs[(p.fixed_dofs % 3 == 2)]
+    reaction = -a * u[base].sum()
+    assert abs(reaction - gam * p.volume) < 1e-6 * gam * p.volume
+    sig = oracle.stress(p.xyz, u, m.pts, p.E, p.nu, p.alpha_s, p.alpha_c, p.q, p.h)
+    avg = np.dot(m.wj, sig[:, 2]) / m.wj.sum()
+    assert abs(avg - (-gam * H / 2)) < 0.03 * gam * H / 2
