@@ -1,0 +1,405 @@
+"""Benchmark of the RPIM global stiffness assembly on GB300.
+
+Workload: the 129 x 17 x 17 cantilever (37,281 field nodes, 298,248 Gauss
+points, support radius 2.5h, multiquadric alpha_c = 4, q = 1.03), FP64,
+seeded synthetic node cloud. One step is the whole assembly path of Sec. 2's
+first stage on device-resident inputs: rpim_build_pattern (Gauss points,
+cell list, supports, node incidence, BSR pattern) + rpim_assemble (shape
+functions, B^T D B, deterministic reduction) + rpim_add_point_loads. The
+penalty stage and the PCG solve are timed once after the timed steps and
+reported under "solve" (full solves/s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank assembles its own replica (weak scaling, no data
+exchange; timing is max over ranks). Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+import gen
+
+METRIC = "RPIM assembly Gauss-pts/s, % of FP64/HBM roofline; batched vs per-instance"
+UNIT = "Gauss-pts/s"
+WORKLOAD = ("cantilever 129x17x17 (37,281 nodes, 298,248 Gauss points), interior jitter 0.2h, "
+            "alpha_s 2.5, MQ alpha_c 4.0 q 1.03, E 1e4 nu 0.3, FP64")
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------------------- flop model
+def shape_flops(n):
+    """Algorithmic flops of one point's shape functions (moment matrix with one
+    kernel evaluation per pair counted as one flop, LU of the (n+4) system,
+    four solves, right-hand sides)."""
+    n = np.asarray(n, dtype=np.float64)
+    N = n + 4
+    return 2 * N**3 / 3 + 8 * N**2 + 5 * n * (n - 1) + 16 * n
+
+
+def pair_flops(n):
+    """Algorithmic flops of one point's B^T D B contributions (45 per pair of
+    the upper triangle, diagonal included)."""
+    n = np.asarray(n, dtype=np.float64)
+    return 22.5 * n * (n + 1)
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "power_w_max": max(pw), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- traffic record
+def _traffic_for(kernel, source):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel's source is unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(source, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+        if kv.get("kernel") == kernel and kv.get("source_sha256") == sha:
+            try:
+                return float(kv["dram_bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+# --------------------------------------------------------------------------- CPU baseline
+def cpu_baseline(p, budget_s=15.0):
+    """The oracle (FP64, OpenMP over points on all host cores) on the first M
+    Gauss points of the workload, M sized to about `budget_s` seconds."""
+    import oracle
+    oracle.build()
+    cores = _cores()
+    oracle.set_threads(cores)
+    pts, wj = oracle.gauss_points(p.cell_lo, p.cell_hi)
+
+    def run(m):
+        t0 = time.perf_counter()
+        oracle.assemble(p.xyz, pts[:m], wj[:m], p.E[:m], p.nu[:m], p.alpha_s, p.alpha_c, p.q, p.h)
+        return time.perf_counter() - t0
+
+    m0 = 1024
+    t0 = run(m0)
+    m = int(min(len(pts), max(m0, m0 * budget_s / max(t0, 1e-3))))
+    dt = run(m)
+    return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of %d Gauss points of the workload (%.1f%%), f64 oracle, OpenMP %d threads, %.1f s"
+                      % (m, len(pts), 100.0 * m / len(pts), cores, dt)}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    p = gen.cantilever_config()
+    import oracle
+    oracle.build()
+    cores = _cores()
+    oracle.set_threads(cores)
+    pts, wj = oracle.gauss_points(p.cell_lo, p.cell_hi)
+
+    def step(m):
+        t0 = time.perf_counter()
+        oracle.assemble(p.xyz, pts[:m], wj[:m], p.E[:m], p.nu[:m], p.alpha_s, p.alpha_c, p.q, p.h)
+        return time.perf_counter() - t0
+
+    # size each step to about 4 s of host work
+    t = step(1024)
+    m = int(min(len(pts), max(1024, 1024 * 4.0 / max(t, 1e-3))))
+    for _ in range(args.warmup):
+        step(m)
+    times = [step(m) for _ in range(args.steps)]
+    ms = 1e3 * sum(times) / len(times)
+    value = m / (ms / 1e3)
+    sample = "first %d of %d Gauss points of the workload per step, f64 oracle, OpenMP %d threads" % (m, len(pts), cores)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample_points": m},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# --------------------------------------------------------------------------- stages 2 and 3
+def _solve(pat, p, E, nu, lxyz, lf, tt, stream):
+    """Penalty (alpha = 1e8 max diag K) and Jacobi-PCG to 1e-10, timed once
+    with CUDA events; the assembly that feeds it is not timed."""
+    import torch
+    K, f = pat.assemble(E, nu)
+    pat.add_point_loads(lxyz, lf, f)
+    dofs, vals = tt(p.fixed_dofs, torch.int64), tt(p.fixed_vals)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    alpha = pat.apply_penalty(K, f, dofs, vals)
+    u, iters, relres = pat.solve_pcg(K, f, rtol=1e-10, max_iter=200000)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    solve_ms = s0.elapsed_time(s1)
+    tip = int(np.nonzero(np.all(np.abs(p.nominal - [8.0, 0.5, 0.5]) < 1e-9, axis=1))[0][0])
+    nnzb = pat.nnz_blocks
+    out = {"pcg_iterations": iters, "relres": relres, "ms": solve_ms, "solves_per_s": 1e3 / solve_ms,
+           "ms_per_iteration": solve_ms / max(iters, 1), "penalty_alpha": alpha,
+           "tip_deflection": -u[3 * tip + 2].item(), "timoshenko": 0.20700,
+           "spmv_algorithmic_bytes": nnzb * (72 + 4) + 8 * (p.n_nodes + 1), "spmv_flops": 18 * nnzb}
+    del K, f, u
+    pat.free()
+    return out
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1802_04256_gb300 as R
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    R.lib()
+    p = gen.cantilever_config()
+    tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    xyz, lo, hi, E, nu = tt(p.xyz), tt(p.cell_lo), tt(p.cell_hi), tt(p.E), tt(p.nu)
+    lxyz, lf = tt(p.load_xyz), tt(p.load_force)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        pat = R.Pattern(xyz, lo, hi, p.alpha_s, p.alpha_c, p.q, p.h)
+        K, f = pat.assemble(E, nu)
+        pat.add_point_loads(lxyz, lf, f)
+        pat.free()
+        return K, f
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    peak_gflops = R.rpim_probe_dfma(5)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    idx = vis.split(",")[local_rank] if vis else str(local_rank)
+    clocks = ClockSampler(idx)
+    clocks.start()
+    R.rpim_profile_read(reset=True)
+    R.rpim_profile_enable(True)
+    launches0 = R.rpim_kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = R.rpim_kernel_launches() - launches0
+    R.rpim_profile_enable(False)
+    prof = R.rpim_profile_read(reset=True)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        tms = torch.tensor([ms], device=dev)
+        dist.all_reduce(tms, op=dist.ReduceOp.MAX)
+        ms = float(tms.item())
+    value = world * p.n_points / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (largest device time)
+    pat = R.Pattern(xyz, lo, hi, p.alpha_s, p.alpha_c, p.q, p.h)
+    _, _, soff, _ = pat.points()
+    nsup = np.diff(soff.cpu().numpy())
+    kinds = {"shape": (shape_flops(nsup).sum(), "shape.cu"), "row": (pair_flops(nsup).sum(), "assemble.cu")}
+    top = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    roof = None
+    if top in kinds:
+        flops, src = kinds[top]
+        nl, tot = prof[top]
+        avg_ms = tot / nl
+        ach = flops / (avg_ms / 1e3) / 1e12
+        peak = peak_gflops / 1e3
+        roof = {"bound": "alu", "kernel": top, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": _traffic_for(top, os.path.join(ROOT, "paper_1802_04256_gb300", "csrc", src)),
+                "peak_source": "FP64 DFMA throughput measured in this run (rpim_probe_dfma)",
+                "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_ms}
+    kernel_ms = {k: round(v[1] / v[0], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    kernel_share = {k: round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4)
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- stage 2 + 3 once: penalty and PCG (full solve)
+    solve = None
+    nnzb = pat.nnz_blocks
+    if args.no_solve:
+        pat.free()
+    else:
+        solve = _solve(pat, p, E, nu, lxyz, lf, tt, stream)
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+                dict(xyz=p.xyz, lo=p.cell_lo, hi=p.cell_hi, E=p.E, nu=p.nu, lx=p.load_xyz, lf=p.load_force).items()}
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        Kh = None
+
+        def e2e_step():
+            nonlocal Kh
+            d = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+            pat = R.Pattern(d["xyz"], d["lo"], d["hi"], p.alpha_s, p.alpha_c, p.q, p.h)
+            K, f = pat.assemble(d["E"], d["nu"])
+            pat.add_point_loads(d["lx"], d["lf"], f)
+            if Kh is None:
+                Kh = (torch.empty(K.shape, dtype=K.dtype, pin_memory=True),
+                      torch.empty(f.shape, dtype=f.dtype, pin_memory=True))
+            Kh[0].copy_(K, non_blocking=True)
+            Kh[1].copy_(f, non_blocking=True)
+            pat.free()
+            return K.numel() * 8 + f.numel() * 8
+
+        e2e_step()
+        torch.cuda.synchronize()
+        n_e2e = max(2, min(args.steps, 5))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(n_e2e):
+            d2h = e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = 1e3 * (time.perf_counter() - t0) / n_e2e
+        if dist is not None:
+            tms = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(tms, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tms.item())
+        e2e = {"value": world * p.n_points / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "n_nodes": p.n_nodes, "n_points": p.n_points,
+                          "step": "rpim_build_pattern + rpim_assemble + rpim_add_point_loads",
+                          "l2": "working set larger than L2 (K %.2f GB, shape functions %.2f GB)"
+                                % (nnzb * 72 / 1e9, nsup.sum() * 32 / 1e9),
+                          "parallelism": "replicas" if world > 1 else "single GPU"},
+               "roofline": roof, "kernel_ms_per_launch": kernel_ms, "kernel_time_share": kernel_share,
+               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+               "solve": solve, "fp64_peak_gflops_measured": peak_gflops}
+        print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the penalty + PCG measurement")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

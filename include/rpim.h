@@ -1,0 +1,219 @@
+/*
+ * rpim.h -- C ABI of the GB300 (sm_103a) RPIM stiffness-assembly library.
+ *
+ * The library follows the three stages of the pipeline described in Sec. 2
+ * of the paper: (1) assemble the global stiffness matrix by integrating the
+ * "element stiffness matrix of each field node" over its background cell,
+ * (2) enforce displacement boundary conditions by the penalty method,
+ * (3) solve the system and recover stresses. The method is the radial point
+ * interpolation method (RPIM) with multiquadric radial basis and linear
+ * polynomial augmentation (Sec. 1, refs. [23,24]).
+ *
+ * Conventions
+ *  - Every array argument is a DEVICE pointer owned by the caller unless it
+ *    is marked "host". Arrays are dense, C order, double or integer as typed.
+ *  - Calls are ordered on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream). A call that must report sizes or convergence synchronises
+ *    `stream`; each entry's comment says so.
+ *  - DOF numbering: 3*node + {0:x, 1:y, 2:z}, nodes in the caller's order.
+ *  - K is stored as a 3x3-block CSR matrix ("BSR"): `rowptr` (int64,
+ *    n_nodes+1), `cols` (int32, ascending within a row), values as 9 doubles
+ *    per block, row-major inside the block. K is symmetric: block (J,I) is
+ *    the transpose of block (I,J), bit for bit.
+ *  - Errors are returned as rpim_status codes, never by trapping; a kernel
+ *    that meets an error records it on the device and the next synchronising
+ *    call of the same pattern returns it. rpim_last_error() gives a
+ *    thread-local message (for example the failing point index).
+ *  - Thread safety: one pattern must not be used from two host threads at
+ *    once; distinct patterns are independent.
+ */
+#ifndef RPIM_H
+#define RPIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rpim_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    RPIM_OK = 0,
+    RPIM_E_ARG = 1,       /* invalid argument (null pointer, bad size, bad parameter)      */
+    RPIM_E_CUDA = 2,      /* a CUDA runtime call failed                                     */
+    RPIM_E_OOM = 3,       /* device or host allocation failed                               */
+    RPIM_E_SUPPORT = 4,   /* a point has fewer than 4 or more than RPIM_MAX_SUPPORT nodes   */
+    RPIM_E_SINGULAR = 5,  /* degenerate support: the moment problem is singular             */
+    RPIM_E_NOCONV = 6,    /* PCG reached max_iter before the tolerance                      */
+    RPIM_E_NONFINITE = 7, /* a NaN or infinity was met in the inputs or the iteration       */
+    RPIM_E_TIMEOUT = 8    /* reserved: a bounded device wait gave up                        */
+} rpim_status;
+
+/* Largest support (nodes per point) the shape-function kernel accepts. */
+#define RPIM_MAX_SUPPORT 216
+
+/*
+ * RPIM parameters. Radii are in units of the nodal spacing h:
+ *   support radius r_s = alpha_s * h;
+ *   multiquadric R(r) = (r^2 + (alpha_c h)^2)^q, written in the local
+ *   coordinates xi = (x - x_point)/h as (|xi|^2 + alpha_c^2)^q (the shape
+ *   functions do not depend on this scaling);
+ *   gauss_order: points per axis of the cell quadrature rule; only 2 is
+ *   implemented (2x2x2 Gauss-Legendre per node cell).
+ */
+typedef struct {
+    double alpha_s;
+    double alpha_c;
+    double q;
+    double h;
+    int32_t gauss_order;
+} rpim_params;
+
+typedef struct rpim_pattern rpim_pattern; /* opaque, owned by the library */
+
+typedef struct {
+    int64_t n_nodes;     /* field nodes                                        */
+    int64_t n_points;    /* volume integration points = 8 n_nodes              */
+    int64_t n_entries;   /* sum over points of the support size                */
+    int64_t nnz_blocks;  /* 3x3 blocks of K                                    */
+    int32_t max_support; /* largest support size                               */
+    int32_t min_support; /* smallest support size                              */
+    int32_t max_row;     /* largest number of blocks in a row                  */
+    int32_t device;      /* CUDA device the pattern lives on                   */
+} rpim_pattern_info;
+
+/*
+ * Stage 1a (Sec. 2): build everything that depends only on the node cloud.
+ * Computes on the device, in order: the 2x2x2 Gauss points of every node
+ * cell (point 8*i + a + 2b + 4c of cell i), a uniform-grid cell list of the
+ * nodes (cell edge >= r_s), the support of every point (nodes with
+ * |x_i - x_g|^2 <= r_s^2, ascending node id), the node -> point incidence,
+ * and the BSR pattern of K (block (I,J) present iff some point supports both
+ * I and J).
+ *   xyz      [n_nodes*3]  node coordinates (device, read during the call only)
+ *   cell_lo  [n_nodes*3]  lower corner of each node's cell (device)
+ *   cell_hi  [n_nodes*3]  upper corner (device)
+ *   params   host pointer
+ *   out      host: receives the new pattern (free with rpim_pattern_free)
+ *   nnz_blocks host, optional: number of 3x3 blocks of K
+ * Synchronises `stream` (sizes come back to the host).
+ * Errors: RPIM_E_ARG, RPIM_E_SUPPORT (point index in rpim_last_error),
+ * RPIM_E_OOM, RPIM_E_CUDA.
+ */
+rpim_status rpim_build_pattern(int64_t n_nodes, const double *xyz, const double *cell_lo,
+                               const double *cell_hi, const rpim_params *params,
+                               rpim_stream_t stream, rpim_pattern **out, int64_t *nnz_blocks);
+
+/* Releases the pattern and all device memory it owns (stream-ordered on the
+ * stream of the last call that used it). NULL is accepted. */
+rpim_status rpim_pattern_free(rpim_pattern *pattern);
+
+/* Sizes of a pattern (host struct). */
+rpim_status rpim_pattern_get_info(const rpim_pattern *pattern, rpim_pattern_info *info);
+
+/* Borrowed device pointers to the BSR structure of K (valid until free). */
+rpim_status rpim_pattern_csr(const rpim_pattern *pattern, const int64_t **rowptr,
+                             const int32_t **cols);
+
+/* Borrowed device pointers to the integration points (n_points x 3, AoS),
+ * their weights w|J| and the point supports (offsets int64 [n_points+1],
+ * node ids int32 [n_entries], ascending within a point). */
+rpim_status rpim_pattern_points(const rpim_pattern *pattern, const double **xyz,
+                                const double **wj, const int64_t **support_offsets,
+                                const int32_t **support_ids);
+
+/*
+ * Copies of the pattern's structure into caller-owned device buffers
+ * (stream ordered, no synchronisation): rowptr [n_nodes+1] (int64),
+ * cols [nnz_blocks] (int32); points [n_points*3], wj [n_points],
+ * support_offsets [n_points+1] (int64), support_ids [n_entries] (int32).
+ * Any output pointer may be NULL to skip it.
+ */
+rpim_status rpim_pattern_copy_csr(const rpim_pattern *pattern, int64_t *rowptr, int32_t *cols,
+                                  rpim_stream_t stream);
+rpim_status rpim_pattern_copy_points(const rpim_pattern *pattern, double *xyz, double *wj,
+                                     int64_t *support_offsets, int32_t *support_ids,
+                                     rpim_stream_t stream);
+
+/*
+ * Stage 1b (Sec. 2): assemble K and the body-force vector.
+ * For every integration point g: RPIM shape functions phi and their
+ * gradients at g from its support (multiquadric + linear polynomial moment
+ * problem, FP64), then, per point, w|J| B_I^T D(E_g, nu_g) B_J for every
+ * pair (I, J) of its support, and f_I = phi_I(g) b w|J|. K and f are sums
+ * over points in ascending point order for every entry (deterministic, no
+ * atomics); K is exactly symmetric.
+ *   E, nu    [n_points]   Young's modulus and Poisson's ratio per point
+ *   body     [3]          body force per unit volume (device), or NULL
+ *   K_vals   [9*nnz_blocks] output, overwritten
+ *   f        [3*n_nodes]  output, overwritten with the body-force vector
+ * Synchronises `stream` to report per-point errors.
+ * Errors: RPIM_E_ARG, RPIM_E_SINGULAR (point index in rpim_last_error),
+ * RPIM_E_NONFINITE, RPIM_E_CUDA.
+ */
+rpim_status rpim_assemble(rpim_pattern *pattern, const double *E, const double *nu,
+                          const double *body, double *K_vals, double *f, rpim_stream_t stream);
+
+/*
+ * Shape functions only: writes, for every support entry e of every
+ * integration point, phi[4e .. 4e+3] = (phi, dphi/dx, dphi/dy, dphi/dz)
+ * in the order of rpim_pattern_points' support lists. Synchronises.
+ */
+rpim_status rpim_shape_functions(rpim_pattern *pattern, double *phi, rpim_stream_t stream);
+
+/*
+ * Surface loads lumped at points (Sec. 3 examples: pressure, shear traction):
+ * f_I += sum_p phi_I(x_p) F_p, with F_p = traction x quadrature weight,
+ * summed in ascending p for each node. Point supports use the pattern's
+ * cell list and parameters.
+ *   n_pts, xyz [n_pts*3], force [n_pts*3]; f [3*n_nodes] accumulated.
+ * Synchronises. Errors as rpim_assemble.
+ */
+rpim_status rpim_add_point_loads(rpim_pattern *pattern, int64_t n_pts, const double *xyz,
+                                 const double *force, double *f, rpim_stream_t stream);
+
+/*
+ * Stage 2 (Sec. 2): penalty enforcement of prescribed displacements, one GPU
+ * thread per constrained DOF as in the paper: alpha = penalty_scale *
+ * max_i K_ii (over all scalar diagonal entries, computed on the device), then
+ * K_dd += alpha and f_d += alpha * values[i] for d = dofs[i].
+ *   m, dofs [m] (int64, unique), values [m]
+ *   alpha_out host, optional: receives alpha (synchronises when given).
+ * Errors: RPIM_E_ARG (DOF out of range or repeated).
+ */
+rpim_status rpim_apply_penalty_bc(rpim_pattern *pattern, double *K_vals, double *f, int64_t m,
+                                  const int64_t *dofs, const double *values, double penalty_scale,
+                                  double *alpha_out, rpim_stream_t stream);
+
+/*
+ * Stage 3 (Sec. 2): solve K u = f by Jacobi-preconditioned conjugate
+ * gradients in FP64 with deterministic reductions. u holds the initial guess
+ * on entry. Stops when ||r||_2 <= rtol ||f||_2 or after max_iter iterations.
+ *   iters, relres host, optional. Synchronises.
+ * Errors: RPIM_E_NOCONV (u holds the last iterate), RPIM_E_NONFINITE.
+ */
+rpim_status rpim_solve_pcg(rpim_pattern *pattern, const double *K_vals, const double *f,
+                           double *u, double rtol, int32_t max_iter, int32_t *iters,
+                           double *relres, rpim_stream_t stream);
+
+/*
+ * Stresses at arbitrary points: sigma_p = D(E_p, nu_p) sum_I B_I(x_p) u_I,
+ * Voigt order xx, yy, zz, yz, xz, xy (engineering shear strains in B).
+ *   n_pts, xyz [n_pts*3], E [n_pts], nu [n_pts], u [3*n_nodes],
+ *   sigma [n_pts*6] output. Synchronises.
+ */
+rpim_status rpim_stress(rpim_pattern *pattern, const double *u, int64_t n_pts,
+                        const double *xyz, const double *E, const double *nu, double *sigma,
+                        rpim_stream_t stream);
+
+/* Thread-local description of the last error returned on this thread. */
+const char *rpim_last_error(void);
+
+/* Library version string. */
+const char *rpim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPIM_H */

@@ -1,0 +1,318 @@
+"""GB300 (sm_103a) RPIM stiffness assembly -- Python binding of librpim.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``librpim.so`` behind the C ABI declared in ``include/rpim.h``.
+PyTorch provides device memory and streams. The functions ``rpim_*`` mirror
+the C entry points one to one; :class:`Pattern` is a thin convenience wrapper.
+
+There is no CPU fallback: if the library is missing or no CUDA device is
+present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librpim.so")
+
+RPIM_MAX_SUPPORT = 216
+STATUS = {0: "OK", 1: "E_ARG", 2: "E_CUDA", 3: "E_OOM", 4: "E_SUPPORT", 5: "E_SINGULAR",
+          6: "E_NOCONV", 7: "E_NONFINITE", 8: "E_TIMEOUT"}
+
+EXPORTED = [
+    "rpim_build_pattern", "rpim_pattern_free", "rpim_pattern_get_info", "rpim_pattern_csr",
+    "rpim_pattern_points", "rpim_pattern_copy_csr", "rpim_pattern_copy_points", "rpim_assemble",
+    "rpim_shape_functions", "rpim_add_point_loads", "rpim_apply_penalty_bc", "rpim_solve_pcg",
+    "rpim_stress", "rpim_last_error", "rpim_version", "rpim_probe_dfma", "rpim_probe_dmma",
+    "rpim_kernel_launches", "rpim_profile_enable", "rpim_profile_read", "rpim_kernel_series_info",
+]
+
+
+class RpimError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__("%s: RPIM_%s (%d): %s" % (where, STATUS.get(status, "?"), status, msg))
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("alpha_s", C.c_double), ("alpha_c", C.c_double), ("q", C.c_double),
+                ("h", C.c_double), ("gauss_order", C.c_int32)]
+
+
+class PatternInfo(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_points", C.c_int64), ("n_entries", C.c_int64),
+                ("nnz_blocks", C.c_int64), ("max_support", C.c_int32), ("min_support", C.c_int32),
+                ("max_row", C.c_int32), ("device", C.c_int32)]
+
+
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile librpim.so in-tree (nvcc, sm_103a)."""
+    from . import _compile
+    return _compile.build(force=force, verbose=verbose)
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("librpim.so is not built (call paper_1802_04256_gb300.build())")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    sig = {
+        "rpim_build_pattern": [i64, vp, vp, vp, C.POINTER(Params), vp, C.POINTER(vp), C.POINTER(i64)],
+        "rpim_pattern_free": [vp],
+        "rpim_pattern_get_info": [vp, C.POINTER(PatternInfo)],
+        "rpim_pattern_csr": [vp, C.POINTER(vp), C.POINTER(vp)],
+        "rpim_pattern_points": [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)],
+        "rpim_pattern_copy_csr": [vp, vp, vp, vp],
+        "rpim_pattern_copy_points": [vp, vp, vp, vp, vp, vp],
+        "rpim_assemble": [vp, vp, vp, vp, vp, vp, vp],
+        "rpim_shape_functions": [vp, vp, vp],
+        "rpim_add_point_loads": [vp, i64, vp, vp, vp, vp],
+        "rpim_apply_penalty_bc": [vp, vp, vp, i64, vp, vp, dbl, C.POINTER(dbl), vp],
+        "rpim_solve_pcg": [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp],
+        "rpim_stress": [vp, vp, i64, vp, vp, vp, vp, vp],
+        "rpim_probe_dfma": [i32, C.POINTER(dbl)],
+        "rpim_probe_dmma": [i32, C.POINTER(dbl)],
+        "rpim_profile_enable": [i32],
+        "rpim_profile_read": [C.c_char_p, i64, i32],
+        "rpim_kernel_series_info": [dbl, dbl, dbl, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                    C.POINTER(dbl)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    L.rpim_kernel_launches.restype = C.c_int64
+    L.rpim_last_error.restype = C.c_char_p
+    L.rpim_version.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(st, where):
+    if st != 0:
+        raise RpimError(st, where, lib().rpim_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype):
+    if t.dtype != dtype:
+        raise TypeError("expected %s, got %s" % (dtype, t.dtype))
+    return _ptr(t)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# --------------------------------------------------------------------------- C entry points
+def rpim_build_pattern(xyz, cell_lo, cell_hi, params: Params, stream=None):
+    h = C.c_void_p()
+    nnz = C.c_int64(0)
+    st = lib().rpim_build_pattern(xyz.shape[0], _dev(xyz, torch.float64), _dev(cell_lo, torch.float64),
+                                  _dev(cell_hi, torch.float64), C.byref(params), _stream(stream),
+                                  C.byref(h), C.byref(nnz))
+    _check(st, "rpim_build_pattern")
+    return h, nnz.value
+
+
+def rpim_pattern_free(handle):
+    lib().rpim_pattern_free(handle)
+
+
+def rpim_pattern_get_info(handle) -> PatternInfo:
+    info = PatternInfo()
+    _check(lib().rpim_pattern_get_info(handle, C.byref(info)), "rpim_pattern_get_info")
+    return info
+
+
+def rpim_pattern_copy_csr(handle, rowptr, cols, stream=None):
+    _check(lib().rpim_pattern_copy_csr(handle, _dev(rowptr, torch.int64), _dev(cols, torch.int32),
+                                       _stream(stream)), "rpim_pattern_copy_csr")
+
+
+def rpim_pattern_copy_points(handle, xyz, wj, soff, sidx, stream=None):
+    _check(lib().rpim_pattern_copy_points(handle, _ptr(xyz), _ptr(wj), _ptr(soff), _ptr(sidx),
+                                          _stream(stream)), "rpim_pattern_copy_points")
+
+
+def rpim_assemble(handle, E, nu, body, K_vals, f, stream=None):
+    _check(lib().rpim_assemble(handle, _dev(E, torch.float64), _dev(nu, torch.float64),
+                               None if body is None else _dev(body, torch.float64),
+                               _dev(K_vals, torch.float64), _dev(f, torch.float64), _stream(stream)),
+           "rpim_assemble")
+
+
+def rpim_shape_functions(handle, phi, stream=None):
+    _check(lib().rpim_shape_functions(handle, _dev(phi, torch.float64), _stream(stream)),
+           "rpim_shape_functions")
+
+
+def rpim_add_point_loads(handle, xyz, force, f, stream=None):
+    _check(lib().rpim_add_point_loads(handle, xyz.shape[0], _dev(xyz, torch.float64),
+                                      _dev(force, torch.float64), _dev(f, torch.float64),
+                                      _stream(stream)), "rpim_add_point_loads")
+
+
+def rpim_apply_penalty_bc(handle, K_vals, f, dofs, values, penalty_scale=1e8, stream=None):
+    a = C.c_double(0)
+    _check(lib().rpim_apply_penalty_bc(handle, _dev(K_vals, torch.float64), _dev(f, torch.float64),
+                                       dofs.shape[0], _dev(dofs, torch.int64),
+                                       _dev(values, torch.float64), penalty_scale, C.byref(a),
+                                       _stream(stream)), "rpim_apply_penalty_bc")
+    return a.value
+
+
+def rpim_solve_pcg(handle, K_vals, f, u, rtol=1e-10, max_iter=100000, stream=None, check=True):
+    it = C.c_int32(0)
+    rr = C.c_double(0)
+    st = lib().rpim_solve_pcg(handle, _dev(K_vals, torch.float64), _dev(f, torch.float64),
+                              _dev(u, torch.float64), rtol, max_iter, C.byref(it), C.byref(rr),
+                              _stream(stream))
+    if check:
+        _check(st, "rpim_solve_pcg")
+    return it.value, rr.value, st
+
+
+def rpim_stress(handle, u, xyz, E, nu, sigma, stream=None):
+    _check(lib().rpim_stress(handle, _dev(u, torch.float64), xyz.shape[0], _dev(xyz, torch.float64),
+                             _dev(E, torch.float64), _dev(nu, torch.float64),
+                             _dev(sigma, torch.float64), _stream(stream)), "rpim_stress")
+
+
+def rpim_probe_dfma(repeats=5) -> float:
+    """Measured FP64 FMA-pipe throughput of the current device, GFLOP/s."""
+    g = C.c_double(0)
+    _check(lib().rpim_probe_dfma(repeats, C.byref(g)), "rpim_probe_dfma")
+    return g.value
+
+
+def rpim_probe_dmma(repeats=5) -> float:
+    """Measured FP64 tensor-core (mma.sync m8n8k4) throughput, GFLOP/s."""
+    g = C.c_double(0)
+    _check(lib().rpim_probe_dmma(repeats, C.byref(g)), "rpim_probe_dmma")
+    return g.value
+
+
+def rpim_kernel_series_info(alpha_c=4.0, alpha_s=2.5, q=1.03):
+    """(pieces, degree, fp64_terms, max_err) of the kernel series (host only)."""
+    p, d, h = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    e = C.c_double(0)
+    st = lib().rpim_kernel_series_info(alpha_c, alpha_s, q, C.byref(p), C.byref(d), C.byref(h), C.byref(e))
+    _check(st, "rpim_kernel_series_info")
+    return p.value, d.value, h.value, e.value
+
+
+def rpim_kernel_launches() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(lib().rpim_kernel_launches())
+
+
+def rpim_profile_enable(on: bool = True) -> None:
+    _check(lib().rpim_profile_enable(1 if on else 0), "rpim_profile_enable")
+
+
+def rpim_profile_read(reset: bool = True) -> dict:
+    """Per-kernel {name: (launches, total_ms)} gathered while timing was on."""
+    import json
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib().rpim_profile_read(buf, len(buf), 1 if reset else 0), "rpim_profile_read")
+    return {k: (v[0], v[1]) for k, v in json.loads(buf.value.decode()).items()}
+
+
+def rpim_version() -> str:
+    return lib().rpim_version().decode()
+
+
+# --------------------------------------------------------------------------- convenience
+class Pattern:
+    """Owns an ``rpim_pattern``: integration points, supports and the BSR
+    pattern of K for one node cloud."""
+
+    def __init__(self, xyz, cell_lo, cell_hi, alpha_s, alpha_c, q, h, stream=None):
+        self.params = Params(alpha_s, alpha_c, q, h, 2)
+        self.device = xyz.device
+        self.handle, self.nnz_blocks = rpim_build_pattern(xyz, cell_lo, cell_hi, self.params, stream)
+        self.info = rpim_pattern_get_info(self.handle)
+
+    @classmethod
+    def from_problem(cls, p, device="cuda", stream=None):
+        t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()
+        return cls(t(p.xyz), t(p.cell_lo), t(p.cell_hi), p.alpha_s, p.alpha_c, p.q, p.h, stream)
+
+    def free(self):
+        if self.handle:
+            rpim_pattern_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def csr(self, stream=None):
+        rowptr = torch.empty(self.info.n_nodes + 1, dtype=torch.int64, device=self.device)
+        cols = torch.empty(max(self.nnz_blocks, 1), dtype=torch.int32, device=self.device)
+        rpim_pattern_copy_csr(self.handle, rowptr, cols, stream)
+        return rowptr, cols[: self.nnz_blocks]
+
+    def points(self, stream=None):
+        i = self.info
+        xyz = torch.empty(i.n_points, 3, dtype=torch.float64, device=self.device)
+        wj = torch.empty(i.n_points, dtype=torch.float64, device=self.device)
+        soff = torch.empty(i.n_points + 1, dtype=torch.int64, device=self.device)
+        sidx = torch.empty(max(i.n_entries, 1), dtype=torch.int32, device=self.device)
+        rpim_pattern_copy_points(self.handle, xyz, wj, soff, sidx, stream)
+        return xyz, wj, soff, sidx[: i.n_entries]
+
+    def shape_functions(self, stream=None):
+        phi = torch.empty(self.info.n_entries, 4, dtype=torch.float64, device=self.device)
+        rpim_shape_functions(self.handle, phi, stream)
+        return phi
+
+    def assemble(self, E, nu, body=None, K=None, f=None, stream=None):
+        if K is None:
+            K = torch.empty(self.nnz_blocks, 9, dtype=torch.float64, device=self.device)
+        if f is None:
+            f = torch.empty(3 * self.info.n_nodes, dtype=torch.float64, device=self.device)
+        rpim_assemble(self.handle, E, nu, body, K, f, stream)
+        return K, f
+
+    def add_point_loads(self, xyz, force, f, stream=None):
+        rpim_add_point_loads(self.handle, xyz, force, f, stream)
+        return f
+
+    def apply_penalty(self, K, f, dofs, values, scale=1e8, stream=None):
+        return rpim_apply_penalty_bc(self.handle, K, f, dofs, values, scale, stream)
+
+    def solve_pcg(self, K, f, u=None, rtol=1e-10, max_iter=100000, stream=None, check=True):
+        if u is None:
+            u = torch.zeros(3 * self.info.n_nodes, dtype=torch.float64, device=self.device)
+        it, rr, st = rpim_solve_pcg(self.handle, K, f, u, rtol, max_iter, stream, check)
+        return u, it, rr
+
+    def stress(self, u, xyz, E, nu, stream=None):
+        sig = torch.empty(xyz.shape[0], 6, dtype=torch.float64, device=self.device)
+        rpim_stress(self.handle, u, xyz, E, nu, sig, stream)
+        return sig

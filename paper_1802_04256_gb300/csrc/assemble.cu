@@ -1,0 +1,371 @@
+// Stage 1b: assembly of K and f, surface loads and stress recovery.
+//
+// K_IJ = sum_g w_g B_I^T D_g B_J. For an isotropic D this 3x3 block is
+//   K_ab = sum_g [ lambda_g w_g dI_a dJ_b + mu_g w_g (dI_b dJ_a + delta_ab dI . dJ) ]
+// with dI = grad phi_I(x_g). Assembly is row-owner: one warp owns row I, walks
+// the points whose support contains I in ascending order and accumulates, in
+// shared memory, the blocks (I, J) for J >= I of each such point. Every block
+// is therefore a fixed-order sum (no atomics, bitwise reproducible). The
+// lower blocks are copied, transposed, from the upper ones.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace rpim {
+
+// per point: (lambda w|J|, mu w|J|) from E and nu
+__global__ void lame_kernel(int64_t n_pts, const double *E, const double *nu, const double *wj,
+                            double *lamw, DevError *err)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_pts;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const double e = E[g], v = nu[g], w = wj[g];
+        if (!(e > 0.0) || !(v > -1.0) || !(v < 0.5) || !isfinite(e)) {
+            dev_fail(err, RPIM_E_ARG, g);
+            lamw[2 * g] = lamw[2 * g + 1] = 0.0;
+            continue;
+        }
+        const double lam = e * v / ((1.0 + v) * (1.0 - 2.0 * v));
+        const double mu = e / (2.0 * (1.0 + v));
+        lamw[2 * g] = lam * w;
+        lamw[2 * g + 1] = mu * w;
+    }
+}
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t key)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Row kernel. One warp owns row I and accumulates the upper blocks (J >= I)
+// of its row in place in K (L2-resident read-modify-write; every block is
+// touched by one lane at a time, in ascending point order). Per-point scalars
+// are prefetched 32 points at a time, one point per lane, and broadcast by
+// shuffles.
+//
+// Uniform rows (all points of the row have the same nu, hence the same
+// kappa = lambda/mu = 2 nu / (1 - 2 nu)) accumulate only
+//   V_ab = sum_g mu_g w_g dI_a dJ_b
+// (9 fused multiply-adds per pair) and finish with
+//   K = kappa V + V^T + tr(V) I.
+// Other rows accumulate K_ab directly (lambda and mu terms, 24 FP64
+// operations per pair).
+__global__ void __launch_bounds__(256) row_kernel(int64_t n_nodes, const int64_t *__restrict__ toff,
+                                                  const int64_t *__restrict__ tent,
+                                                  const int32_t *__restrict__ entry_pt,
+                                                  const int64_t *__restrict__ soff,
+                                                  const int32_t *__restrict__ sidx,
+                                                  const double *__restrict__ phi,
+                                                  const double *__restrict__ lamw,
+                                                  const double *__restrict__ wj,
+                                                  const double *__restrict__ nu,
+                                                  const double *__restrict__ body,
+                                                  const int64_t *__restrict__ rowptr,
+                                                  const int32_t *__restrict__ cols,
+                                                  const int64_t *__restrict__ diag, double *K,
+                                                  double *__restrict__ f, DevError *err)
+{
+    const int lane = threadIdx.x & 31;
+    double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+    if (body) { b0 = body[0]; b1 = body[1]; b2 = body[2]; }
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < n_nodes; I += warps) {
+        const int64_t sd = diag[I], rend = rowptr[I + 1];
+        const int U = (int)(rend - sd);
+        const int32_t *ucols = cols + sd;
+        double *Ku = K + 9 * sd;
+        for (int64_t i = lane; i < 9 * (int64_t)U; i += 32) Ku[i] = 0.0;
+        const int64_t t0 = toff[I], t1 = toff[I + 1];
+        // uniform Poisson ratio over the row's points?
+        const double nu0 = nu[entry_pt[tent[t0]]];
+        bool uni = true;
+        for (int64_t t = t0 + lane; t < t1; t += 32) uni &= nu[entry_pt[tent[t]]] == nu0;
+        uni = __all_sync(0xffffffffu, uni);
+        __syncwarp();
+        double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+        for (int64_t tb = t0; tb < t1; tb += 32) {
+            // prefetch: lane l loads the scalars of point tb + l
+            int64_t pe = 0, pend = 0;
+            double pA0 = 0, pA1 = 0, pA2 = 0, pM0 = 0, pM1 = 0, pM2 = 0, pw = 0;
+            if (tb + lane < t1) {
+                pe = tent[tb + lane];
+                const int32_t g = entry_pt[pe];
+                pend = soff[g + 1];
+                const double2 pa = *(const double2 *)(phi + 4 * pe);
+                const double2 pb = *(const double2 *)(phi + 4 * pe + 2);
+                const double lw = lamw[2 * (int64_t)g], mw = lamw[2 * (int64_t)g + 1];
+                pA0 = lw * pa.y; pA1 = lw * pb.x; pA2 = lw * pb.y;
+                pM0 = mw * pa.y; pM1 = mw * pb.x; pM2 = mw * pb.y;
+                pw = pa.x * wj[g];
+            }
+            const int cnt = (int)min((int64_t)32, t1 - tb);
+            for (int k = 0; k < cnt; k++) {
+                const int64_t e = __shfl_sync(0xffffffffu, pe, k);
+                const int64_t end = __shfl_sync(0xffffffffu, pend, k);
+                const double M0 = __shfl_sync(0xffffffffu, pM0, k), M1 = __shfl_sync(0xffffffffu, pM1, k),
+                             M2 = __shfl_sync(0xffffffffu, pM2, k);
+                const double w = __shfl_sync(0xffffffffu, pw, k);
+                f0 = fma(w, b0, f0);
+                f1 = fma(w, b1, f1);
+                f2 = fma(w, b2, f2);
+                if (uni) {
+                    for (int64_t q = e + lane; q < end; q += 32) {
+                        const int32_t J = sidx[q];
+                        const int slot = lower_bound_i32(ucols, U, J);
+                        if (slot >= U || ucols[slot] != J) { dev_fail(err, RPIM_E_ARG, I); continue; }
+                        const double2 qa = *(const double2 *)(phi + 4 * q);
+                        const double2 qb = *(const double2 *)(phi + 4 * q + 2);
+                        const double d0 = qa.y, d1 = qb.x, d2 = qb.y;
+                        double *o = Ku + 9 * slot;
+                        o[0] = fma(M0, d0, o[0]); o[1] = fma(M0, d1, o[1]); o[2] = fma(M0, d2, o[2]);
+                        o[3] = fma(M1, d0, o[3]); o[4] = fma(M1, d1, o[4]); o[5] = fma(M1, d2, o[5]);
+                        o[6] = fma(M2, d0, o[6]); o[7] = fma(M2, d1, o[7]); o[8] = fma(M2, d2, o[8]);
+                    }
+                } else {
+                    const double A0 = __shfl_sync(0xffffffffu, pA0, k), A1 = __shfl_sync(0xffffffffu, pA1, k),
+                                 A2 = __shfl_sync(0xffffffffu, pA2, k);
+                    for (int64_t q = e + lane; q < end; q += 32) {
+                        const int32_t J = sidx[q];
+                        const int slot = lower_bound_i32(ucols, U, J);
+                        if (slot >= U || ucols[slot] != J) { dev_fail(err, RPIM_E_ARG, I); continue; }
+                        const double2 qa = *(const double2 *)(phi + 4 * q);
+                        const double2 qb = *(const double2 *)(phi + 4 * q + 2);
+                        const double d0 = qa.y, d1 = qb.x, d2 = qb.y;
+                        const double md = fma(M2, d2, fma(M1, d1, M0 * d0));
+                        double *o = Ku + 9 * slot;
+                        o[0] = fma(M0, d0, fma(A0, d0, o[0] + md));
+                        o[1] = fma(M1, d0, fma(A0, d1, o[1]));
+                        o[2] = fma(M2, d0, fma(A0, d2, o[2]));
+                        o[3] = fma(M0, d1, fma(A1, d0, o[3]));
+                        o[4] = fma(M1, d1, fma(A1, d1, o[4] + md));
+                        o[5] = fma(M2, d1, fma(A1, d2, o[5]));
+                        o[6] = fma(M0, d2, fma(A2, d0, o[6]));
+                        o[7] = fma(M1, d2, fma(A2, d1, o[7]));
+                        o[8] = fma(M2, d2, fma(A2, d2, o[8] + md));
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // finish the upper blocks
+        const double kappa = 2.0 * nu0 / (1.0 - 2.0 * nu0);
+        for (int s = lane; s < U; s += 32) {
+            double *o = Ku + 9 * s;
+            double k[9];
+#pragma unroll
+            for (int i = 0; i < 9; i++) k[i] = o[i];
+            if (uni) {
+                const double tr = (k[0] + k[4]) + k[8];
+                double v[9];
+#pragma unroll
+                for (int i = 0; i < 9; i++) v[i] = k[i];
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+#pragma unroll
+                    for (int bb = 0; bb < 3; bb++) k[3 * a + bb] = fma(kappa, v[3 * a + bb], v[3 * bb + a]);
+                k[0] += tr; k[4] += tr; k[8] += tr;
+            }
+            if (s == 0) { k[3] = k[1]; k[6] = k[2]; k[7] = k[5]; } // diagonal block: exact symmetry
+#pragma unroll
+            for (int i = 0; i < 9; i++) o[i] = k[i];
+        }
+        if (lane == 0) {
+            f[3 * I] = f0;
+            f[3 * I + 1] = f1;
+            f[3 * I + 2] = f2;
+        }
+        __syncwarp();
+    }
+}
+
+// lower blocks: K_IJ = (K_JI)^T for J < I
+__global__ void mirror_kernel(int64_t n_nodes, const int64_t *rowptr, const int32_t *cols, double *K)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < n_nodes; I += warps) {
+        const int64_t r0 = rowptr[I], r1 = rowptr[I + 1];
+        for (int64_t t = r0 + lane; t < r1; t += 32) {
+            const int32_t J = cols[t];
+            if (J >= I) break;
+            const int64_t j0 = rowptr[J];
+            const int len = (int)(rowptr[J + 1] - j0);
+            const int off = lower_bound_i32(cols + j0, len, (int32_t)I);
+            if (off >= len || cols[j0 + off] != (int32_t)I) continue;
+            const double *src = K + 9 * (j0 + off);
+            double *dst = K + 9 * t;
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int b = 0; b < 3; b++) dst[3 * a + b] = src[3 * b + a];
+        }
+    }
+}
+
+// f_I += sum over load entries of node I (ascending) of phi * F_point
+__global__ void load_gather_kernel(int64_t n_nodes, const int64_t *toff, const int64_t *tent,
+                                   const int32_t *entry_pt, const double *phi, const double *force,
+                                   double *f)
+{
+    for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < n_nodes;
+         I += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t0 = toff[I], t1 = toff[I + 1];
+        if (t0 == t1) continue;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int64_t t = t0; t < t1; t++) {
+            const int64_t e = tent[t];
+            const int64_t p = entry_pt[e];
+            const double ph = phi[4 * e];
+            a0 = fma(ph, force[3 * p], a0);
+            a1 = fma(ph, force[3 * p + 1], a1);
+            a2 = fma(ph, force[3 * p + 2], a2);
+        }
+        f[3 * I] += a0;
+        f[3 * I + 1] += a1;
+        f[3 * I + 2] += a2;
+    }
+}
+
+__device__ __forceinline__ double wsum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sigma = D(E, nu) sum_j B_j u_j, one warp per point
+__global__ void stress_kernel(int64_t n_pts, const int64_t *soff, const int32_t *sidx, const double *phi,
+                              const double *u, const double *E, const double *nu, double *sigma,
+                              DevError *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n_pts; p += warps) {
+        double e[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t q = soff[p] + lane; q < soff[p + 1]; q += 32) {
+            const int64_t J = sidx[q];
+            const double gx = phi[4 * q + 1], gy = phi[4 * q + 2], gz = phi[4 * q + 3];
+            const double ux = u[3 * J], uy = u[3 * J + 1], uz = u[3 * J + 2];
+            e[0] = fma(gx, ux, e[0]);
+            e[1] = fma(gy, uy, e[1]);
+            e[2] = fma(gz, uz, e[2]);
+            e[3] = fma(gz, uy, fma(gy, uz, e[3]));
+            e[4] = fma(gz, ux, fma(gx, uz, e[4]));
+            e[5] = fma(gy, ux, fma(gx, uy, e[5]));
+        }
+#pragma unroll
+        for (int k = 0; k < 6; k++) e[k] = wsum(e[k]);
+        if (lane == 0) {
+            const double Ev = E[p], v = nu[p];
+            if (!(Ev > 0.0) || !(v > -1.0) || !(v < 0.5)) {
+                dev_fail(err, RPIM_E_ARG, p);
+                continue;
+            }
+            const double lam = Ev * v / ((1.0 + v) * (1.0 - 2.0 * v));
+            const double mu = Ev / (2.0 * (1.0 + v));
+            const double tr = e[0] + e[1] + e[2];
+            double *o = sigma + 6 * p;
+            o[0] = lam * tr + 2.0 * mu * e[0];
+            o[1] = lam * tr + 2.0 * mu * e[1];
+            o[2] = lam * tr + 2.0 * mu * e[2];
+            o[3] = mu * e[3];
+            o[4] = mu * e[4];
+            o[5] = mu * e[5];
+        }
+    }
+}
+
+static rpim_status ensure_phi(rpim_pattern *p, cudaStream_t s)
+{
+    if (!p->phi) RPIM_CHECK(dalloc(&p->phi, 4 * p->n_entries, s));
+    if (!p->lamw) RPIM_CHECK(dalloc(&p->lamw, 2 * p->n_points, s));
+    return RPIM_OK;
+}
+
+} // namespace rpim
+
+using namespace rpim;
+
+extern "C" rpim_status rpim_shape_functions(rpim_pattern *p, double *phi, rpim_stream_t stream)
+{
+    if (!p || !phi) return fail(RPIM_E_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    RPIM_CHECK(shape_functions(p, p->n_points, p->pts, p->soff, p->sidx, p->max_support, phi, s, "shape"));
+    return check_device_error(p, "shape functions");
+}
+
+extern "C" rpim_status rpim_assemble(rpim_pattern *p, const double *E, const double *nu, const double *body,
+                                     double *K, double *f, rpim_stream_t stream)
+{
+    if (!p || !E || !nu || !K || !f) return fail(RPIM_E_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    RPIM_CHECK(ensure_phi(p, s));
+    launch("lame", lame_kernel, grid_size(p->sm_count, 4, p->n_points, 256), 256, 0, s, p->n_points, E, nu, p->wj, p->lamw, p->err);
+    RPIM_CHECK(shape_functions(p, p->n_points, p->pts, p->soff, p->sidx, p->max_support, p->phi, s, "shape"));
+    launch("row", row_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, 0, s, p->n_nodes, p->toff,
+           p->tent, p->entry_pt, p->soff, p->sidx, p->phi, p->lamw, p->wj, nu, body, p->rowptr, p->cols, p->diag,
+           K, f, p->err);
+    RPIM_CUDA(cudaGetLastError());
+    launch("mirror", mirror_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, 0, s, p->n_nodes, p->rowptr, p->cols, K);
+    RPIM_CUDA(cudaGetLastError());
+    return check_device_error(p, "assemble");
+}
+
+extern "C" rpim_status rpim_add_point_loads(rpim_pattern *p, int64_t n_pts, const double *xyz,
+                                            const double *force, double *f, rpim_stream_t stream)
+{
+    if (!p || (n_pts > 0 && (!xyz || !force || !f)) || n_pts < 0) return fail(RPIM_E_ARG, "bad argument");
+    if (n_pts == 0) return RPIM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    int64_t *soff = nullptr, *toff = nullptr, *tent = nullptr, ne = 0;
+    int32_t *sidx = nullptr, *ept = nullptr, mx = 0, mn = 0, mi = 0;
+    double *phi = nullptr;
+    RPIM_CHECK(search_supports(p, n_pts, xyz, &soff, &sidx, &ne, &mx, &mn, s, "search_loads"));
+    rpim_status st = RPIM_OK;
+    if ((st = dalloc(&phi, 4 * ne, s)) == RPIM_OK && (st = dalloc(&ept, ne, s)) == RPIM_OK) {
+        st = shape_functions(p, n_pts, xyz, soff, sidx, mx, phi, s, "shape_loads");
+        if (st == RPIM_OK) {
+            launch("entry_points_loads", entry_points_kernel, grid_size(p->sm_count, 8, n_pts * 32, 256), 256, 0, s, n_pts, soff, ept);
+            st = build_incidence(p->n_nodes, ne, sidx, &toff, &tent, &mi, s, p->sm_count);
+        }
+        if (st == RPIM_OK) {
+            launch("load_gather", load_gather_kernel, grid_size(p->sm_count, 4, p->n_nodes, 256), 256, 0, s, p->n_nodes, toff, tent, ept, phi, force, f);
+            if (cudaGetLastError() != cudaSuccess) st = fail(RPIM_E_CUDA, "load kernel launch");
+        }
+    }
+    if (st == RPIM_OK) st = check_device_error(p, "point loads");
+    dfree(soff, s); dfree(sidx, s); dfree(phi, s); dfree(ept, s); dfree(toff, s); dfree(tent, s);
+    return st;
+}
+
+extern "C" rpim_status rpim_stress(rpim_pattern *p, const double *u, int64_t n_pts, const double *xyz,
+                                   const double *E, const double *nu, double *sigma, rpim_stream_t stream)
+{
+    if (!p || n_pts < 0 || (n_pts > 0 && (!u || !xyz || !E || !nu || !sigma))) return fail(RPIM_E_ARG, "bad argument");
+    if (n_pts == 0) return RPIM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    int64_t *soff = nullptr, ne = 0;
+    int32_t *sidx = nullptr, mx = 0, mn = 0;
+    double *phi = nullptr;
+    RPIM_CHECK(search_supports(p, n_pts, xyz, &soff, &sidx, &ne, &mx, &mn, s, "search_stress"));
+    rpim_status st = dalloc(&phi, 4 * ne, s);
+    if (st == RPIM_OK) st = shape_functions(p, n_pts, xyz, soff, sidx, mx, phi, s, "shape_stress");
+    if (st == RPIM_OK) {
+        launch("stress", stress_kernel, grid_size(p->sm_count, 8, n_pts * 32, 256), 256, 0, s, n_pts, soff, sidx, phi, u, E, nu, sigma, p->err);
+        if (cudaGetLastError() != cudaSuccess) st = fail(RPIM_E_CUDA, "stress kernel launch");
+    }
+    if (st == RPIM_OK) st = check_device_error(p, "stress");
+    dfree(soff, s); dfree(sidx, s); dfree(phi, s);
+    return st;
+}

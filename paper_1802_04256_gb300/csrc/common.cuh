@@ -1,0 +1,202 @@
+// Internal definitions shared by the translation units of librpim.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/rpim.h"
+
+namespace rpim {
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+rpim_status fail(rpim_status st, const std::string &msg);
+rpim_status cuda_fail(cudaError_t e, const char *what);
+
+#define RPIM_CUDA(call)                                         \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return ::rpim::cuda_fail(e_, #call); \
+    } while (0)
+
+#define RPIM_CHECK(st)                       \
+    do {                                     \
+        rpim_status s_ = (st);               \
+        if (s_ != RPIM_OK) return s_;        \
+    } while (0)
+
+// Device error record: the first failing (code, index) pair wins, encoded as
+// code << 48 | index so that atomicMin keeps the lowest code, then the lowest
+// index (deterministic report).
+struct DevError {
+    unsigned long long word; // 0xFFFF... when clean
+};
+
+__device__ __forceinline__ void dev_fail(DevError *err, int code, long long index)
+{
+    unsigned long long w = ((unsigned long long)code << 48) | ((unsigned long long)index & 0xFFFFFFFFFFFFull);
+    atomicMin(&err->word, w);
+}
+
+// ---------------------------------------------------------------------------
+// kernel-basis series: the multiquadric with its affine-in-s part removed,
+// as piecewise power series in t = (s - centre) / half_width, s = r^2 + c^2.
+// ---------------------------------------------------------------------------
+constexpr int kMaxPieces = 16;
+constexpr int kMaxHead = 16;   // FP64 (head) terms of the value series
+constexpr int kMaxDegree = 24;
+
+struct KernelSeries {
+    int pieces;
+    int degree;                         // highest power kept
+    int n64;                            // powers 0..n64-1 in FP64, n64..degree in FP32
+    float log2_lo;                      // piece = floor((log2 s - log2_lo) * inv_log2r)
+    float inv_log2r;
+    double c2;                          // alpha_c^2
+    double diag;                        // value at s = c2 (r = 0)
+    double check_err;                   // largest error of the host check
+    double centre[kMaxPieces];          // centre of each piece
+    double inv_w[kMaxPieces];           // 1 / half_width
+    double coef[kMaxPieces][kMaxHead];          // value series, powers 0..n64-1
+    float coef_f[kMaxPieces][kMaxDegree + 1];   // value series, powers n64..degree
+    double dcoef[kMaxPieces][kMaxDegree + 1];   // d/ds series, powers 0..degree-1
+};
+
+// Builds the series on the host (long double arithmetic) and checks it
+// against the closed form on a dense sample.
+rpim_status build_kernel_series(double alpha_c, double alpha_s, double q, KernelSeries *ks);
+
+// ---------------------------------------------------------------------------
+// pattern object
+// ---------------------------------------------------------------------------
+struct Grid {
+    double lo[3];
+    double inv_edge;     // 1 / cell edge
+    int n[3];            // cells per axis
+    int64_t cells;
+};
+
+struct Workspace {      // PCG vectors and reduction scratch (lazily sized)
+    double *buf = nullptr;
+    int64_t doubles = 0;
+};
+
+} // namespace rpim
+
+struct rpim_pattern {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    rpim_params prm{};
+    double rs2 = 0.0;      // support radius squared (physical units)
+    double inv_h = 0.0;
+
+    int64_t n_nodes = 0, n_points = 0, n_entries = 0, nnzb = 0;
+    int32_t max_support = 0, min_support = 0, max_row = 0;
+    int32_t max_incident = 0;  // largest number of (point, entry) pairs per node
+    int32_t max_cell = 0;      // largest node count of a grid cell
+
+    rpim::Grid grid{};
+    // nodes
+    double *xyz = nullptr;          // [n_nodes*3] copy of the coordinates
+    double *sorted_xyz = nullptr;   // [n_nodes*4] coordinates in cell order (x,y,z,pad)
+    int32_t *sorted_ids = nullptr;  // [n_nodes] node ids in cell order
+    int32_t *cell_start = nullptr;  // [cells+1]
+    int32_t *node_cell = nullptr;   // [n_nodes] linear cell index of each node
+    int32_t *node_rank = nullptr;   // [n_nodes] position of the node in its cell
+    // integration points
+    double *pts = nullptr;          // [n_points*3]
+    double *wj = nullptr;           // [n_points]
+    // supports
+    int64_t *soff = nullptr;        // [n_points+1]
+    int32_t *sidx = nullptr;        // [n_entries]
+    int32_t *entry_pt = nullptr;    // [n_entries] point of each entry
+    // node -> entries incidence, ascending entry (hence ascending point)
+    int64_t *toff = nullptr;        // [n_nodes+1]
+    int64_t *tent = nullptr;        // [n_entries]
+    // BSR pattern of K
+    int64_t *rowptr = nullptr;      // [n_nodes+1]
+    int32_t *cols = nullptr;        // [nnzb]
+    int64_t *diag = nullptr;        // [n_nodes] slot of the diagonal block
+    // assembly scratch
+    double *phi = nullptr;          // [n_entries*4]
+    double *lamw = nullptr;         // [n_points*2] (lambda w|J|, mu w|J|)
+    // device scalars
+    rpim::DevError *err = nullptr;
+    double *scal = nullptr;         // [16] device scalars (penalty, PCG)
+    rpim::KernelSeries *series = nullptr; // device copy
+    rpim::KernelSeries series_host{};
+    rpim::Workspace ws;
+    int sm_count = 0;
+};
+
+namespace rpim {
+
+// allocation helpers (stream ordered)
+template <class T>
+rpim_status dalloc(T **p, int64_t count, cudaStream_t s)
+{
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMallocAsync((void **)p, (size_t)count * sizeof(T), s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(RPIM_E_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+    }
+    return RPIM_OK;
+}
+template <class T>
+void dfree(T *&p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+}
+
+// device-wide exclusive scan of int64 counts (in place on `data`, n+1
+// entries: data[n] receives the total). Uses `tmp` of scan_tmp_size(n).
+int64_t scan_tmp_size(int64_t n);
+rpim_status exclusive_scan(int64_t *data, int64_t n, int64_t *tmp, cudaStream_t s);
+rpim_status exclusive_scan32(int32_t *data, int64_t n, int64_t *tmp, cudaStream_t s);
+
+// reads the device error word; returns RPIM_OK or the recorded status
+rpim_status check_device_error(rpim_pattern *p, const char *stage);
+
+// support search for arbitrary points (count + fill); output offsets/ids
+// are allocated here (stream ordered) and owned by the caller.
+rpim_status search_supports(rpim_pattern *p, int64_t n_pts, const double *pts,
+                            int64_t **soff, int32_t **sidx, int64_t *n_entries,
+                            int32_t *max_n, int32_t *min_n, cudaStream_t s, const char *tag);
+
+// shape functions of n_pts points with given supports -> phi [entries*4]
+rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts,
+                            const int64_t *soff, const int32_t *sidx, int32_t max_n,
+                            double *phi, cudaStream_t s, const char *tag);
+
+// node -> entries incidence (stable: ascending entry) of a support list
+rpim_status build_incidence(int64_t n_nodes, int64_t n_entries, const int32_t *sidx,
+                            int64_t **toff, int64_t **tent, int32_t *max_incident,
+                            cudaStream_t s, int sm_count);
+
+int grid_size(int sm_count, int blocks_per_sm_hint, int64_t work, int threads);
+
+// kernel launch bookkeeping: every launch of the library is counted, and
+// when profiling is on (rpim_profile_enable) bracketed by CUDA events on its
+// stream so that per-kernel device times can be read back.
+int64_t launch_begin(const char *name, cudaStream_t s);
+void launch_end(int64_t token, cudaStream_t s);
+
+template <typename... KArgs, typename... Args>
+inline void launch(const char *name, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                   cudaStream_t s, Args... args)
+{
+    const int64_t tok = launch_begin(name, s);
+    kernel<<<grid, block, smem, s>>>(args...);
+    launch_end(tok, s);
+}
+
+// entry -> point map of a support list (one warp per point)
+__global__ void entry_points_kernel(int64_t n_pts, const int64_t *soff, int32_t *entry_pt);
+
+} // namespace rpim

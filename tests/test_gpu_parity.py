@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Tolerances (derived from the arithmetic; see the pins for the floors):
+ * Integration points, supports and the BSR pattern are integer or
+   bit-reproducible results: compared for equality.
+ * Shape functions: the MQ moment problem (alpha_c = 4, q = 1.03) has
+   cond(G) ~ 1e9-1e10, so the plain FP64 evaluation of the definition (the
+   f64 oracle) carries errors e64 of a few 1e-9 and more on clouds with
+   anisotropic spacing. The CUDA path removes the chord of the kernel (exact
+   in exact arithmetic), which cuts that error by two to three orders. It
+   must agree with the extended-precision oracle to
+   max(TOL_PHI_LD, GAIN * e64), e64 measured on the same points, i.e. be at
+   least 1/GAIN = 20 times more accurate than plain FP64 (gradients scaled by
+   h). Against the f64 oracle the difference is bounded by e64 + that bound.
+ * K: entrywise, relative to max|K|, the same rule with TOL_K_LD (the
+   extended oracle assembles the cubes; other cases use sampled rows).
+ * u: relative 2-norm against the solution of the same system by the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+from gpu_util import GpuRun, bsr_matvec, t
+
+import paper_1802_04256_gb300 as R
+
+pytestmark = pytest.mark.gpu
+
+TOL_PHI_LD = 1e-9
+TOL_K_LD = 1e-10
+GAIN = 0.05
+TOL_U = 1e-7
+
+
+def _varied_material():
+    """Jittered cube with E and nu drawn per integration point (exercises the
+    non-uniform-nu assembly path)."""
+    p = gen.cube_config(jitter=0.2, seed=21)
+    p.E = gen.uniform(21, 50, p.n_points, 5e3, 2e4)
+    p.nu = gen.uniform(21, 51, p.n_points, 0.2, 0.4)
+    return p
+
+
+PROBLEMS = {
+    "cube6": lambda: gen.cube_config(),
+    "material": _varied_material,
+    "cube6_jitter": lambda: gen.cube_config(jitter=0.2, seed=7),
+    "beam33": lambda: gen.cantilever_config(shape=(33, 5, 5)),
+    "column": lambda: gen.gravity_column(),
+    "ragged": lambda: gen.cantilever_config(shape=(9, 7, 7), length=1.0, jitter=0.15, seed=9),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(PROBLEMS))
+def case(request):
+    p = PROBLEMS[request.param]()
+    g = GpuRun(p)
+    m = oracle.assemble_problem(p, "f64")
+    return p, g, m
+
+
+def test_integration_points_bitwise(case):
+    p, g, m = case
+    xyz, wj, soff, sidx = g.pat.points()
+    assert np.array_equal(xyz.cpu().numpy(), m.pts)
+    assert np.array_equal(wj.cpu().numpy(), m.wj)
+
+
+def test_supports_identical(case):
+    p, g, m = case
+    xyz, wj, soff, sidx = g.pat.points()
+    assert np.array_equal(soff.cpu().numpy(), m.soff)
+    assert np.array_equal(sidx.cpu().numpy(), m.sidx)
+
+
+def test_pattern_identical(case):
+    p, g, m = case
+    rowptr, cols = g.host_csr()
+    assert np.array_equal(rowptr, m.rowptr)
+    assert np.array_equal(cols, m.cols)
+
+
+def test_shape_functions_vs_oracle(case):
+    p, g, m = case
+    phi = g.pat.shape_functions().cpu().numpy()
+    xyz, wj, soff, sidx = [a.cpu().numpy() for a in g.pat.points()]
+    scale = np.array([1.0, p.h, p.h, p.h])
+    worst_f64 = worst_ld = e64 = 0.0
+    for k in range(0, p.n_points, max(1, p.n_points // 100)):
+        s = sidx[soff[k]:soff[k + 1]]
+        mine = phi[soff[k]:soff[k + 1]].T * scale[:, None]
+        a = oracle.shape(p.xyz, s, xyz[k], p.h, p.alpha_c, p.q, "f64") * scale[:, None]
+        b = oracle.shape(p.xyz, s, xyz[k], p.h, p.alpha_c, p.q, "ld") * scale[:, None]
+        worst_f64 = max(worst_f64, np.abs(mine - a).max())
+        worst_ld = max(worst_ld, np.abs(mine - b).max())
+        e64 = max(e64, np.abs(a - b).max())
+    tol = max(TOL_PHI_LD, GAIN * e64)
+    print("phi: |gpu - ld| %.3e (tol %.1e), |f64 - ld| %.3e, |gpu - f64| %.3e" % (worst_ld, tol, e64, worst_f64))
+    assert worst_ld < tol
+    assert worst_f64 < e64 + tol
+
+
+def test_K_and_f_vs_oracle(case):
+    p, g, m = case
+    K = g.host_K()
+    kmax = np.abs(m.vals).max()
+    d64 = np.abs(K - m.vals).max() / kmax
+    if p.n_nodes <= 250:
+        ml = oracle.assemble_problem(p, "ld")
+        e64 = np.abs(m.vals - ml.vals).max() / kmax
+        dld = np.abs(K - ml.vals).max() / kmax
+        fl = ml.f
+    else:  # rows 0 and n-1 and a middle row from the extended oracle
+        rowptr, cols = g.host_csr()
+        pts, wj = m.pts, m.wj
+        e64 = dld = d64 = 0.0
+        for I in (0, p.n_nodes // 2, p.n_nodes - 1):
+            sel = [k for k in range(len(pts)) if I in m.sidx[m.soff[k]:m.soff[k + 1]]]
+            ml = oracle.assemble(p.xyz, pts[sel], wj[sel], p.E[sel], p.nu[sel], p.alpha_s, p.alpha_c,
+                                 p.q, p.h, kind="ld")
+            sl = slice(rowptr[I], rowptr[I + 1])
+            e64 = max(e64, np.abs(m.vals[sl] - ml.vals[ml.rowptr[I]:ml.rowptr[I + 1]]).max() / kmax)
+            dld = max(dld, np.abs(K[sl] - ml.vals[ml.rowptr[I]:ml.rowptr[I + 1]]).max() / kmax)
+            d64 = max(d64, np.abs(K[sl] - m.vals[sl]).max() / kmax)
+        fl = m.f
+    tol = max(TOL_K_LD, GAIN * e64)
+    print("K: |gpu - ld| %.3e (tol %.1e), |f64 - ld| %.3e, |gpu - f64| %.3e" % (dld, tol, e64, d64))
+    assert dld < tol
+    assert d64 < e64 + tol
+    fd = np.abs(g.f.cpu().numpy() - fl).max() / max(np.abs(fl).max(), 1e-300)
+    print("f: rel %.3e" % fd)
+    assert fd < 1e-8
+
+
+def test_K_exactly_symmetric_and_deterministic(case):
+    p, g, m = case
+    rowptr, cols = g.host_csr()
+    K = g.host_K().reshape(-1, 3, 3)
+    rows = np.repeat(np.arange(p.n_nodes), np.diff(rowptr))
+    # block (J, I) is the transpose of block (I, J), bit for bit
+    key = rows.astype(np.int64) * p.n_nodes + cols
+    tkey = cols.astype(np.int64) * p.n_nodes + rows
+    order = np.argsort(key)
+    pos = order[np.searchsorted(key[order], tkey)]
+    assert np.array_equal(K, np.transpose(K[pos], (0, 2, 1)))
+    K2, f2 = g.pat.assemble(g.E, g.nu, g.body)
+    assert torch.equal(K2, g.K)
+
+
+def test_penalty_matches_oracle_bitwise(case):
+    p, g, m = case
+    rowptr, cols = g.host_csr()
+    K = g.K.clone()
+    f = g.f.clone()
+    a = g.pat.apply_penalty(K, f, t(p.fixed_dofs, torch.int64), t(p.fixed_vals), 1e8)
+    vals = g.host_K().ravel().copy()
+    fh = g.f.cpu().numpy().copy()
+    a2 = oracle.penalty(p.n_nodes, rowptr, cols, vals, fh, p.fixed_dofs, p.fixed_vals, 1e8)
+    assert a == a2
+    assert np.array_equal(K.cpu().numpy().ravel(), vals)
+    assert np.array_equal(f.cpu().numpy(), fh)
+
+
+def test_pcg_solution_vs_oracle(case):
+    p, g, m = case
+    u, it, rr, alpha, K, f = g.solve(rtol=1e-12)
+    assert rr <= 1e-12
+    rowptr, cols = g.host_csr()
+    Kh = K.cpu().numpy().ravel()
+    fh = f.cpu().numpy()
+    uo, ito, rro, st = oracle.pcg(p.n_nodes, rowptr, cols, Kh, fh, rtol=1e-12)
+    assert st == 0
+    uh = u.cpu().numpy()
+    d = np.linalg.norm(uh - uo) / np.linalg.norm(uo)
+    print("u: PCG iterations gpu %d oracle %d, rel diff %.3e" % (it, ito, d))
+    assert d < TOL_U
+    # true residual of the GPU solution, computed on the host: bounded by the
+    # recursive residual plus the rounding floor of f - K u in FP64
+    r = fh - bsr_matvec(rowptr, cols, Kh, uh)
+    floor = 64 * np.finfo(float).eps * np.linalg.norm(bsr_matvec(rowptr, cols, np.abs(Kh), np.abs(uh)))
+    assert np.linalg.norm(r) <= 2e-12 * np.linalg.norm(fh) + floor
+
+
+def test_full_pipeline_u_vs_oracle(case):
+    """u from the GPU pipeline against u from the oracle's own K and f."""
+    p, g, m = case
+    u, it, rr, alpha, K, f = g.solve(rtol=1e-12)
+    mo, uo, ito, rro, ao = oracle.solve_problem(p, "f64", rtol=1e-12)
+    d = np.linalg.norm(u.cpu().numpy() - uo) / np.linalg.norm(uo)
+    print("pipeline u rel diff %.3e" % d)
+    assert d < 1e-5
+
+
+def test_stress_vs_oracle(case):
+    p, g, m = case
+    u, it, rr, alpha, K, f = g.solve(rtol=1e-12)
+    uh = u.cpu().numpy()
+    pts = m.pts[:: max(1, len(m.pts) // 64)]
+    E = np.full(len(pts), p.E[0])
+    nu = np.full(len(pts), p.nu[0])
+    sg = g.pat.stress(u, t(pts), t(E), t(nu)).cpu().numpy()
+    so = oracle.stress(p.xyz, uh, pts, E, nu, p.alpha_s, p.alpha_c, p.q, p.h, "f64")
+    d = np.abs(sg - so).max() / np.abs(so).max()
+    print("stress rel %.3e" % d)
+    assert d < 1e-6
+
+
+def test_point_loads_vs_oracle():
+    p = gen.cantilever_config(shape=(33, 5, 5))
+    pat = R.Pattern.from_problem(p)
+    f = torch.zeros(3 * p.n_nodes, dtype=torch.float64, device="cuda")
+    pat.add_point_loads(t(p.load_xyz), t(p.load_force), f)
+    fo = np.zeros(3 * p.n_nodes)
+    oracle.point_loads(p.xyz, p.load_xyz, p.load_force, p.alpha_s, p.alpha_c, p.q, p.h, fo)
+    assert np.abs(f.cpu().numpy() - fo).max() < 1e-8 * np.abs(fo).max()
+    assert abs(f.cpu().numpy().reshape(-1, 3).sum(0)[2] + 1.0) < 1e-12
