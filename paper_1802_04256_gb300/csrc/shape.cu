@@ -37,13 +37,41 @@
 
 namespace rpim {
 
+// Conversions between double and float by bit manipulation on the integer
+// pipe (the FP64 pipe is the bottleneck of this kernel). Both truncate and
+// flush values outside the single-precision normal range to zero.
+__device__ __forceinline__ float f32_from_f64(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const int e = (int)((hi >> 20) & 0x7FF) - 1023 + 127;
+    if (e <= 0 || e >= 255) return 0.0f;
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
+__device__ __forceinline__ double f64_from_f32(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0;
+    const unsigned hi = (u & 0x80000000u) | ((e - 127 + 1023) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// true for a positive, finite, normal double (integer test)
+__device__ __forceinline__ bool positive_normal(double d)
+{
+    const int hi = __double2hiint(d);
+    return hi > 0x000FFFFF && hi < 0x7FF00000;
+}
+
 // Reciprocal by Newton-Raphson iteration r <- r (2 - d r) from a
 // single-precision seed: the relative error squares at each step
-// (2^-23 -> 2^-46 -> below double rounding), so two steps give a result
-// within an ulp or two of 1/d for |d| inside the single-precision range.
+// (2^-22 -> 2^-44 -> below double rounding), so two steps give a result
+// within an ulp or two of 1/d. d must be a positive double inside the
+// single-precision normal range.
 __device__ __forceinline__ double recip_nr(double d)
 {
-    double r = (double)__frcp_rn((float)d);
+    double r = f64_from_f32(__frcp_rn(f32_from_f64(d)));
     double e = fma(-d, r, 1.0);
     r = fma(r, e, r);
     e = fma(-d, r, 1.0);
@@ -52,7 +80,7 @@ __device__ __forceinline__ double recip_nr(double d)
 
 __device__ __forceinline__ int piece_of(const KernelSeries &ks, double s)
 {
-    const float f = (__log2f((float)s) - ks.log2_lo) * ks.inv_log2r;
+    const float f = (__log2f(f32_from_f64(s)) - ks.log2_lo) * ks.inv_log2r;
     const int k = (int)f;
     return min(max(k, 0), ks.pieces - 1);
 }
@@ -63,11 +91,11 @@ __device__ __forceinline__ double series_A(const KernelSeries &ks, double s)
     const double t = (s - ks.centre[k]) * ks.inv_w[k];
     double v = 0.0;
     if (ks.n64 <= ks.degree) {
-        const float tf = (float)t;
+        const float tf = f32_from_f64(t);
         const float *cf = ks.coef_f[k];
         float h = cf[ks.degree];
         for (int j = ks.degree - 1; j >= ks.n64; j--) h = fmaf(h, tf, cf[j]);
-        v = (double)h;
+        v = f64_from_f32(h);
     }
     const double *c = ks.coef[k];
     for (int j = ks.n64 - 1; j >= 0; j--) v = fma(v, t, c[j]);
@@ -85,41 +113,55 @@ __device__ __forceinline__ void series_A_dA(const KernelSeries &ks, double s, do
     dA = dv;
 }
 
-struct WarpSmem {
+struct PointSmem {
     double *xi;     // [3][NC]
     float *xf;      // [3][NC] single-precision copy for the pivot search
     double *C;      // [4][NC]  C[k][r]
     double *Y;      // [4][NC]  A_rp then Y
     double *v;      // [4][NC]  v[rhs][j] (original order); column buffer later
-    double *invd;   // [NC]     1 / D_kk
-    double *S;      // packed lower triangle, (NC-4)(NC-3)/2
+    double *S;      // packed lower triangle of order NC: S, then 4 rhs rows
     double *M;      // [16] P_p^{-T}, row-major
     double *App;    // [16]
+    double *red;    // [4 * 16] per-warp partial sums of the pivot values
+    float *redv;    // [4 passes][4 warps] argmax values
+    int *redj;      // [4 passes][4 warps] argmax indices
     int *r2o;       // [NC] rest index -> original index
 };
 
-__host__ __device__ inline int64_t warp_smem_doubles(int NC)
+__host__ __device__ inline int64_t point_smem_doubles(int NC)
 {
-    int64_t m = NC - 4;
-    return 3 * NC + (3 * NC + 1) / 2 + 4 * NC + 4 * NC + 4 * NC + NC + m * (m + 1) / 2 + 32 + (NC + 1) / 2 + 2;
+    return 3 * NC + (3 * NC + 1) / 2 + 4 * NC + 4 * NC + 4 * NC + (int64_t)NC * (NC + 1) / 2 + 32 + 64 + 8 + 8 +
+           (NC + 1) / 2 + 2;
 }
 
-__device__ __forceinline__ WarpSmem carve(double *base, int NC)
+__device__ __forceinline__ PointSmem carve(double *base, int NC)
 {
-    WarpSmem w;
-    int64_t m = NC - 4;
+    PointSmem w;
     double *p = base;
     w.xi = p; p += 3 * NC;
     w.xf = (float *)p; p += (3 * NC + 1) / 2;
     w.C = p; p += 4 * NC;
     w.Y = p; p += 4 * NC;
     w.v = p; p += 4 * NC;
-    w.invd = p; p += NC;
-    w.S = p; p += m * (m + 1) / 2;
+    w.S = p; p += (int64_t)NC * (NC + 1) / 2;
     w.M = p; p += 16;
     w.App = p; p += 16;
+    w.red = p; p += 64;
+    w.redv = (float *)p; p += 8;
+    w.redj = (int *)p; p += 8;
     w.r2o = (int *)p;
     return w;
+}
+
+struct ArgMax {
+    float v;
+    int j;
+};
+
+// named barrier over the `count` threads of one point group
+__device__ __forceinline__ void group_sync(int bar, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
 // warp argmax of (value, index): larger value, then smaller index
@@ -149,13 +191,15 @@ __device__ __forceinline__ void tri_decode(int u, int &i, int &j)
     j = u - r * (r + 1) / 2;
 }
 
-template <int R>
-__global__ void __launch_bounds__(256) shape_kernel(int64_t n_pts, const double *__restrict__ pts,
-                                                    const int64_t *__restrict__ soff,
-                                                    const int32_t *__restrict__ sidx,
-                                                    const double *__restrict__ xyz, double inv_h,
-                                                    const KernelSeries *__restrict__ ks_g,
-                                                    double *__restrict__ phi, int NC, DevError *err)
+// One group of G warps per point. Every loop below is a flattened parallel
+// loop over the group's G*32 threads; the phases are separated by a named
+// barrier of the group. Groups of one block are independent.
+__global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double *__restrict__ pts,
+                                                     const int64_t *__restrict__ soff,
+                                                     const int32_t *__restrict__ sidx,
+                                                     const double *__restrict__ xyz, double inv_h,
+                                                     const KernelSeries *__restrict__ ks_g,
+                                                     double *__restrict__ phi, int NC, int G, DevError *err)
 {
     extern __shared__ double dsm[];
     __shared__ KernelSeries ks;
@@ -166,91 +210,110 @@ __global__ void __launch_bounds__(256) shape_kernel(int64_t n_pts, const double 
         for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    WarpSmem W = carve(dsm + (size_t)wid * warp_smem_doubles(NC), NC);
+    const int GT = G * 32;
+    const int grp = threadIdx.x / GT, gt = threadIdx.x - grp * GT;
+    const int lane = threadIdx.x & 31, wig = gt >> 5;
+    const int ppb = blockDim.x / GT;
+    const int bar = 1 + grp;
+    PointSmem W = carve(dsm + (size_t)grp * point_smem_doubles(NC), NC);
     const double c2 = ks.c2;
-    const int64_t stride = (int64_t)gridDim.x * nwarps;
+    const int64_t stride = (int64_t)gridDim.x * ppb;
 
-    for (int64_t p = (int64_t)blockIdx.x * nwarps + wid; p < n_pts; p += stride) {
+    for (int64_t p = (int64_t)blockIdx.x * ppb + grp; p < n_pts; p += stride) {
         const int64_t base = soff[p];
         const int n = (int)(soff[p + 1] - base);
         if (n < 4 || n > NC) {
-            if (lane == 0) dev_fail(err, RPIM_E_SUPPORT, p);
+            if (gt == 0) dev_fail(err, RPIM_E_SUPPORT, p);
             continue;
         }
         const int m = n - 4;
         const double gx = pts[3 * p], gy = pts[3 * p + 1], gz = pts[3 * p + 2];
 
         // 1. local coordinates (FP64) and a single-precision copy
-        for (int j = lane; j < n; j += 32) {
+        for (int j = gt; j < n; j += GT) {
             const int64_t J = sidx[base + j];
             const double a = (xyz[3 * J] - gx) * inv_h, b = (xyz[3 * J + 1] - gy) * inv_h,
                          c = (xyz[3 * J + 2] - gz) * inv_h;
             W.xi[j] = a;
             W.xi[NC + j] = b;
             W.xi[2 * NC + j] = c;
-            W.xf[j] = (float)a;
-            W.xf[NC + j] = (float)b;
-            W.xf[2 * NC + j] = (float)c;
+            W.xf[j] = f32_from_f64(a);
+            W.xf[NC + j] = f32_from_f64(b);
+            W.xf[2 * NC + j] = f32_from_f64(c);
         }
-        __syncwarp();
+        group_sync(bar, GT);
 
-        // 2. greedy pivot tetrahedron (single precision is enough to choose)
+        // 2. greedy pivot tetrahedron (single precision is enough to choose);
+        //    each pass: warp argmax, then the group combines the G warps in
+        //    order
         const float *X = W.xf, *Yc = W.xf + NC, *Z = W.xf + 2 * NC;
+        auto group_argmax = [&](float bv, int bj, int pass) {
+            warp_argmax(bv, bj);
+            if (lane == 0) {
+                W.redv[4 * pass + wig] = bv;
+                W.redj[4 * pass + wig] = bj;
+            }
+            group_sync(bar, GT);
+            float v = W.redv[4 * pass];
+            int j = W.redj[4 * pass];
+            for (int w = 1; w < G; w++) {
+                const float ov = W.redv[4 * pass + w];
+                const int oj = W.redj[4 * pass + w];
+                if (ov > v || (ov == v && oj < j)) { v = ov; j = oj; }
+            }
+            return ArgMax{v, j};
+        };
         int p0, p1, p2, p3;
         {
             float bv = -INFINITY;
             int bj = 0x7fffffff;
-            for (int j = lane; j < n; j += 32)
+            for (int j = gt; j < n; j += GT)
                 if (-X[j] > bv) { bv = -X[j]; bj = j; }
-            warp_argmax(bv, bj);
-            p0 = bj;
+            p0 = group_argmax(bv, bj, 0).j;
         }
         const float ax = X[p0], ay = Yc[p0], az = Z[p0];
         {
             float bv = -1.0f;
             int bj = 0x7fffffff;
-            for (int j = lane; j < n; j += 32) {
+            for (int j = gt; j < n; j += GT) {
                 float dx = X[j] - ax, dy = Yc[j] - ay, dz = Z[j] - az;
                 float d = dx * dx + dy * dy + dz * dz;
                 if (d > bv) { bv = d; bj = j; }
             }
-            warp_argmax(bv, bj);
-            p1 = bj;
+            p1 = group_argmax(bv, bj, 1).j;
         }
         const float ux = X[p1] - ax, uy = Yc[p1] - ay, uz = Z[p1] - az;
         {
             float bv = -1.0f;
             int bj = 0x7fffffff;
-            for (int j = lane; j < n; j += 32) {
+            for (int j = gt; j < n; j += GT) {
                 float dx = X[j] - ax, dy = Yc[j] - ay, dz = Z[j] - az;
                 float cx = dy * uz - dz * uy, cy = dz * ux - dx * uz, cz = dx * uy - dy * ux;
                 float d = cx * cx + cy * cy + cz * cz;
                 if (d > bv) { bv = d; bj = j; }
             }
-            warp_argmax(bv, bj);
-            p2 = bj;
+            p2 = group_argmax(bv, bj, 2).j;
         }
         {
             const float vx = X[p2] - ax, vy = Yc[p2] - ay, vz = Z[p2] - az;
             const float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
             float bv = -1.0f;
             int bj = 0x7fffffff;
-            for (int j = lane; j < n; j += 32) {
+            for (int j = gt; j < n; j += GT) {
                 float d = fabsf((X[j] - ax) * nx + (Yc[j] - ay) * ny + (Z[j] - az) * nz);
                 if (d > bv) { bv = d; bj = j; }
             }
-            warp_argmax(bv, bj);
-            p3 = bj;
+            auto r = group_argmax(bv, bj, 3);
+            p3 = r.j;
             const float ulen2 = ux * ux + uy * uy + uz * uz;
-            if (!(bv > 1e-5f * ulen2 * sqrtf(ulen2))) {
-                if (lane == 0) dev_fail(err, RPIM_E_SINGULAR, p);
+            if (!(r.v > 1e-5f * ulen2 * sqrtf(ulen2))) {
+                if (gt == 0) dev_fail(err, RPIM_E_SINGULAR, p);
+                group_sync(bar, GT);
                 continue;
             }
         }
         // rest ordering: original order without the pivots
-        for (int j = lane; j < n; j += 32) {
+        for (int j = gt; j < n; j += GT) {
             int less = (p0 < j) + (p1 < j) + (p2 < j) + (p3 < j);
             bool isp = j == p0 || j == p1 || j == p2 || j == p3;
             if (!isp) W.r2o[j - less] = j;
@@ -258,7 +321,8 @@ __global__ void __launch_bounds__(256) shape_kernel(int64_t n_pts, const double 
         auto pivot = [&](int k) { return k == 0 ? p0 : k == 1 ? p1 : k == 2 ? p2 : p3; };
 
         // 3. M = P_p^{-T} = cofactor matrix / det, one cofactor per lane 0..15
-        {
+        //    of the group's first warp
+        if (wig == 0) {
             const int ri = (lane >> 2) & 3, cj = lane & 3;
             double e[3][3];
             int rr = 0;
@@ -273,9 +337,7 @@ __global__ void __launch_bounds__(256) shape_kernel(int64_t n_pts, const double 
             }
             double cof = det3(e[0][0], e[0][1], e[0][2], e[1][0], e[1][1], e[1][2], e[2][0], e[2][1], e[2][2]);
             if ((ri + cj) & 1) cof = -cof;
-            // det = sum_j P_p[0][j] cof(0, j) from lanes 0..3
-            const int p0r = p0;
-            const double prow = cj == 0 ? 1.0 : W.xi[(cj - 1) * NC + p0r];
+            const double prow = cj == 0 ? 1.0 : W.xi[(cj - 1) * NC + p0];
             double part = lane < 4 ? prow * cof : 0.0;
             part += __shfl_xor_sync(0xffffffffu, part, 1);
             part += __shfl_xor_sync(0xffffffffu, part, 2);
@@ -283,34 +345,32 @@ __global__ void __launch_bounds__(256) shape_kernel(int64_t n_pts, const double 
             const double idet = recip_nr(det);
             if (lane < 16) W.M[lane] = cof * idet;
         }
-        __syncwarp();
+        group_sync(bar, GT);
 
-        // 4. A_pp (lanes 0..15), C and A_rp (lanes over rest rows)
-        if (lane < 16) {
-            const int a = lane >> 2, b = lane & 3;
+        // 4. A_pp, C and A_rp
+        if (gt < 16) {
+            const int a = gt >> 2, b = gt & 3;
             const int ia = pivot(a), ib = pivot(b);
             double val = ks.diag;
             if (a != b) {
                 double dx = W.xi[ia] - W.xi[ib], dy = W.xi[NC + ia] - W.xi[NC + ib], dz = W.xi[2 * NC + ia] - W.xi[2 * NC + ib];
                 val = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
             }
-            W.App[lane] = val;
+            W.App[gt] = val;
         }
-        for (int r = lane; r < m; r += 32) {
+        for (int t = gt; t < 4 * m; t += GT) {
+            const int r = t >> 2, k = t & 3;
             const int j = W.r2o[r];
             const double x0 = W.xi[j], x1 = W.xi[NC + j], x2 = W.xi[2 * NC + j];
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                W.C[k * NC + r] = fma(W.M[4 * k + 3], x2, fma(W.M[4 * k + 2], x1, fma(W.M[4 * k + 1], x0, W.M[4 * k])));
-                const int ik = pivot(k);
-                double dx = x0 - W.xi[ik], dy = x1 - W.xi[NC + ik], dz = x2 - W.xi[2 * NC + ik];
-                W.Y[k * NC + r] = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
-            }
+            W.C[k * NC + r] = fma(W.M[4 * k + 3], x2, fma(W.M[4 * k + 2], x1, fma(W.M[4 * k + 1], x0, W.M[4 * k])));
+            const int ik = pivot(k);
+            double dx = x0 - W.xi[ik], dy = x1 - W.xi[NC + ik], dz = x2 - W.xi[2 * NC + ik];
+            W.Y[k * NC + r] = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
         }
-        __syncwarp();
+        group_sync(bar, GT);
 
         // 5. right-hand sides v = r - A_:p d  (d = columns of M), all nodes
-        for (int j = lane; j < n; j += 32) {
+        for (int j = gt; j < n; j += GT) {
             const double x0 = W.xi[j], x1 = W.xi[NC + j], x2 = W.xi[2 * NC + j];
             double Aj, dAj;
             series_A_dA(ks, fma(x2, x2, fma(x1, x1, fma(x0, x0, c2))), Aj, dAj);
@@ -337,28 +397,26 @@ __global__ void __launch_bounds__(256) shape_kernel(int64_t n_pts, const double 
                 W.v[q * NC + j] = acc;
             }
         }
-        __syncwarp();
+        group_sync(bar, GT);
         // Y = A_rp - C' A_pp / 2
-        for (int r = lane; r < m; r += 32) {
-            double y[4];
+        for (int t = gt; t < 4 * m; t += GT) {
+            const int r = t >> 2, k = t & 3;
+            double acc = 0.0;
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                double acc = 0.0;
-#pragma unroll
-                for (int t = 0; t < 4; t++) acc = fma(W.C[t * NC + r], W.App[4 * t + k], acc);
-                y[k] = fma(-0.5, acc, W.Y[k * NC + r]);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; k++) W.Y[k * NC + r] = y[k];
+            for (int s2 = 0; s2 < 4; s2++) acc = fma(W.C[s2 * NC + r], W.App[4 * s2 + k], acc);
+            W.Y[k * NC + r] = fma(-0.5, acc, W.Y[k * NC + r]);  // each thread owns its element
         }
-        __syncwarp();
+        group_sync(bar, GT);
 
-        // 6. S = A_rr - Y C - C' Y' (packed lower triangle)
+        // 6. S = A_rr - Y C - C' Y' (packed lower triangle, rows 0..m-1),
+        //    then the reduced right-hand sides as rows m..m+3 (entries
+        //    j < m), so that the elimination below also performs the
+        //    forward substitution
         {
             const int T = m * (m + 1) / 2;
-            int i, j;
-            tri_decode(lane, i, j);
-            for (int u = lane; u < T; u += 32) {
+            for (int u = gt; u < T; u += GT) {
+                int i, j;
+                tri_decode(u, i, j);
                 const int oi = W.r2o[i], oj = W.r2o[j];
                 double a;
                 if (i == j) {
@@ -373,137 +431,85 @@ __global__ void __launch_bounds__(256) shape_kernel(int64_t n_pts, const double 
                     a = fma(-W.C[k * NC + i], W.Y[k * NC + j], a);
                 }
                 W.S[u] = a;
-                j += 32;
-                while (j > i) { j -= i + 1; i++; }
             }
         }
-        // reduced right-hand sides into lane-owned rows
-        double b[R][4];
-#pragma unroll
-        for (int s = 0; s < R; s++) {
-            const int r = lane + 32 * s;
-#pragma unroll
-            for (int q = 0; q < 4; q++) b[s][q] = 0.0;
+        for (int t = gt; t < 4 * (m + 4); t += GT) {
+            const int q = t / (m + 4), r = t - q * (m + 4);
+            double acc = 0.0;
             if (r < m) {
                 const int j = W.r2o[r];
+                acc = W.v[q * NC + j];
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    double acc = W.v[q * NC + j];
-#pragma unroll
-                    for (int k = 0; k < 4; k++) acc = fma(-W.C[k * NC + r], W.v[q * NC + pivot(k)], acc);
-                    b[s][q] = acc;
-                }
+                for (int k = 0; k < 4; k++) acc = fma(-W.C[k * NC + r], W.v[q * NC + pivot(k)], acc);
             }
+            if (r <= m + q) W.S[(m + q) * (m + q + 1) / 2 + r] = acc;
         }
-        __syncwarp();
+        group_sync(bar, GT);
 
-        // 7. S = L D L' (right-looking, packed, in place; W.v holds the
-        //    unscaled column of the current step)
+        // 7. S = L D L' (right-looking, packed, in place) on the order-(m+4)
+        //    triangle; W.v holds the unscaled column of the current step.
+        //    After step m-1 the rhs rows hold z = D^-1 L^-1 rhs.
+        const int M2 = m + 4;
         double *col = W.v;
         bool ok = true;
         for (int k = 0; k < m; k++) {
             const int kb = k * (k + 1) / 2;
             const double dkk = W.S[kb + k];
-            if (!(dkk > 0.0)) { ok = false; break; }
+            if (!positive_normal(dkk)) { ok = false; break; }
             const double iv = recip_nr(dkk);
-            if (lane == 0) W.invd[k] = iv;
-            for (int i = k + 1 + lane; i < m; i += 32) {
+            for (int i = k + 1 + gt; i < M2; i += GT) {
                 const int ik = i * (i + 1) / 2 + k;
                 const double a = W.S[ik];
                 col[i] = a;
                 W.S[ik] = a * iv;
             }
-            __syncwarp();
-            const int tk = m - k - 1;
+            group_sync(bar, GT);
+            const int tk = M2 - k - 1;
             const int T = tk * (tk + 1) / 2;
-            if (T > 0) {
+            for (int u = gt; u < T; u += GT) {
                 int ri, rj;
-                tri_decode(lane, ri, rj);
-                int i = k + 1 + ri, j = k + 1 + rj;
-                for (int u = lane; u < T; u += 32) {
-                    const int ib = i * (i + 1) / 2;
-                    W.S[ib + j] = fma(-W.S[ib + k], col[j], W.S[ib + j]);
-                    j += 32;
-                    while (j > i) { j -= i - k; i++; }
-                }
+                tri_decode(u, ri, rj);
+                const int i = k + 1 + ri, j = k + 1 + rj;
+                const int ib = i * (i + 1) / 2;
+                W.S[ib + j] = fma(-W.S[ib + k], col[j], W.S[ib + j]);
             }
-            __syncwarp();
+            group_sync(bar, GT);
         }
         if (!ok) {
-            if (lane == 0) dev_fail(err, RPIM_E_SINGULAR, p);
-            __syncwarp();
+            if (gt == 0) dev_fail(err, RPIM_E_SINGULAR, p);
+            group_sync(bar, GT);
             continue;
         }
 
-        // 8. L y = b (unit diagonal), y /= D, L' a = y (lane-owned rows)
-        for (int k = 0; k < m - 1; k++) {
-            const int owner = k & 31, slot = k >> 5;
-            double y[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                double mine = 0.0;
-#pragma unroll
-                for (int s = 0; s < R; s++)
-                    if (s == slot) mine = b[s][q];
-                y[q] = __shfl_sync(0xffffffffu, mine, owner);
-            }
-#pragma unroll
-            for (int s = 0; s < R; s++) {
-                const int i = lane + 32 * s;
-                if (i > k && i < m) {
-                    const double l = W.S[i * (i + 1) / 2 + k];
-#pragma unroll
-                    for (int q = 0; q < 4; q++) b[s][q] = fma(-l, y[q], b[s][q]);
-                }
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < R; s++) {
-            const int i = lane + 32 * s;
-            if (i < m) {
-                const double iv = W.invd[i];
-#pragma unroll
-                for (int q = 0; q < 4; q++) b[s][q] *= iv;
-            }
-        }
+        // 8. L' a = z, column by column; threads over (row, rhs) pairs
+        double *Z0 = W.S + (size_t)m * (m + 1) / 2;  // rhs row q starts at Z0 + q*m + q*(q+1)/2
         for (int k = m - 1; k > 0; k--) {
-            const int owner = k & 31, slot = k >> 5;
-            double a[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                double mine = 0.0;
-#pragma unroll
-                for (int s = 0; s < R; s++)
-                    if (s == slot) mine = b[s][q];
-                a[q] = __shfl_sync(0xffffffffu, mine, owner);
-            }
             const int kb = k * (k + 1) / 2;
-#pragma unroll
-            for (int s = 0; s < R; s++) {
-                const int i = lane + 32 * s;
-                if (i < k) {
-                    const double l = W.S[kb + i];
-#pragma unroll
-                    for (int q = 0; q < 4; q++) b[s][q] = fma(-l, a[q], b[s][q]);
-                }
+            for (int t = gt; t < 4 * k; t += GT) {
+                const int q = t & 3, i = t >> 2;
+                double *zq = Z0 + q * m + q * (q + 1) / 2;
+                zq[i] = fma(-W.S[kb + i], zq[k], zq[i]);
             }
+            group_sync(bar, GT);
         }
 
         // 9. pivot values a_p = d - C a_r: 16 sums over the rest rows,
-        //    reduce-scattered so that lane l ends with sum number l >> 1
+        //    reduce-scattered inside each warp (lane l ends with sum l >> 1),
+        //    then summed over the group's warps in order
         double v[16];
 #pragma unroll
-        for (int k = 0; k < 4; k++)
+        for (int k = 0; k < 16; k++) v[k] = 0.0;
+        for (int r = gt; r < m; r += GT) {
+            double ar[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                double acc = 0.0;
+            for (int q = 0; q < 4; q++) ar[q] = Z0[q * m + q * (q + 1) / 2 + r];
 #pragma unroll
-                for (int s = 0; s < R; s++) {
-                    const int r = lane + 32 * s;
-                    if (r < m) acc = fma(W.C[k * NC + r], b[s][q], acc);
-                }
-                v[4 * k + q] = acc;
+            for (int k = 0; k < 4; k++) {
+                const double c = W.C[k * NC + r];
+#pragma unroll
+                for (int q = 0; q < 4; q++) v[4 * k + q] = fma(c, ar[q], v[4 * k + q]);
             }
+        }
 #pragma unroll
         for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
             const bool up = (lane & bit) != 0;
@@ -515,52 +521,31 @@ __global__ void __launch_bounds__(256) shape_kernel(int64_t n_pts, const double 
             }
         }
         v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+        if ((lane & 1) == 0) W.red[16 * wig + (lane >> 1)] = v[0];
 
         double *out = phi + 4 * base;
         bool finite = true;
-#pragma unroll
-        for (int s = 0; s < R; s++) {
-            const int r = lane + 32 * s;
-            if (r < m) {
-                const int j = W.r2o[r];
-                double2 lo2 = make_double2(b[s][0], b[s][1] * inv_h);
-                double2 hi2 = make_double2(b[s][2] * inv_h, b[s][3] * inv_h);
-                finite &= isfinite(lo2.x) && isfinite(lo2.y) && isfinite(hi2.x) && isfinite(hi2.y);
-                *(double2 *)(out + 4 * j) = lo2;
-                *(double2 *)(out + 4 * j + 2) = hi2;
-            }
+        for (int r = gt; r < m; r += GT) {
+            const int j = W.r2o[r];
+            double2 lo2 = make_double2(Z0[r], Z0[m + 1 + r] * inv_h);
+            double2 hi2 = make_double2(Z0[2 * m + 3 + r] * inv_h, Z0[3 * m + 6 + r] * inv_h);
+            finite &= isfinite(lo2.x) && isfinite(lo2.y) && isfinite(hi2.x) && isfinite(hi2.y);
+            *(double2 *)(out + 4 * j) = lo2;
+            *(double2 *)(out + 4 * j + 2) = hi2;
         }
-        if ((lane & 1) == 0) {
-            const int idx = lane >> 1, k = idx >> 2, q = idx & 3;
-            double val = W.M[4 * k + q] - v[0];
+        group_sync(bar, GT);
+        if (gt < 16) {
+            double sum = W.red[gt];
+            for (int w = 1; w < G; w++) sum += W.red[16 * w + gt];
+            const int k = gt >> 2, q = gt & 3;
+            double val = W.M[4 * k + q] - sum;
             if (q) val *= inv_h;
             finite &= isfinite(val);
             out[4 * pivot(k) + q] = val;
         }
         if (!__all_sync(0xffffffffu, finite) && lane == 0) dev_fail(err, RPIM_E_NONFINITE, p);
-        __syncwarp();
+        group_sync(bar, GT);
     }
-}
-
-template <int R>
-static rpim_status launch_shape(rpim_pattern *p, int64_t n_pts, const double *pts, const int64_t *soff,
-                                const int32_t *sidx, int NC, double *phi, cudaStream_t s, const char *tag)
-{
-    const size_t per = (size_t)warp_smem_doubles(NC) * sizeof(double);
-    const size_t budget = 216 * 1024;
-    int wpb = (int)std::min<size_t>(8, budget / per);
-    if (wpb < 1) return fail(RPIM_E_SUPPORT, "support too large for shared memory");
-    const size_t smem = (size_t)wpb * per;
-    RPIM_CUDA(cudaFuncSetAttribute(shape_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int bps = 0;
-    RPIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, shape_kernel<R>, wpb * 32, smem));
-    if (bps < 1) bps = 1;
-    int64_t blocks = std::min<int64_t>((int64_t)p->sm_count * bps, (n_pts + wpb - 1) / wpb);
-    if (blocks < 1) blocks = 1;
-    launch(tag, shape_kernel<R>, (unsigned)blocks, wpb * 32, smem, s, n_pts, pts, soff, sidx, p->xyz, p->inv_h,
-                                                              p->series, phi, NC, p->err);
-    RPIM_CUDA(cudaGetLastError());
-    return RPIM_OK;
 }
 
 rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, const int64_t *soff,
@@ -569,11 +554,19 @@ rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, c
     if (n_pts == 0) return RPIM_OK;
     if (max_n > RPIM_MAX_SUPPORT) return fail(RPIM_E_SUPPORT, "support larger than RPIM_MAX_SUPPORT");
     const int NC = std::max(8, (int)max_n);
-    const int m = NC - 4;
-    if (m <= 32) return launch_shape<1>(p, n_pts, pts, soff, sidx, NC, phi, s, tag);
-    if (m <= 64) return launch_shape<2>(p, n_pts, pts, soff, sidx, NC, phi, s, tag);
-    if (m <= 128) return launch_shape<4>(p, n_pts, pts, soff, sidx, NC, phi, s, tag);
-    return launch_shape<7>(p, n_pts, pts, soff, sidx, NC, phi, s, tag);
+    const size_t per = (size_t)point_smem_doubles(NC) * sizeof(double);
+    const size_t budget = 216 * 1024;
+    int ppb = (int)std::min<size_t>(15, budget / per);  // points (groups) per block
+    if (ppb < 1) return fail(RPIM_E_SUPPORT, "support too large for shared memory");
+    const int G = std::max(1, std::min(4, 32 / ppb));  // warps per point, <= 1024 threads per block
+    const size_t smem = (size_t)ppb * per;
+    RPIM_CUDA(cudaFuncSetAttribute(shape_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t blocks = std::min<int64_t>((int64_t)p->sm_count, (n_pts + ppb - 1) / ppb);
+    if (blocks < 1) blocks = 1;
+    launch(tag, shape_kernel, (unsigned)blocks, ppb * G * 32, smem, s, n_pts, pts, soff, sidx,
+           (const double *)p->xyz, p->inv_h, (const KernelSeries *)p->series, phi, NC, G, p->err);
+    RPIM_CUDA(cudaGetLastError());
+    return RPIM_OK;
 }
 
 } // namespace rpim
