@@ -207,6 +207,31 @@ rpim_status rpim_stress(rpim_pattern *pattern, const double *u, int64_t n_pts,
                         const double *xyz, const double *E, const double *nu, double *sigma,
                         rpim_stream_t stream);
 
+/*
+ * rpim_stress without any device allocation, for callers that cannot allocate
+ * device memory while they run: hosts that fix and account their device-memory
+ * budget at start-up, or loops that keep other streams busy and cannot accept
+ * the device synchronisation that cudaMalloc/cudaFree may imply. (The paper
+ * has no counterpart; this is a deployment variant of rpim_stress.)
+ * Same arguments and results as rpim_stress. The per-call scratch (support
+ * lists and shape functions of the points) lives in one fixed array of
+ * device memory owned by the library: 9.45 MB on every GPU that loads
+ * the library, held until the process exits.
+ *   Limits: at most RPIM_NOALLOC_MAX_POINTS points per call and at most
+ *   RPIM_NOALLOC_MAX_ENTRIES support entries in total (sum of the points'
+ *   support sizes); larger calls return RPIM_E_ARG and compute nothing.
+ *   The first call on each device looks up the array's device address (no
+ *   allocation); make that first call before any stream capture.
+ *   Every call uses the same array: calls that may overlap on the GPU (other
+ *   streams, other host threads) race and must be serialised by the caller.
+ * Synchronises `stream`.
+ */
+#define RPIM_NOALLOC_MAX_POINTS 2048
+#define RPIM_NOALLOC_MAX_ENTRIES 262144
+rpim_status rpim_stress_noalloc(rpim_pattern *pattern, const double *u, int64_t n_pts,
+                                const double *xyz, const double *E, const double *nu,
+                                double *sigma, rpim_stream_t stream);
+
 /* Thread-local description of the last error returned on this thread. */
 const char *rpim_last_error(void);
 

@@ -26,7 +26,7 @@ EXPORTED = [
     "rpim_build_pattern", "rpim_pattern_free", "rpim_pattern_get_info", "rpim_pattern_csr",
     "rpim_pattern_points", "rpim_pattern_copy_csr", "rpim_pattern_copy_points", "rpim_assemble",
     "rpim_shape_functions", "rpim_add_point_loads", "rpim_apply_penalty_bc", "rpim_solve_pcg",
-    "rpim_stress", "rpim_last_error", "rpim_version", "rpim_probe_dfma", "rpim_probe_dmma",
+    "rpim_stress", "rpim_stress_noalloc", "rpim_last_error", "rpim_version", "rpim_probe_dfma", "rpim_probe_dmma",
     "rpim_kernel_launches", "rpim_profile_enable", "rpim_profile_read", "rpim_kernel_series_info",
 ]
 
@@ -80,6 +80,7 @@ def lib():
         "rpim_apply_penalty_bc": [vp, vp, vp, i64, vp, vp, dbl, C.POINTER(dbl), vp],
         "rpim_solve_pcg": [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp],
         "rpim_stress": [vp, vp, i64, vp, vp, vp, vp, vp],
+        "rpim_stress_noalloc": [vp, vp, i64, vp, vp, vp, vp, vp],
         "rpim_probe_dfma": [i32, C.POINTER(dbl)],
         "rpim_probe_dmma": [i32, C.POINTER(dbl)],
         "rpim_profile_enable": [i32],
@@ -238,6 +239,14 @@ def rpim_profile_read(reset: bool = True) -> dict:
     buf = C.create_string_buffer(1 << 16)
     _check(lib().rpim_profile_read(buf, len(buf), 1 if reset else 0), "rpim_profile_read")
     return {k: (v[0], v[1]) for k, v in json.loads(buf.value.decode()).items()}
+
+
+def rpim_stress_noalloc(handle, u, xyz, E, nu, sigma, stream=None):
+    """rpim_stress with its scratch in the library's fixed device array
+    (no allocation; at most 2048 points per call; calls must not overlap)."""
+    _check(lib().rpim_stress_noalloc(handle, _dev(u, torch.float64), xyz.shape[0], _dev(xyz, torch.float64),
+                                     _dev(E, torch.float64), _dev(nu, torch.float64),
+                                     _dev(sigma, torch.float64), _stream(stream)), "rpim_stress_noalloc")
 
 
 def rpim_version() -> str:

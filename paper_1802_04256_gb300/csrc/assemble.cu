@@ -282,6 +282,16 @@ __global__ void stress_kernel(int64_t n_pts, const int64_t *soff, const int32_t 
     }
 }
 
+// stress kernel on given supports and shape functions (no allocation)
+rpim_status launch_stress(rpim_pattern *p, int64_t n_pts, const int64_t *soff, const int32_t *sidx, const double *phi,
+                          const double *u, const double *E, const double *nu, double *sigma, cudaStream_t s)
+{
+    launch("stress", stress_kernel, grid_size(p->sm_count, 8, n_pts * 32, 256), 256, 0, s, n_pts, soff, sidx, phi, u,
+           E, nu, sigma, p->err);
+    RPIM_CUDA(cudaGetLastError());
+    return RPIM_OK;
+}
+
 static rpim_status ensure_phi(rpim_pattern *p, cudaStream_t s)
 {
     if (!p->phi) RPIM_CHECK(dalloc(&p->phi, 4 * p->n_entries, s));

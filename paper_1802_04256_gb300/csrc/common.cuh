@@ -169,6 +169,15 @@ rpim_status search_supports(rpim_pattern *p, int64_t n_pts, const double *pts,
                             int64_t **soff, int32_t **sidx, int64_t *n_entries,
                             int32_t *max_n, int32_t *min_n, cudaStream_t s, const char *tag);
 
+// support search into caller-provided buffers (no allocation)
+rpim_status search_supports_into(rpim_pattern *p, int64_t n_pts, const double *pts, int64_t *soff, int64_t *tmp,
+                                 int *minmax, int32_t *sidx, int64_t cap, int64_t *n_entries, int32_t *max_n,
+                                 cudaStream_t s, const char *tag);
+
+// stress kernel on given supports and shape functions (no allocation)
+rpim_status launch_stress(rpim_pattern *p, int64_t n_pts, const int64_t *soff, const int32_t *sidx, const double *phi,
+                          const double *u, const double *E, const double *nu, double *sigma, cudaStream_t s);
+
 // shape functions of n_pts points with given supports -> phi [entries*4]
 rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts,
                             const int64_t *soff, const int32_t *sidx, int32_t max_n,

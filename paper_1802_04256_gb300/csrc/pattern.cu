@@ -287,6 +287,45 @@ rpim_status search_supports(rpim_pattern *p, int64_t n_pts, const double *pts, i
     return RPIM_OK;
 }
 
+// Support search into caller-provided device buffers (no allocation):
+// soff [n_pts+1], tmp [scan_tmp_size(n_pts)], minmax [2], sidx [cap].
+// Returns RPIM_E_ARG when the supports need more than `cap` entries.
+// Synchronises s (the entry count comes back to the host).
+rpim_status search_supports_into(rpim_pattern *p, int64_t n_pts, const double *pts, int64_t *soff, int64_t *tmp,
+                                 int *minmax, int32_t *sidx, int64_t cap, int64_t *n_entries, int32_t *max_n,
+                                 cudaStream_t s, const char *tag)
+{
+    const int init[2] = {1 << 30, 0};
+    RPIM_CUDA(cudaMemcpyAsync(minmax, init, sizeof init, cudaMemcpyHostToDevice, s));
+    const int grid = grid_size(p->sm_count, 8, n_pts * 32, 256);
+    launch(tag, search_kernel<0>, grid, 256, 0, s, n_pts, pts, p->grid, p->cell_start,
+           (const double4 *)p->sorted_xyz, p->sorted_ids, p->rs2, soff, (int32_t *)nullptr, minmax, p->err);
+    RPIM_CUDA(cudaGetLastError());
+    RPIM_CHECK(exclusive_scan(soff, n_pts, tmp, s));
+    int hm[2];
+    int64_t ne = 0;
+    RPIM_CUDA(cudaMemcpyAsync(hm, minmax, sizeof hm, cudaMemcpyDeviceToHost, s));
+    RPIM_CUDA(cudaMemcpyAsync(&ne, soff + n_pts, sizeof ne, cudaMemcpyDeviceToHost, s));
+    RPIM_CUDA(cudaStreamSynchronize(s));
+    if (hm[0] < 4 || hm[1] > RPIM_MAX_SUPPORT) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "support sizes %d..%d outside [4, %d]", hm[0], hm[1], RPIM_MAX_SUPPORT);
+        return fail(RPIM_E_SUPPORT, buf);
+    }
+    if (ne > cap) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "%lld support entries exceed the fixed scratch capacity of %lld", (long long)ne,
+                 (long long)cap);
+        return fail(RPIM_E_ARG, buf);
+    }
+    launch(tag, search_kernel<1>, grid, 256, 0, s, n_pts, pts, p->grid, p->cell_start,
+           (const double4 *)p->sorted_xyz, p->sorted_ids, p->rs2, soff, sidx, (int *)nullptr, p->err);
+    RPIM_CUDA(cudaGetLastError());
+    *n_entries = ne;
+    *max_n = hm[1];
+    return RPIM_OK;
+}
+
 __global__ void entry_points_kernel(int64_t n_pts, const int64_t *soff, int32_t *entry_pt)
 {
     const int lane = threadIdx.x & 31;
