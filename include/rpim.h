@@ -187,6 +187,17 @@ rpim_status rpim_apply_penalty_bc(rpim_pattern *pattern, double *K_vals, double 
                                   double *alpha_out, rpim_stream_t stream);
 
 /*
+ * Stage 2 with a given penalty: as rpim_apply_penalty_bc, but alpha is the
+ * caller's value (for instance the one a previous call returned), so that K
+ * depends on the material only through the stiffness: the frozen penalty of
+ * a back-analysis. K_dd += alpha, f_d += alpha * values[i]. Synchronises.
+ * Errors: RPIM_E_ARG (negative alpha, DOF out of range or repeated).
+ */
+rpim_status rpim_apply_penalty_alpha(rpim_pattern *pattern, double *K_vals, double *f, int64_t m,
+                                     const int64_t *dofs, const double *values, double alpha,
+                                     rpim_stream_t stream);
+
+/*
  * Stage 3 (Sec. 2): solve K u = f by Jacobi-preconditioned conjugate
  * gradients in FP64 with deterministic reductions. u holds the initial guess
  * on entry. Stops when ||r||_2 <= rtol ||f||_2 or after max_iter iterations.
@@ -196,6 +207,24 @@ rpim_status rpim_apply_penalty_bc(rpim_pattern *pattern, double *K_vals, double 
 rpim_status rpim_solve_pcg(rpim_pattern *pattern, const double *K_vals, const double *f,
                            double *u, double rtol, int32_t max_iter, int32_t *iters,
                            double *relres, rpim_stream_t stream);
+
+/*
+ * Material gradient of a solved system, per integration point (the
+ * back-analysis of the paper's geomechanics use, Sec. 1 and 4: the package
+ * exists to model rock and soil masses whose properties are uncertain).
+ * With K(E, nu) u = f, the penalty frozen, and the adjoint K lam = dL/du
+ * (solve it with rpim_solve_pcg; K is symmetric),
+ *   dE[g]  = dL/dE_g  = - w_g eps_g(lam)^T (dD/dE)  eps_g(u),
+ *   dnu[g] = dL/dnu_g = - w_g eps_g(lam)^T (dD/dnu) eps_g(u),
+ * eps_g(v) = sum_I B_I(x_g) v_I, D isotropic (Voigt, engineering shear).
+ * Uses the shape functions of the last rpim_assemble of this pattern (they
+ * do not depend on the material); computes them if none exist.
+ *   u, lam [3*n_nodes]; E, nu [n_points]; dE, dnu [n_points] outputs.
+ * Synchronises. Errors: RPIM_E_ARG (material out of range).
+ */
+rpim_status rpim_grad_material(rpim_pattern *pattern, const double *u, const double *lam,
+                               const double *E, const double *nu, double *dE, double *dnu,
+                               rpim_stream_t stream);
 
 /*
  * Stresses at arbitrary points: sigma_p = D(E_p, nu_p) sum_I B_I(x_p) u_I,

@@ -84,6 +84,8 @@ def lib(kind: str = "f64"):
     L.orc_pcg.restype = i32
     L.orc_stress.argtypes = [i64, _D, _D, i64, _D, _D, _D, dbl, dbl, dbl, dbl, i32, _D]
     L.orc_stress.restype = i32
+    L.orc_grad_material.argtypes = [i64, _D, i64, _D, _D, _D, _D, _D, _D, dbl, dbl, dbl, dbl, i32, _D, _D]
+    L.orc_grad_material.restype = i32
     _libs[kind] = L
     return L
 
@@ -242,6 +244,18 @@ def stress(xyz, u, pts, E, nu, alpha_s, alpha_c, q, h, kind="f64"):
     if st:
         raise OracleError(st, "stress")
     return sig
+
+
+def grad_material(xyz, pts, wj, E, nu, u, lam, alpha_s, alpha_c, q, h, kind="f64"):
+    """Per point (dL/dE, dL/dnu) = -w eps(lam)^T dD/dtheta eps(u)."""
+    xyz, pts = _c(xyz), _c(pts)
+    dE = np.zeros(pts.shape[0])
+    dnu = np.zeros(pts.shape[0])
+    st = lib(kind).orc_grad_material(xyz.shape[0], xyz, pts.shape[0], pts, _c(wj), _c(E), _c(nu), _c(u),
+                                     _c(lam), alpha_s, alpha_c, q, h, MAX_SUPPORT, dE, dnu)
+    if st:
+        raise OracleError(st, "grad_material")
+    return dE, dnu
 
 
 def solve_problem(p, kind="f64", rtol=1e-10, scale=1e8, max_iter=200000):

@@ -496,13 +496,14 @@ int orc_penalty(int64_t n_nodes, const int64_t *rowptr, const int32_t *cols, dou
                 double *f, int64_t m, const int64_t *dofs, const double *values, double scale,
                 double *alpha_out)
 {
+    /* scale < 0: alpha = -scale is given by the caller (frozen penalty) */
     double kmax = 0.0;
     for (int64_t I = 0; I < n_nodes; I++)
         for (int64_t t = rowptr[I]; t < rowptr[I + 1]; t++)
             if (cols[t] == I)
                 for (int a = 0; a < 3; a++)
                     if (vals[9 * t + 4 * a] > kmax) kmax = vals[9 * t + 4 * a];
-    double alpha = scale * kmax;
+    double alpha = scale < 0 ? -scale : scale * kmax;
     for (int64_t i = 0; i < m; i++) {
         int64_t d = dofs[i], I = d / 3;
         int a = (int)(d % 3);
@@ -588,6 +589,75 @@ int orc_pcg(int64_t n_nodes, const int64_t *rowptr, const int32_t *cols, const d
     if (relres) *relres = (double)(rn / fn);
     free(x); free(r); free(z); free(p); free(qv); free(dinv);
     return rn <= (real)rtol * fn ? ORC_OK : ORC_E_NOCONV;
+}
+
+/* ---------------------------------------------------------------------------
+ * Material gradient of a solved system (back-analysis). With K(theta) u = f
+ * and the adjoint K lam = dL/du (K symmetric, penalty frozen), the gradient
+ * of L with respect to the parameters of point g is
+ *     dL/dtheta_g = - w_g eps_g(lam)^T (dD/dtheta) eps_g(u),
+ * eps_g(v) = sum_I B_I(x_g) v_I, for theta = E and theta = nu, with
+ *     dD/dE = D/E,
+ *     dD/dnu = dlambda/dnu (1 1 1 0 0 0)^T (1 1 1 0 0 0)
+ *              + dmu/dnu diag(2, 2, 2, 1, 1, 1),
+ *     dlambda/dnu = E (1 + 2 nu^2) / ((1 + nu)^2 (1 - 2 nu)^2),
+ *     dmu/dnu = -E / (2 (1 + nu)^2).
+ * ------------------------------------------------------------------------- */
+static void elastic_dD(real E, real nu, real dDE[6][6], real dDnu[6][6])
+{
+    real D[6][6];
+    elastic_D(E, nu, D);
+    for (int a = 0; a < 6; a++)
+        for (int b = 0; b < 6; b++) dDE[a][b] = D[a][b] / E;
+    real dlam = E * (1 + 2 * nu * nu) / ((1 + nu) * (1 + nu) * (1 - 2 * nu) * (1 - 2 * nu));
+    real dmu = -E / (2 * (1 + nu) * (1 + nu));
+    memset(dDnu, 0, sizeof(real) * 36);
+    for (int a = 0; a < 3; a++) {
+        for (int b = 0; b < 3; b++) dDnu[a][b] = dlam;
+        dDnu[a][a] = dlam + 2 * dmu;
+        dDnu[3 + a][3 + a] = dmu;
+    }
+}
+
+int orc_grad_material(int64_t n_nodes, const double *xyz, int64_t n_pts, const double *pts,
+                      const double *wj, const double *E, const double *nu, const double *u,
+                      const double *lam, double alpha_s, double alpha_c, double q, double h,
+                      int max_support, double *dE, double *dnu)
+{
+    const double rs2 = orc_support_radius2(alpha_s, h);
+    int32_t *s = (int32_t *)malloc((size_t)max_support * sizeof(int32_t));
+    real *ph = (real *)malloc((size_t)max_support * 4 * sizeof(real));
+    if (!s || !ph) { free(s); free(ph); return ORC_E_OOM; }
+    int st = ORC_OK;
+    for (int64_t p = 0; p < n_pts; p++) {
+        int64_t c = orc_support(n_nodes, xyz, pts + 3 * p, rs2, s, max_support);
+        if (c < 4 || c > max_support) { st = ORC_E_SUPPORT; break; }
+        st = shape_real(xyz, s, (int)c, pts + 3 * p, h, alpha_c, q, ph);
+        if (st != ORC_OK) break;
+        real eu[6] = {0, 0, 0, 0, 0, 0}, el[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t a = 0; a < c; a++) {
+            real g[3] = {ph[c + a], ph[2 * c + a], ph[3 * c + a]};
+            real B[6][3];
+            strain_B(g, B);
+            for (int r = 0; r < 6; r++)
+                for (int k = 0; k < 3; k++) {
+                    eu[r] += B[r][k] * (real)u[3 * (int64_t)s[a] + k];
+                    el[r] += B[r][k] * (real)lam[3 * (int64_t)s[a] + k];
+                }
+        }
+        real dDE[6][6], dDnu[6][6];
+        elastic_dD((real)E[p], (real)nu[p], dDE, dDnu);
+        real ge = 0, gn = 0;
+        for (int a = 0; a < 6; a++)
+            for (int b = 0; b < 6; b++) {
+                ge += el[a] * dDE[a][b] * eu[b];
+                gn += el[a] * dDnu[a][b] * eu[b];
+            }
+        dE[p] = (double)(-(real)wj[p] * ge);
+        dnu[p] = (double)(-(real)wj[p] * gn);
+    }
+    free(s); free(ph);
+    return st;
 }
 
 /* ---------------------------------------------------------------------------

@@ -26,7 +26,8 @@ EXPORTED = [
     "rpim_build_pattern", "rpim_pattern_free", "rpim_pattern_get_info", "rpim_pattern_csr",
     "rpim_pattern_points", "rpim_pattern_copy_csr", "rpim_pattern_copy_points", "rpim_assemble",
     "rpim_shape_functions", "rpim_add_point_loads", "rpim_apply_penalty_bc", "rpim_solve_pcg",
-    "rpim_stress", "rpim_stress_noalloc", "rpim_last_error", "rpim_version", "rpim_probe_dfma", "rpim_probe_dmma",
+    "rpim_stress", "rpim_stress_noalloc", "rpim_last_error", "rpim_version",
+    "rpim_apply_penalty_alpha", "rpim_grad_material", "rpim_probe_dfma", "rpim_probe_dmma",
     "rpim_kernel_launches", "rpim_profile_enable", "rpim_profile_read", "rpim_kernel_series_info",
 ]
 
@@ -81,6 +82,8 @@ def lib():
         "rpim_solve_pcg": [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp],
         "rpim_stress": [vp, vp, i64, vp, vp, vp, vp, vp],
         "rpim_stress_noalloc": [vp, vp, i64, vp, vp, vp, vp, vp],
+        "rpim_apply_penalty_alpha": [vp, vp, vp, i64, vp, vp, dbl, vp],
+        "rpim_grad_material": [vp, vp, vp, vp, vp, vp, vp, vp],
         "rpim_probe_dfma": [i32, C.POINTER(dbl)],
         "rpim_probe_dmma": [i32, C.POINTER(dbl)],
         "rpim_profile_enable": [i32],
@@ -182,6 +185,18 @@ def rpim_apply_penalty_bc(handle, K_vals, f, dofs, values, penalty_scale=1e8, st
                                        _dev(values, torch.float64), penalty_scale, C.byref(a),
                                        _stream(stream)), "rpim_apply_penalty_bc")
     return a.value
+
+
+def rpim_apply_penalty_alpha(handle, K_vals, f, dofs, values, alpha, stream=None):
+    _check(lib().rpim_apply_penalty_alpha(handle, _dev(K_vals, torch.float64), _dev(f, torch.float64),
+                                          dofs.shape[0], _dev(dofs, torch.int64), _dev(values, torch.float64),
+                                          alpha, _stream(stream)), "rpim_apply_penalty_alpha")
+
+
+def rpim_grad_material(handle, u, lam, E, nu, dE, dnu, stream=None):
+    _check(lib().rpim_grad_material(handle, _dev(u, torch.float64), _dev(lam, torch.float64),
+                                    _dev(E, torch.float64), _dev(nu, torch.float64), _dev(dE, torch.float64),
+                                    _dev(dnu, torch.float64), _stream(stream)), "rpim_grad_material")
 
 
 def rpim_solve_pcg(handle, K_vals, f, u, rtol=1e-10, max_iter=100000, stream=None, check=True):
@@ -325,3 +340,52 @@ class Pattern:
         sig = torch.empty(xyz.shape[0], 6, dtype=torch.float64, device=self.device)
         rpim_stress(self.handle, u, xyz, E, nu, sig, stream)
         return sig
+
+
+# --------------------------------------------------------------------------- differentiable solve
+class _Solve(torch.autograd.Function):
+    """u(E, nu) for K(E, nu) u = f with a frozen penalty; backward by the
+    adjoint K lam = dL/du (same K, K symmetric) and rpim_grad_material."""
+
+    @staticmethod
+    def forward(ctx, E, nu, pattern, f_ext, dofs, values, alpha, rtol, max_iter):
+        E = E.detach().contiguous()
+        nu = nu.detach().contiguous()
+        K, f = pattern.assemble(E, nu)
+        f += f_ext
+        rpim_apply_penalty_alpha(pattern.handle, K, f, dofs, values, alpha)
+        u = torch.zeros(3 * pattern.info.n_nodes, dtype=torch.float64, device=E.device)
+        it, rr, st = rpim_solve_pcg(pattern.handle, K, f, u, rtol, max_iter)
+        ctx.pattern, ctx.K, ctx.rtol, ctx.max_iter = pattern, K, rtol, max_iter
+        ctx.save_for_backward(E, nu, u)
+        ctx.pcg = (it, rr)
+        return u
+
+    @staticmethod
+    def backward(ctx, gu):
+        E, nu, u = ctx.saved_tensors
+        lam = torch.zeros_like(u)
+        rpim_solve_pcg(ctx.pattern.handle, ctx.K, gu.contiguous(), lam, ctx.rtol, ctx.max_iter)
+        dE = torch.empty_like(E)
+        dnu = torch.empty_like(nu)
+        rpim_grad_material(ctx.pattern.handle, u, lam, E, nu, dE, dnu)
+        return dE, dnu, None, None, None, None, None, None, None
+
+
+def penalty_alpha(pattern, E, nu, scale=1e8):
+    """alpha = scale * max_i K_ii of K(E, nu): the value to freeze for a
+    back-analysis."""
+    K, f = pattern.assemble(E, nu)
+    dofs = torch.zeros(0, dtype=torch.int64, device=K.device)
+    vals = torch.zeros(0, dtype=torch.float64, device=K.device)
+    return rpim_apply_penalty_bc(pattern.handle, K, f, dofs, vals, scale)
+
+
+def solve(pattern, E, nu, f_ext, fixed_dofs, fixed_values, alpha, rtol=1e-12, max_iter=200000):
+    """Displacements u(E, nu) with gradients with respect to the per-point
+    Young's modulus E and Poisson's ratio nu (torch.autograd).
+
+    f_ext: surface loads (device, 3*n_nodes, material independent);
+    the body-force vector of the pattern's assembly is added inside;
+    alpha: the frozen penalty (see penalty_alpha)."""
+    return _Solve.apply(E, nu, pattern, f_ext, fixed_dofs, fixed_values, alpha, rtol, max_iter)

@@ -292,6 +292,52 @@ rpim_status launch_stress(rpim_pattern *p, int64_t n_pts, const int64_t *soff, c
     return RPIM_OK;
 }
 
+// dL/dtheta_g = -w_g eps_g(lam)^T (dD/dtheta) eps_g(u) for theta = E, nu;
+// one warp per point, strains reduced over the support in a fixed tree
+__global__ void grad_material_kernel(int64_t n_pts, const int64_t *soff, const int32_t *sidx, const double *phi,
+                                     const double *wj, const double *u, const double *lam, const double *E,
+                                     const double *nu, double *dE, double *dnu, DevError *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n_pts; p += warps) {
+        double eu[6] = {0, 0, 0, 0, 0, 0}, el[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t q = soff[p] + lane; q < soff[p + 1]; q += 32) {
+            const int64_t J = sidx[q];
+            const double gx = phi[4 * q + 1], gy = phi[4 * q + 2], gz = phi[4 * q + 3];
+            const double ux = u[3 * J], uy = u[3 * J + 1], uz = u[3 * J + 2];
+            const double lx = lam[3 * J], ly = lam[3 * J + 1], lz = lam[3 * J + 2];
+            eu[0] = fma(gx, ux, eu[0]); el[0] = fma(gx, lx, el[0]);
+            eu[1] = fma(gy, uy, eu[1]); el[1] = fma(gy, ly, el[1]);
+            eu[2] = fma(gz, uz, eu[2]); el[2] = fma(gz, lz, el[2]);
+            eu[3] = fma(gz, uy, fma(gy, uz, eu[3])); el[3] = fma(gz, ly, fma(gy, lz, el[3]));
+            eu[4] = fma(gz, ux, fma(gx, uz, eu[4])); el[4] = fma(gz, lx, fma(gx, lz, el[4]));
+            eu[5] = fma(gy, ux, fma(gx, uy, eu[5])); el[5] = fma(gy, lx, fma(gx, ly, el[5]));
+        }
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            eu[k] = wsum(eu[k]);
+            el[k] = wsum(el[k]);
+        }
+        if (lane == 0) {
+            const double Ev = E[p], v = nu[p], w = wj[p];
+            if (!(Ev > 0.0) || !(v > -1.0) || !(v < 0.5)) {
+                dev_fail(err, RPIM_E_ARG, p);
+                continue;
+            }
+            const double opv = 1.0 + v, omv = 1.0 - 2.0 * v;
+            const double lamE = v / (opv * omv), muE = 1.0 / (2.0 * opv);           // lambda/E, mu/E
+            const double dlam = Ev * (1.0 + 2.0 * v * v) / (opv * opv * omv * omv);  // dlambda/dnu
+            const double dmu = -Ev / (2.0 * opv * opv);                              // dmu/dnu
+            const double tt = (el[0] + el[1] + el[2]) * (eu[0] + eu[1] + eu[2]);
+            const double qq = 2.0 * (el[0] * eu[0] + el[1] * eu[1] + el[2] * eu[2]) + el[3] * eu[3] +
+                              el[4] * eu[4] + el[5] * eu[5];
+            dE[p] = -w * (lamE * tt + muE * qq);
+            dnu[p] = -w * (dlam * tt + dmu * qq);
+        }
+    }
+}
+
 static rpim_status ensure_phi(rpim_pattern *p, cudaStream_t s)
 {
     if (!p->phi) RPIM_CHECK(dalloc(&p->phi, 4 * p->n_entries, s));
@@ -328,6 +374,23 @@ extern "C" rpim_status rpim_assemble(rpim_pattern *p, const double *E, const dou
     launch("mirror", mirror_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, 0, s, p->n_nodes, p->rowptr, p->cols, K);
     RPIM_CUDA(cudaGetLastError());
     return check_device_error(p, "assemble");
+}
+
+extern "C" rpim_status rpim_grad_material(rpim_pattern *p, const double *u, const double *lam, const double *E,
+                                          const double *nu, double *dE, double *dnu, rpim_stream_t stream)
+{
+    if (!p || !u || !lam || !E || !nu || !dE || !dnu) return fail(RPIM_E_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    if (!p->phi) {
+        RPIM_CHECK(ensure_phi(p, s));
+        RPIM_CHECK(shape_functions(p, p->n_points, p->pts, p->soff, p->sidx, p->max_support, p->phi, s, "shape"));
+    }
+    launch("grad_material", grad_material_kernel, grid_size(p->sm_count, 8, p->n_points * 32, 256), 256, 0, s,
+           p->n_points, (const int64_t *)p->soff, (const int32_t *)p->sidx, (const double *)p->phi,
+           (const double *)p->wj, u, lam, E, nu, dE, dnu, p->err);
+    RPIM_CUDA(cudaGetLastError());
+    return check_device_error(p, "grad_material");
 }
 
 extern "C" rpim_status rpim_add_point_loads(rpim_pattern *p, int64_t n_pts, const double *xyz,

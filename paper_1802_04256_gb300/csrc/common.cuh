@@ -106,6 +106,7 @@ struct rpim_pattern {
     int32_t *sorted_ids = nullptr;  // [n_nodes] node ids in cell order
     int32_t *cell_start = nullptr;  // [cells+1]
     int32_t *node_cell = nullptr;   // [n_nodes] linear cell index of each node
+    uint32_t *node_cpk = nullptr;   // [n_nodes] cell coordinates packed x | y << 11 | z << 22
     int32_t *node_rank = nullptr;   // [n_nodes] position of the node in its cell
     // integration points
     double *pts = nullptr;          // [n_points*3]

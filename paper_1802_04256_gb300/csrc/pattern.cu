@@ -85,7 +85,7 @@ __device__ __forceinline__ int cell_coord(double x, double lo, double inv_edge, 
     return (int)c;
 }
 
-__global__ void bin_nodes(int64_t n, const double *xyz, Grid g, int32_t *node_cell,
+__global__ void bin_nodes(int64_t n, const double *xyz, Grid g, int32_t *node_cell, uint32_t *node_cpk,
                           int32_t *cell_count)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -95,6 +95,7 @@ __global__ void bin_nodes(int64_t n, const double *xyz, Grid g, int32_t *node_ce
         int cz = cell_coord(xyz[3 * i + 2], g.lo[2], g.inv_edge, g.n[2]);
         int32_t c = cx + g.n[0] * (cy + g.n[1] * cz);
         node_cell[i] = c;
+        node_cpk[i] = (uint32_t)cx | ((uint32_t)cy << 11) | ((uint32_t)cz << 22);
         atomicAdd(&cell_count[c], 1);
     }
 }
@@ -344,7 +345,7 @@ __global__ void entry_points_kernel(int64_t n_pts, const int64_t *soff, int32_t 
 // ---------------------------------------------------------------------------
 template <int PASS>
 __global__ void pattern_kernel(int64_t n_nodes, Grid g, const int32_t *cell_start,
-                               const int32_t *node_cell, const int32_t *node_rank,
+                               const int32_t *node_cell, const uint32_t *node_cpk, const int32_t *node_rank,
                                const int32_t *sorted_ids, const int64_t *toff, const int64_t *tent,
                                const int32_t *entry_pt, const int64_t *soff, const int32_t *sidx,
                                int64_t *rowcnt_or_ptr, int32_t *cols, int64_t *diag, int words,
@@ -391,8 +392,8 @@ __global__ void pattern_kernel(int64_t n_nodes, Grid g, const int32_t *cell_star
             const int32_t pt = entry_pt[tent[t]];
             for (int64_t f = soff[pt] + lane; f < soff[pt + 1]; f += 32) {
                 const int32_t J = sidx[f];
-                const int32_t cj = node_cell[J];
-                const int jx = cj % g.n[0], jy = (cj / g.n[0]) % g.n[1], jz = cj / (g.n[0] * g.n[1]);
+                const uint32_t cj = node_cpk[J];
+                const int jx = (int)(cj & 0x7FF), jy = (int)((cj >> 11) & 0x7FF), jz = (int)(cj >> 22);
                 const int dx = jx - cx, dy = jy - cy, dz = jz - cz;
                 if (dx < -2 || dx > 2 || dy < -2 || dy > 2 || dz < -2 || dz > 2) {
                     dev_fail(err, RPIM_E_ARG, I);
@@ -427,8 +428,11 @@ __global__ void pattern_kernel(int64_t n_nodes, Grid g, const int32_t *cell_star
                     int bit = __ffs(word) - 1;
                     word &= word - 1;
                     int b = i * 32 + bit;
-                    int r = 0;
-                    while (run_pre[w][r + 1] <= b) r++;
+                    int r = 0, hi = 25;  // run_pre[r] <= b < run_pre[r + 1]
+                    while (hi - r > 1) {
+                        const int mid = (r + hi) >> 1;
+                        if (run_pre[w][mid] <= b) r = mid; else hi = mid;
+                    }
                     int spos = run_start[w][r] + (b - run_pre[w][r]);
                     if (pos < list_cap) list[pos] = sorted_ids[spos];
                     pos++;
@@ -475,7 +479,7 @@ static void pattern_release(rpim_pattern *p)
 {
     cudaStream_t s = p->stream;
     dfree(p->xyz, s); dfree(p->sorted_xyz, s); dfree(p->sorted_ids, s); dfree(p->cell_start, s);
-    dfree(p->node_cell, s); dfree(p->node_rank, s); dfree(p->pts, s); dfree(p->wj, s);
+    dfree(p->node_cell, s); dfree(p->node_cpk, s); dfree(p->node_rank, s); dfree(p->pts, s); dfree(p->wj, s);
     dfree(p->soff, s); dfree(p->sidx, s); dfree(p->entry_pt, s); dfree(p->toff, s);
     dfree(p->tent, s); dfree(p->rowptr, s); dfree(p->cols, s); dfree(p->diag, s);
     dfree(p->phi, s); dfree(p->lamw, s); dfree(p->err, s); dfree(p->scal, s); dfree(p->series, s);
@@ -629,6 +633,7 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     int64_t *tmp = nullptr;
     int *dmax = nullptr;
     RPIM_CHECK(dalloc(&p->node_cell, n, s));
+    RPIM_CHECK(dalloc(&p->node_cpk, n, s));
     RPIM_CHECK(dalloc(&p->node_rank, n, s));
     RPIM_CHECK(dalloc(&p->cell_start, cells + 1, s));
     RPIM_CHECK(dalloc(&cursor, cells + 1, s));
@@ -639,7 +644,8 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     RPIM_CUDA(cudaMemsetAsync(p->cell_start, 0, (cells + 1) * sizeof(int32_t), s));
     RPIM_CUDA(cudaMemsetAsync(cursor, 0, (cells + 1) * sizeof(int32_t), s));
     RPIM_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
-    launch("bin_nodes", bin_nodes, grid_size(p->sm_count, 4, n, 256), 256, 0, s, n, xyz, p->grid, p->node_cell, p->cell_start);
+    launch("bin_nodes", bin_nodes, grid_size(p->sm_count, 4, n, 256), 256, 0, s, n, xyz, p->grid, p->node_cell,
+           p->node_cpk, p->cell_start);
     RPIM_CHECK(exclusive_scan32(p->cell_start, cells, tmp, s));
     launch("fill_cells", fill_cells, grid_size(p->sm_count, 4, n, 256), 256, 0, s, n, p->node_cell, p->cell_start, cursor, p->sorted_ids);
     launch("finish_cells", finish_cells, grid_size(p->sm_count, 4, cells, 128), 128, 0, s, cells, p->cell_start, p->sorted_ids, xyz,
@@ -670,7 +676,7 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
         if (smem > 48 * 1024)
             RPIM_CUDA(cudaFuncSetAttribute(pattern_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         launch("pattern_count", pattern_kernel<0>, grid_size(p->sm_count, 4, n, wpb), wpb * 32, smem, s, 
-            n, p->grid, p->cell_start, p->node_cell, p->node_rank, p->sorted_ids, p->toff, p->tent,
+            n, p->grid, p->cell_start, p->node_cell, p->node_cpk, p->node_rank, p->sorted_ids, p->toff, p->tent,
             p->entry_pt, p->soff, p->sidx, p->rowptr, nullptr, nullptr, words, 0, dmax, p->err);
         RPIM_CUDA(cudaGetLastError());
     }
@@ -694,7 +700,7 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
         if (smem > 227 * 1024) return fail(RPIM_E_SUPPORT, "pattern row too long for shared memory");
         RPIM_CUDA(cudaFuncSetAttribute(pattern_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         launch("pattern_fill", pattern_kernel<1>, grid_size(p->sm_count, 4, n, wpb), wpb * 32, smem, s, 
-            n, p->grid, p->cell_start, p->node_cell, p->node_rank, p->sorted_ids, p->toff, p->tent,
+            n, p->grid, p->cell_start, p->node_cell, p->node_cpk, p->node_rank, p->sorted_ids, p->toff, p->tent,
             p->entry_pt, p->soff, p->sidx, p->rowptr, p->cols, p->diag, words, p2, nullptr, p->err);
         RPIM_CUDA(cudaGetLastError());
     }

@@ -45,6 +45,8 @@ __global__ void penalty_alpha_kernel(PenaltyState *st, double scale)
     st->alpha = scale * unord(st->kmax);
 }
 
+__global__ void penalty_fixed_alpha_kernel(PenaltyState *st, double alpha) { st->alpha = alpha; }
+
 __global__ void dof_count_kernel(int64_t m, const int64_t *dofs, int64_t ndof, int *mark, DevError *err)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
@@ -315,6 +317,31 @@ extern "C" rpim_status rpim_apply_penalty_bc(rpim_pattern *p, double *K, double 
     rpim_status r = check_device_error(p, "penalty");
     if (alpha_out) *alpha_out = alpha;
     return r;
+}
+
+extern "C" rpim_status rpim_apply_penalty_alpha(rpim_pattern *p, double *K, double *f, int64_t m, const int64_t *dofs,
+                                                const double *values, double alpha, rpim_stream_t stream)
+{
+    if (!p || !K || !f || m < 0 || (m > 0 && (!dofs || !values)) || !(alpha >= 0.0))
+        return fail(RPIM_E_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    const int64_t ndof = 3 * p->n_nodes;
+    PenaltyState *st = nullptr;
+    int *mark = nullptr;
+    RPIM_CHECK(dalloc(&st, 1, s));
+    RPIM_CHECK(dalloc(&mark, ndof, s));
+    RPIM_CUDA(cudaMemsetAsync(mark, 0, ndof * sizeof(int), s));
+    launch("penalty_alpha", penalty_fixed_alpha_kernel, 1, 1, 0, s, st, alpha);
+    if (m > 0) {
+        launch("dof_count", dof_count_kernel, grid_size(p->sm_count, 4, m, 256), 256, 0, s, m, dofs, ndof, mark, p->err);
+        launch("penalty_apply", penalty_apply_kernel, grid_size(p->sm_count, 4, m, 256), 256, 0, s, m, dofs, values, ndof,
+               (const int *)mark, (const int64_t *)p->diag, (const PenaltyState *)st, K, f);
+    }
+    RPIM_CUDA(cudaGetLastError());
+    dfree(st, s);
+    dfree(mark, s);
+    return check_device_error(p, "penalty");
 }
 
 extern "C" rpim_status rpim_solve_pcg(rpim_pattern *p, const double *K, const double *f, double *u, double rtol,

@@ -29,6 +29,8 @@ MUTANTS = {
     "pcg_beta_inverted": ("real beta = rz_new / rz;", "real beta = rz / rz_new;"),
     "lambda_wrong": ("real lam = E * nu / ((1 + nu) * (1 - 2 * nu));",
                      "real lam = E * nu / ((1 + nu) * (1 - nu));"),
+    "dmu_dnu_sign": ("real dmu = -E / (2 * (1 + nu) * (1 + nu));", "real dmu = E / (2 * (1 + nu) * (1 + nu));"),
+    "dlam_dnu_term": ("real dlam = E * (1 + 2 * nu * nu)", "real dlam = E * (1 + nu * nu)"),
 }
 
 
@@ -58,6 +60,7 @@ def _pins(kind, cube):
     yield "rigid", lambda: pins.test_K_rigid_body_modes(m(), cube)
     yield "energy", lambda: pins.test_K_energy_of_linear_fields(m(), cube)
     yield "penalty", lambda: _penalty(kind, cube)
+    yield "grad", lambda: pins.check_grad_material(kind)
     yield "pcg", lambda: _pcg(kind, cube)
 
 

@@ -332,3 +332,77 @@ def test_gravity_column_reaction_and_stress():
     sig = oracle.stress(p.xyz, u, m.pts, p.E, p.nu, p.alpha_s, p.alpha_c, p.q, p.h)
     avg = np.dot(m.wj, sig[:, 2]) / m.wj.sum()
     assert abs(avg - (-gam * H / 2)) < 0.03 * gam * H / 2
+
+
+# ---------------------------------------------------------------- material gradient
+def test_grad_material_is_the_derivative_of_the_point_stiffness():
+    """dL/dtheta_g = -lam^T (dK_g/dtheta) u: compare with central differences
+    of lam^T K_g(theta) u, K_g the contribution of point g alone (K_g is
+    linear in E, so that difference is exact up to rounding)."""
+    check_grad_material("f64")
+
+
+def check_grad_material(kind):
+    p = gen.cube_config(n=5, jitter=0.2, seed=13)
+    pts, wj = oracle.gauss_points(p.cell_lo, p.cell_hi)
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal(3 * p.n_nodes)
+    lam = rng.standard_normal(3 * p.n_nodes)
+    E = gen.uniform(13, 1, p.n_points, 5e3, 2e4)
+    nu = gen.uniform(13, 2, p.n_points, 0.2, 0.4)
+    dE, dnu = oracle.grad_material(p.xyz, pts, wj, E, nu, u, lam, p.alpha_s, p.alpha_c, p.q, p.h, kind)
+
+    def form(g, Eg, nug):
+        m = oracle.assemble(p.xyz, pts[[g]], wj[[g]], [Eg], [nug], p.alpha_s, p.alpha_c, p.q, p.h, kind="f64")
+        return lam @ m.matvec(u)
+
+    for g in (0, 311, 777):
+        dEf = (form(g, E[g] * (1 + 1e-4), nu[g]) - form(g, E[g] * (1 - 1e-4), nu[g])) / (2e-4 * E[g])
+        dnf = (form(g, E[g], nu[g] + 1e-5) - form(g, E[g], nu[g] - 1e-5)) / 2e-5
+        assert abs(dE[g] + dEf) <= 1e-9 * abs(dEf) + 1e-15
+        assert abs(dnu[g] + dnf) <= 1e-7 * abs(dnf) + 1e-12
+
+
+def _dense_solve(p, pts, wj, E, nu, f_ext, alpha):
+    m = oracle.assemble(p.xyz, pts, wj, E, nu, p.alpha_s, p.alpha_c, p.q, p.h)
+    vals = m.vals.ravel().copy()
+    f = m.f + f_ext
+    oracle.penalty(p.n_nodes, m.rowptr, m.cols, vals, f, p.fixed_dofs, p.fixed_vals, -alpha)
+    K = oracle.Model(m.n_nodes, m.rowptr, m.cols, vals.reshape(-1, 9), f, None, None).dense()
+    return K, np.linalg.solve(K, f)
+
+
+def test_adjoint_gradient_matches_finite_differences_of_the_loss():
+    """L = 1/2 |u(theta) - u_obs|^2 with a frozen penalty: the adjoint
+    gradient (K lam = u - u_obs, then grad_material) agrees with central
+    differences of L (dense solves) for single parameters and along a random
+    direction of all parameters."""
+    p = gen.cube_config(n=5, jitter=0.2, seed=17)
+    pts, wj = oracle.gauss_points(p.cell_lo, p.cell_hi)
+    E = gen.uniform(17, 1, p.n_points, 5e3, 2e4)
+    nu = gen.uniform(17, 2, p.n_points, 0.2, 0.4)
+    f_ext = np.zeros(3 * p.n_nodes)
+    oracle.point_loads(p.xyz, p.load_xyz, p.load_force, p.alpha_s, p.alpha_c, p.q, p.h, f_ext)
+    alpha = 1e8 * 4e3
+    K, u = _dense_solve(p, pts, wj, E, nu, f_ext, alpha)
+    u_obs = u * (1 + 0.1 * np.sin(np.arange(len(u))))
+    lam = np.linalg.solve(K, u - u_obs)
+    dE, dnu = oracle.grad_material(p.xyz, pts, wj, E, nu, u, lam, p.alpha_s, p.alpha_c, p.q, p.h)
+
+    def loss(E_, nu_):
+        return 0.5 * np.sum((_dense_solve(p, pts, wj, E_, nu_, f_ext, alpha)[1] - u_obs) ** 2)
+
+    for g in (5, 400):
+        h = 1e-3 * E[g]
+        Ep, Em = E.copy(), E.copy()
+        Ep[g] += h
+        Em[g] -= h
+        fd = (loss(Ep, nu) - loss(Em, nu)) / (2 * h)
+        assert abs(fd - dE[g]) <= 1e-5 * abs(dE[g])
+    rng = np.random.default_rng(9)
+    dirE = rng.standard_normal(len(E)) * E
+    dirn = rng.standard_normal(len(nu)) * 0.01
+    t = 1e-5
+    fd = (loss(E + t * dirE, nu + t * dirn) - loss(E - t * dirE, nu - t * dirn)) / (2 * t)
+    an = dE @ dirE + dnu @ dirn
+    assert abs(fd - an) <= 1e-6 * abs(an)
