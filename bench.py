@@ -7,7 +7,9 @@ first stage on device-resident inputs: rpim_build_pattern (Gauss points,
 cell list, supports, node incidence, BSR pattern) + rpim_assemble (shape
 functions, B^T D B, deterministic reduction) + rpim_add_point_loads. The
 penalty stage and the PCG solve are timed once after the timed steps and
-reported under "solve" (full solves/s).
+reported under "solve" (full solves/s). "batched" compares one batched
+pattern + assembly + batched PCG over blocks of the 512-block workload with
+the same blocks run one by one through the plain entry points.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -38,6 +40,18 @@ METRIC = "RPIM assembly Gauss-pts/s, % of FP64/HBM roofline; batched vs per-inst
 UNIT = "Gauss-pts/s"
 WORKLOAD = ("cantilever 129x17x17 (37,281 nodes, 298,248 Gauss points), interior jitter 0.2h, "
             "alpha_s 2.5, MQ alpha_c 4.0 q 1.03, E 1e4 nu 0.3, FP64")
+
+
+def _hbm_peak():
+    """Measured copy bandwidth of this GPU pool (GB/s), else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured copy bandwidth, MEASURED_PEAKS.json (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback copy bandwidth 6.8 TB/s (of fallback)"
+
+
+HBM_PEAK, HBM_SRC = _hbm_peak()
 
 
 def _cores():
@@ -198,7 +212,7 @@ def run_reference(args, rank):
 
 
 # --------------------------------------------------------------------------- stages 2 and 3
-def _solve(pat, p, E, nu, lxyz, lf, tt, stream):
+def _solve(pat, p, E, nu, lxyz, lf, tt, stream, peak_gflops):
     """Penalty (alpha = 1e8 max diag K) and Jacobi-PCG to 1e-10, timed once
     with CUDA events; the assembly that feeds it is not timed."""
     import torch
@@ -215,13 +229,186 @@ def _solve(pat, p, E, nu, lxyz, lf, tt, stream):
     solve_ms = s0.elapsed_time(s1)
     tip = int(np.nonzero(np.all(np.abs(p.nominal - [8.0, 0.5, 0.5]) < 1e-9, axis=1))[0][0])
     nnzb = pat.nnz_blocks
+    # per-kernel times of the iteration: 256 more iterations with event timing
+    import paper_1802_04256_gb300 as R
+    R.rpim_profile_read(reset=True)
+    R.rpim_profile_enable(True)
+    pat.solve_pcg(K, f, u.clone(), rtol=0.0, max_iter=256, check=False)
+    R.rpim_profile_enable(False)
+    prof = R.rpim_profile_read(reset=True)
+    spmv_bytes = nnzb * (72 + 4) + p.n_nodes * (8 + 24 + 24)
+    roof = None
+    if "pcg_spmv" in prof:
+        # 9 FMA per 3x3 block: on this chip the FP64 time of a product
+        # (18 nnzb / DFMA peak) exceeds its HBM time (bytes / copy bandwidth)
+        c, tot = prof["pcg_spmv"]
+        t = tot / c / 1e3
+        t_alu, t_hbm = 18 * nnzb / (peak_gflops * 1e9), spmv_bytes / (HBM_PEAK * 1e9)
+        if t_alu >= t_hbm:
+            ach = 18 * nnzb / t / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": peak_gflops / 1e3, "unit": "TFLOP/s",
+                    "frac": ach * 1e3 / peak_gflops, "peak_source": "FP64 DFMA throughput measured in this run"}
+        else:
+            ach = spmv_bytes / t / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK, "unit": "GB/s", "frac": ach / HBM_PEAK,
+                    "peak_source": HBM_SRC}
+        roof.update({"kernel": "pcg_spmv", "algorithmic_bytes_per_launch": spmv_bytes,
+                     "algorithmic_flops_per_launch": 18 * nnzb, "hbm_GBps": spmv_bytes / t / 1e9,
+                     "hbm_frac": spmv_bytes / t / 1e9 / HBM_PEAK, "avg_launch_ms": tot / c})
     out = {"pcg_iterations": iters, "relres": relres, "ms": solve_ms, "solves_per_s": 1e3 / solve_ms,
            "ms_per_iteration": solve_ms / max(iters, 1), "penalty_alpha": alpha,
            "tip_deflection": -u[3 * tip + 2].item(), "timoshenko": 0.20700,
-           "spmv_algorithmic_bytes": nnzb * (72 + 4) + 8 * (p.n_nodes + 1), "spmv_flops": 18 * nnzb}
+           "spmv_algorithmic_bytes": spmv_bytes, "spmv_flops": 18 * nnzb, "spmv_roofline": roof,
+           "iteration_kernel_ms": {k: round(v[1] / v[0], 4) for k, v in prof.items()}}
     del K, f, u
     pat.free()
     return out
+
+
+# --------------------------------------------------------------------------- differentiable solve
+def _backanalysis(dev, stream, rtol=1e-10):
+    """One gradient of the back-analysis misfit L = 1/2 sum |u - u_obs|^2 at
+    500 observed nodes with respect to the per-point E and nu of the
+    64 x 32 x 32 block (524,288 points): forward = assembly + frozen penalty
+    + PCG, backward = adjoint PCG + the per-point gradient kernel. Timed once
+    with CUDA events after one untimed gradient."""
+    import torch
+    import paper_1802_04256_gb300 as R
+    p = gen.backanalysis_config()
+    tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    pat = R.Pattern.from_problem(p)
+    f_ext = torch.zeros(3 * p.n_nodes, dtype=torch.float64, device=dev)
+    pat.add_point_loads(tt(p.load_xyz), tt(p.load_force), f_ext)
+    dofs, vals = tt(p.fixed_dofs, torch.int64), tt(p.fixed_vals)
+    obs = tt(p.meta["obs_nodes"], torch.int64)
+    E0, nu0 = tt(p.E), tt(p.nu)
+    alpha = R.penalty_alpha(pat, E0, nu0)
+    with torch.no_grad():   # observations: displacements of the hidden field
+        u_obs = R.solve(pat, tt(p.meta["E_hidden"]), tt(p.meta["nu_hidden"]), f_ext, dofs, vals, alpha,
+                        rtol=rtol).view(-1, 3)[obs].clone()
+
+    def one():
+        E = E0.clone().requires_grad_()
+        nu = nu0.clone().requires_grad_()
+        e0, e1, e2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e0.record(stream)
+        u = R.solve(pat, E, nu, f_ext, dofs, vals, alpha, rtol=rtol)
+        loss = 0.5 * ((u.view(-1, 3)[obs] - u_obs) ** 2).sum()
+        e1.record(stream)
+        loss.backward()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), float(E.grad.abs().max()), float(nu.grad.abs().max())
+
+    one()
+    fwd, bwd, gE, gn = one()
+    pat.free()
+    return {"workload": "back-analysis block 64x32x32 (65,536 nodes, 524,288 points), log-normal E field, "
+                        "500 observed nodes", "parameters": 2 * p.n_points, "rtol": rtol,
+            "forward_ms": fwd, "backward_ms": bwd, "gradients_per_s": 1e3 / (fwd + bwd),
+            "max_abs_dL_dE": gE, "max_abs_dL_dnu": gn,
+            "step": "forward: rpim_assemble + rpim_apply_penalty_alpha + rpim_solve_pcg; "
+                    "backward: rpim_solve_pcg (adjoint) + rpim_grad_material"}
+
+
+# --------------------------------------------------------------------------- batched vs per-instance
+def _batched(n_sel, dev, stream, reps=1):
+    """Blocks of the 512-instance batched workload (node counts log-uniform in
+    500-20,000, alpha_s uniform in [2, 3.5]), every (512 / n_sel)-th one:
+    one batched pattern + assembly + loads + per-instance penalty + batched
+    PCG, against the same instances through the plain entry points one after
+    another. Device-resident inputs; CUDA events on the launching stream."""
+    import torch
+    import paper_1802_04256_gb300 as R
+    allp = gen.batched_configs()
+    sel = allp[::max(1, len(allp) // n_sel)][:n_sel]
+    tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    offs = np.concatenate([[0], np.cumsum([p.n_nodes for p in sel])])
+    inst = [(p.n_nodes, p.alpha_s, p.h) for p in sel]
+    cat = lambda name: np.concatenate([getattr(p, name) for p in sel])
+    bx, blo, bhi, bE, bnu = tt(cat("xyz")), tt(cat("cell_lo")), tt(cat("cell_hi")), tt(cat("E")), tt(cat("nu"))
+    blx, blf = tt(cat("load_xyz")), tt(cat("load_force"))
+    bli = tt(np.concatenate([np.full(len(p.load_xyz), k, np.int32) for k, p in enumerate(sel)]), torch.int32)
+    bdofs = tt(np.concatenate([p.fixed_dofs + 3 * offs[k] for k, p in enumerate(sel)]), torch.int64)
+    bvals = tt(cat("fixed_vals"))
+    single = [dict(x=tt(p.xyz), lo=tt(p.cell_lo), hi=tt(p.cell_hi), E=tt(p.E), nu=tt(p.nu), lx=tt(p.load_xyz),
+                   lf=tt(p.load_force), dofs=tt(p.fixed_dofs, torch.int64), vals=tt(p.fixed_vals)) for p in sel]
+    rtol = 1e-10
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    def b_assemble():
+        pat = R.Pattern(bx, blo, bhi, None, sel[0].alpha_c, sel[0].q, None, instances=inst)
+        K, f = pat.assemble(bE, bnu)
+        pat.add_point_loads(blx, blf, f, inst=bli)
+        return pat, K, f
+
+    def b_solve(pat, K, f):
+        pat.apply_penalty(K, f, bdofs, bvals)
+        return pat.solve_pcg_batched(K, f, rtol=rtol, max_iter=500000)
+
+    def s_assemble(p, d):
+        pat = R.Pattern(d["x"], d["lo"], d["hi"], p.alpha_s, p.alpha_c, p.q, p.h)
+        K, f = pat.assemble(d["E"], d["nu"])
+        pat.add_point_loads(d["lx"], d["lf"], f)
+        return pat, K, f
+
+    def s_solve(pat, K, f, d):
+        pat.apply_penalty(K, f, d["dofs"], d["vals"])
+        return pat.solve_pcg(K, f, rtol=rtol, max_iter=500000)
+
+    def run_batched():
+        ta, (pat, K, f) = timed(b_assemble)
+        ts, (u, its, rrs) = timed(lambda: b_solve(pat, K, f))
+        pat.free()
+        return ta, ts, u, its
+
+    def run_single():
+        ta = ts = 0.0
+        us, its = [], []
+        for p, d in zip(sel, single):
+            a, (pat, K, f) = timed(lambda: s_assemble(p, d))
+            s, (u, it, rr) = timed(lambda: s_solve(pat, K, f, d))
+            pat.free()
+            ta, ts = ta + a, ts + s
+            us.append(u)
+            its.append(it)
+        return ta, ts, us, its
+
+    run_batched()
+    run_single()
+    l0 = R.rpim_kernel_launches()
+    bres = [run_batched() for _ in range(reps)]
+    lb = (R.rpim_kernel_launches() - l0) / reps
+    l0 = R.rpim_kernel_launches()
+    sres = [run_single() for _ in range(reps)]
+    ls = (R.rpim_kernel_launches() - l0) / reps
+    ba, bs = min(r[0] for r in bres), min(r[1] for r in bres)
+    sa, ss = min(r[0] for r in sres), min(r[1] for r in sres)
+    ub, itb = bres[-1][2], bres[-1][3]
+    us, its = sres[-1][2], sres[-1][3]
+    du = max(float(torch.linalg.norm(ub[3 * offs[k]:3 * offs[k + 1]] - us[k]) / torch.linalg.norm(us[k]))
+             for k in range(len(sel)))
+    npts = int(sum(p.n_points for p in sel))
+    return {"instances": len(sel), "of": len(allp), "selection": "every %d-th block of the 512-block workload"
+            % max(1, len(allp) // n_sel), "n_nodes": int(offs[-1]), "n_points": npts,
+            "node_range": [int(min(p.n_nodes for p in sel)), int(max(p.n_nodes for p in sel))],
+            "assembly": {"batched_ms": ba, "per_instance_ms": sa, "speedup": sa / ba,
+                         "batched_pts_per_s": npts / (ba / 1e3), "per_instance_pts_per_s": npts / (sa / 1e3)},
+            "solve": {"batched_ms": bs, "per_instance_ms": ss, "speedup": ss / bs, "rtol": rtol,
+                      "iterations_max": int(max(itb)), "iterations_sum_per_instance": int(sum(its))},
+            "end_to_end": {"batched_ms": ba + bs, "per_instance_ms": sa + ss, "speedup": (sa + ss) / (ba + bs)},
+            "kernel_launches": {"batched": lb, "per_instance": ls},
+            "u_max_rel_diff_batched_vs_per_instance": du,
+            "step": "build pattern + assemble + surface loads (assembly); penalty + Jacobi-PCG to 1e-10 (solve)"}
 
 
 # --------------------------------------------------------------------------- our arm
@@ -293,16 +480,19 @@ def run_ours(args, rank, world, local_rank):
     top = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
     roof = None
     if top in kinds:
+        # the shape kernel runs once per support-size bucket: the algorithmic
+        # flops of one step (all points) over the kernel's device time per step
         flops, src = kinds[top]
         nl, tot = prof[top]
-        avg_ms = tot / nl
-        ach = flops / (avg_ms / 1e3) / 1e12
+        step_ms = tot / args.steps
+        ach = flops / (step_ms / 1e3) / 1e12
         peak = peak_gflops / 1e3
         roof = {"bound": "alu", "kernel": top, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": _traffic_for(top, os.path.join(ROOT, "paper_1802_04256_gb300", "csrc", src)),
                 "peak_source": "FP64 DFMA throughput measured in this run (rpim_probe_dfma)",
-                "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_ms}
-    kernel_ms = {k: round(v[1] / v[0], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+                "algorithmic_flops_per_step": flops, "launches_per_step": nl / args.steps,
+                "kernel_ms_per_step": step_ms, "avg_launch_ms": tot / nl}
+    kernel_ms = {k: round(v[1] / args.steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     kernel_share = {k: round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4)
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
@@ -312,7 +502,7 @@ def run_ours(args, rank, world, local_rank):
     if args.no_solve:
         pat.free()
     else:
-        solve = _solve(pat, p, E, nu, lxyz, lf, tt, stream)
+        solve = _solve(pat, p, E, nu, lxyz, lf, tt, stream, peak_gflops)
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
     e2e = None
@@ -355,6 +545,13 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": world * p.n_points / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
+    batched = None
+    if args.batched_instances > 0:
+        batched = _batched(args.batched_instances, dev, stream)
+    grad = None
+    if not args.no_grad:
+        grad = _backanalysis(dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p)
@@ -368,9 +565,10 @@ def run_ours(args, rank, world, local_rank):
                           "l2": "working set larger than L2 (K %.2f GB, shape functions %.2f GB)"
                                 % (nnzb * 72 / 1e9, nsup.sum() * 32 / 1e9),
                           "parallelism": "replicas" if world > 1 else "single GPU"},
-               "roofline": roof, "kernel_ms_per_launch": kernel_ms, "kernel_time_share": kernel_share,
+               "roofline": roof, "kernel_ms_per_step": kernel_ms, "kernel_time_share": kernel_share,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-               "solve": solve, "fp64_peak_gflops_measured": peak_gflops}
+               "solve": solve, "batched": batched, "backanalysis": grad,
+               "fp64_peak_gflops_measured": peak_gflops}
         print(json.dumps(out))
 
 
@@ -383,6 +581,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the penalty + PCG measurement")
+    ap.add_argument("--no-grad", action="store_true", help="skip the back-analysis gradient measurement")
+    ap.add_argument("--batched-instances", type=int, default=32,
+                    help="blocks of the 512-block batched workload in the batched vs per-instance "
+                         "comparison (512 = all; 0 = skip)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

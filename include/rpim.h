@@ -105,6 +105,28 @@ rpim_status rpim_build_pattern(int64_t n_nodes, const double *xyz, const double 
                                const double *cell_hi, const rpim_params *params,
                                rpim_stream_t stream, rpim_pattern **out, int64_t *nnz_blocks);
 
+/*
+ * Batched stage 1a: one pattern for many independent node clouds
+ * ("instances", e.g. hundreds of blocks of a parameter study). Instance i
+ * owns the next inst[i].n_nodes nodes of xyz/cell_lo/cell_hi and has its own
+ * support radius alpha_s*h and spacing h (alpha_c, q and gauss_order are
+ * common). Every instance gets its own uniform grid, so supports never mix
+ * instances and K is block diagonal; each stage then runs in one launch
+ * over all instances. rpim_build_pattern is the one-instance case.
+ *   inst     host [n_inst]
+ * Synchronises. Errors as rpim_build_pattern.
+ */
+typedef struct {
+    int64_t n_nodes; /* nodes of this instance (consecutive)           */
+    double alpha_s;  /* support radius in units of h                   */
+    double h;        /* nodal spacing of this instance                 */
+} rpim_instance;
+
+rpim_status rpim_build_pattern_batched(int32_t n_inst, const rpim_instance *inst, const double *xyz,
+                                       const double *cell_lo, const double *cell_hi, double alpha_c,
+                                       double q, int32_t gauss_order, rpim_stream_t stream,
+                                       rpim_pattern **out, int64_t *nnz_blocks);
+
 /* Releases the pattern and all device memory it owns (stream-ordered on the
  * stream of the last call that used it). NULL is accepted. */
 rpim_status rpim_pattern_free(rpim_pattern *pattern);
@@ -174,6 +196,16 @@ rpim_status rpim_add_point_loads(rpim_pattern *pattern, int64_t n_pts, const dou
                                  const double *force, double *f, rpim_stream_t stream);
 
 /*
+ * Batched surface loads: as rpim_add_point_loads, with the instance of every
+ * load point (device int32 [n_pts]). Required for batched patterns.
+ * Errors: RPIM_E_ARG also when an id is outside [0, n_inst) (checked on the
+ * device before any use; the load index is in rpim_last_error).
+ */
+rpim_status rpim_add_point_loads_batched(rpim_pattern *pattern, int64_t n_pts, const double *xyz,
+                                         const double *force, const int32_t *inst, double *f,
+                                         rpim_stream_t stream);
+
+/*
  * Stage 2 (Sec. 2): penalty enforcement of prescribed displacements, one GPU
  * thread per constrained DOF as in the paper: alpha = penalty_scale *
  * max_i K_ii (over all scalar diagonal entries, computed on the device), then
@@ -185,6 +217,16 @@ rpim_status rpim_add_point_loads(rpim_pattern *pattern, int64_t n_pts, const dou
 rpim_status rpim_apply_penalty_bc(rpim_pattern *pattern, double *K_vals, double *f, int64_t m,
                                   const int64_t *dofs, const double *values, double penalty_scale,
                                   double *alpha_out, rpim_stream_t stream);
+
+/*
+ * Batched stage 2: one alpha per instance (scale * the instance's largest
+ * diagonal entry), each DOF penalised with its instance's alpha.
+ *   alpha_out host [n_inst], optional. Synchronises.
+ */
+rpim_status rpim_apply_penalty_bc_batched(rpim_pattern *pattern, double *K_vals, double *f, int64_t m,
+                                          const int64_t *dofs, const double *values,
+                                          double penalty_scale, double *alpha_out,
+                                          rpim_stream_t stream);
 
 /*
  * Stage 2 with a given penalty: as rpim_apply_penalty_bc, but alpha is the
@@ -207,6 +249,21 @@ rpim_status rpim_apply_penalty_alpha(rpim_pattern *pattern, double *K_vals, doub
 rpim_status rpim_solve_pcg(rpim_pattern *pattern, const double *K_vals, const double *f,
                            double *u, double rtol, int32_t max_iter, int32_t *iters,
                            double *relres, rpim_stream_t stream);
+
+/*
+ * Batched stage 3: the instances of a batched pattern are independent
+ * systems (K is block diagonal by instance), each iterated with its own
+ * PCG scalars and stopped on its own test ||r_i||_2 <= rtol ||f_i||_2 or
+ * after max_iter iterations; finished instances drop out of the sweeps. All
+ * instances advance in the same launches. Works on any pattern (one
+ * instance: the same iteration as rpim_solve_pcg).
+ *   iters host int32 [n_inst], relres host [n_inst], optional. Synchronises.
+ * Errors: RPIM_E_NOCONV, RPIM_E_NONFINITE (the first failing instance in
+ * rpim_last_error; u holds every instance's last iterate).
+ */
+rpim_status rpim_solve_pcg_batched(rpim_pattern *pattern, const double *K_vals, const double *f,
+                                   double *u, double rtol, int32_t max_iter, int32_t *iters,
+                                   double *relres, rpim_stream_t stream);
 
 /*
  * Material gradient of a solved system, per integration point (the
@@ -260,6 +317,14 @@ rpim_status rpim_stress(rpim_pattern *pattern, const double *u, int64_t n_pts,
 rpim_status rpim_stress_noalloc(rpim_pattern *pattern, const double *u, int64_t n_pts,
                                 const double *xyz, const double *E, const double *nu,
                                 double *sigma, rpim_stream_t stream);
+
+/* Batched stresses: as rpim_stress, with the instance of every point
+ * (device int32 [n_pts]). Required for batched patterns. Errors: RPIM_E_ARG
+ * also when an id is outside [0, n_inst), checked on the device before any
+ * use. */
+rpim_status rpim_stress_batched(rpim_pattern *pattern, const double *u, int64_t n_pts,
+                                const double *xyz, const int32_t *inst, const double *E,
+                                const double *nu, double *sigma, rpim_stream_t stream);
 
 /* Thread-local description of the last error returned on this thread. */
 const char *rpim_last_error(void);

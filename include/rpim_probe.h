@@ -11,6 +11,8 @@
  *     (2 flops per DFMA).
  *   rpim_probe_dmma: mma.sync m8n8k4 FP64 tensor-core instructions
  *     (512 flops each).
+ *   rpim_probe_fp64_mixed: half the warps on each of the two (equal flops
+ *     per half): the combined rate tells whether the paths add up.
  * Errors: RPIM_E_ARG (null pointer), RPIM_E_CUDA.
  */
 #ifndef RPIM_PROBE_H
@@ -21,6 +23,7 @@ extern "C" {
 #endif
 rpim_status rpim_probe_dfma(int32_t repeats, double *gflops);
 rpim_status rpim_probe_dmma(int32_t repeats, double *gflops);
+rpim_status rpim_probe_fp64_mixed(int32_t repeats, double *gflops);
 
 /* Host-only (no GPU needed): the piecewise series that the shape-function
  * kernel uses for the multiquadric minus its chord, for the given

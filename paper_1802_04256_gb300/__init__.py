@@ -13,6 +13,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -27,7 +28,9 @@ EXPORTED = [
     "rpim_pattern_points", "rpim_pattern_copy_csr", "rpim_pattern_copy_points", "rpim_assemble",
     "rpim_shape_functions", "rpim_add_point_loads", "rpim_apply_penalty_bc", "rpim_solve_pcg",
     "rpim_stress", "rpim_stress_noalloc", "rpim_last_error", "rpim_version",
-    "rpim_apply_penalty_alpha", "rpim_grad_material", "rpim_probe_dfma", "rpim_probe_dmma",
+    "rpim_apply_penalty_alpha", "rpim_grad_material", "rpim_build_pattern_batched",
+    "rpim_add_point_loads_batched", "rpim_apply_penalty_bc_batched", "rpim_stress_batched",
+    "rpim_solve_pcg_batched", "rpim_probe_dfma", "rpim_probe_dmma", "rpim_probe_fp64_mixed",
     "rpim_kernel_launches", "rpim_profile_enable", "rpim_profile_read", "rpim_kernel_series_info",
 ]
 
@@ -41,6 +44,10 @@ class RpimError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("alpha_s", C.c_double), ("alpha_c", C.c_double), ("q", C.c_double),
                 ("h", C.c_double), ("gauss_order", C.c_int32)]
+
+
+class Instance(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("alpha_s", C.c_double), ("h", C.c_double)]
 
 
 class PatternInfo(C.Structure):
@@ -84,8 +91,15 @@ def lib():
         "rpim_stress_noalloc": [vp, vp, i64, vp, vp, vp, vp, vp],
         "rpim_apply_penalty_alpha": [vp, vp, vp, i64, vp, vp, dbl, vp],
         "rpim_grad_material": [vp, vp, vp, vp, vp, vp, vp, vp],
+        "rpim_build_pattern_batched": [i32, C.POINTER(Instance), vp, vp, vp, dbl, dbl, i32, vp, C.POINTER(vp),
+                                       C.POINTER(i64)],
+        "rpim_add_point_loads_batched": [vp, i64, vp, vp, vp, vp, vp],
+        "rpim_apply_penalty_bc_batched": [vp, vp, vp, i64, vp, vp, dbl, C.POINTER(dbl), vp],
+        "rpim_stress_batched": [vp, vp, i64, vp, vp, vp, vp, vp, vp],
+        "rpim_solve_pcg_batched": [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp],
         "rpim_probe_dfma": [i32, C.POINTER(dbl)],
         "rpim_probe_dmma": [i32, C.POINTER(dbl)],
+        "rpim_probe_fp64_mixed": [i32, C.POINTER(dbl)],
         "rpim_profile_enable": [i32],
         "rpim_profile_read": [C.c_char_p, i64, i32],
         "rpim_kernel_series_info": [dbl, dbl, dbl, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
@@ -138,6 +152,38 @@ def rpim_build_pattern(xyz, cell_lo, cell_hi, params: Params, stream=None):
                                   C.byref(h), C.byref(nnz))
     _check(st, "rpim_build_pattern")
     return h, nnz.value
+
+
+def rpim_build_pattern_batched(instances, xyz, cell_lo, cell_hi, alpha_c, q, stream=None):
+    """instances: sequence of (n_nodes, alpha_s, h); nodes are consecutive."""
+    arr = (Instance * len(instances))(*[Instance(int(n), float(a), float(h)) for n, a, h in instances])
+    hnd = C.c_void_p()
+    nnz = C.c_int64(0)
+    st = lib().rpim_build_pattern_batched(len(instances), arr, _dev(xyz, torch.float64), _dev(cell_lo, torch.float64),
+                                          _dev(cell_hi, torch.float64), alpha_c, q, 2, _stream(stream),
+                                          C.byref(hnd), C.byref(nnz))
+    _check(st, "rpim_build_pattern_batched")
+    return hnd, nnz.value
+
+
+def rpim_add_point_loads_batched(handle, xyz, force, inst, f, stream=None):
+    _check(lib().rpim_add_point_loads_batched(handle, xyz.shape[0], _dev(xyz, torch.float64),
+                                              _dev(force, torch.float64), _dev(inst, torch.int32),
+                                              _dev(f, torch.float64), _stream(stream)), "rpim_add_point_loads_batched")
+
+
+def rpim_apply_penalty_bc_batched(handle, n_inst, K_vals, f, dofs, values, penalty_scale=1e8, stream=None):
+    a = (C.c_double * n_inst)()
+    _check(lib().rpim_apply_penalty_bc_batched(handle, _dev(K_vals, torch.float64), _dev(f, torch.float64),
+                                               dofs.shape[0], _dev(dofs, torch.int64), _dev(values, torch.float64),
+                                               penalty_scale, a, _stream(stream)), "rpim_apply_penalty_bc_batched")
+    return list(a)
+
+
+def rpim_stress_batched(handle, u, xyz, inst, E, nu, sigma, stream=None):
+    _check(lib().rpim_stress_batched(handle, _dev(u, torch.float64), xyz.shape[0], _dev(xyz, torch.float64),
+                                     _dev(inst, torch.int32), _dev(E, torch.float64), _dev(nu, torch.float64),
+                                     _dev(sigma, torch.float64), _stream(stream)), "rpim_stress_batched")
 
 
 def rpim_pattern_free(handle):
@@ -210,6 +256,17 @@ def rpim_solve_pcg(handle, K_vals, f, u, rtol=1e-10, max_iter=100000, stream=Non
     return it.value, rr.value, st
 
 
+def rpim_solve_pcg_batched(handle, n_inst, K_vals, f, u, rtol=1e-10, max_iter=100000, stream=None, check=True):
+    """Returns (iterations per instance, relative residual per instance, status)."""
+    it = (C.c_int32 * n_inst)()
+    rr = (C.c_double * n_inst)()
+    st = lib().rpim_solve_pcg_batched(handle, _dev(K_vals, torch.float64), _dev(f, torch.float64),
+                                      _dev(u, torch.float64), rtol, max_iter, it, rr, _stream(stream))
+    if check:
+        _check(st, "rpim_solve_pcg_batched")
+    return list(it), list(rr), st
+
+
 def rpim_stress(handle, u, xyz, E, nu, sigma, stream=None):
     _check(lib().rpim_stress(handle, _dev(u, torch.float64), xyz.shape[0], _dev(xyz, torch.float64),
                              _dev(E, torch.float64), _dev(nu, torch.float64),
@@ -220,6 +277,12 @@ def rpim_probe_dfma(repeats=5) -> float:
     """Measured FP64 FMA-pipe throughput of the current device, GFLOP/s."""
     g = C.c_double(0)
     _check(lib().rpim_probe_dfma(repeats, C.byref(g)), "rpim_probe_dfma")
+    return g.value
+
+
+def rpim_probe_fp64_mixed(repeats=5) -> float:
+    g = C.c_double(0)
+    _check(lib().rpim_probe_fp64_mixed(repeats, C.byref(g)), "rpim_probe_fp64_mixed")
     return g.value
 
 
@@ -273,11 +336,30 @@ class Pattern:
     """Owns an ``rpim_pattern``: integration points, supports and the BSR
     pattern of K for one node cloud."""
 
-    def __init__(self, xyz, cell_lo, cell_hi, alpha_s, alpha_c, q, h, stream=None):
-        self.params = Params(alpha_s, alpha_c, q, h, 2)
+    def __init__(self, xyz, cell_lo, cell_hi, alpha_s, alpha_c, q, h, stream=None, instances=None):
         self.device = xyz.device
-        self.handle, self.nnz_blocks = rpim_build_pattern(xyz, cell_lo, cell_hi, self.params, stream)
+        if instances is None:
+            self.params = Params(alpha_s, alpha_c, q, h, 2)
+            self.handle, self.nnz_blocks = rpim_build_pattern(xyz, cell_lo, cell_hi, self.params, stream)
+            self.n_inst = 1
+        else:
+            self.params = None
+            self.handle, self.nnz_blocks = rpim_build_pattern_batched(instances, xyz, cell_lo, cell_hi, alpha_c, q,
+                                                                      stream)
+            self.n_inst = len(instances)
         self.info = rpim_pattern_get_info(self.handle)
+
+    @classmethod
+    def batched(cls, problems, device="cuda", stream=None):
+        """One pattern for a list of gen.Problem instances (concatenated in
+        order); returns (pattern, node offsets)."""
+        xyz = np.concatenate([p.xyz for p in problems])
+        lo = np.concatenate([p.cell_lo for p in problems])
+        hi = np.concatenate([p.cell_hi for p in problems])
+        t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()
+        inst = [(p.n_nodes, p.alpha_s, p.h) for p in problems]
+        offs = np.concatenate([[0], np.cumsum([p.n_nodes for p in problems])])
+        return cls(t(xyz), t(lo), t(hi), None, problems[0].alpha_c, problems[0].q, None, stream, inst), offs
 
     @classmethod
     def from_problem(cls, p, device="cuda", stream=None):
@@ -323,11 +405,17 @@ class Pattern:
         rpim_assemble(self.handle, E, nu, body, K, f, stream)
         return K, f
 
-    def add_point_loads(self, xyz, force, f, stream=None):
-        rpim_add_point_loads(self.handle, xyz, force, f, stream)
+    def add_point_loads(self, xyz, force, f, stream=None, inst=None):
+        if inst is None:
+            rpim_add_point_loads(self.handle, xyz, force, f, stream)
+        else:
+            rpim_add_point_loads_batched(self.handle, xyz, force, inst, f, stream)
         return f
 
     def apply_penalty(self, K, f, dofs, values, scale=1e8, stream=None):
+        """alpha (a list of one alpha per instance for batched patterns)."""
+        if self.n_inst > 1:
+            return rpim_apply_penalty_bc_batched(self.handle, self.n_inst, K, f, dofs, values, scale, stream)
         return rpim_apply_penalty_bc(self.handle, K, f, dofs, values, scale, stream)
 
     def solve_pcg(self, K, f, u=None, rtol=1e-10, max_iter=100000, stream=None, check=True):
@@ -336,9 +424,19 @@ class Pattern:
         it, rr, st = rpim_solve_pcg(self.handle, K, f, u, rtol, max_iter, stream, check)
         return u, it, rr
 
-    def stress(self, u, xyz, E, nu, stream=None):
+    def solve_pcg_batched(self, K, f, u=None, rtol=1e-10, max_iter=100000, stream=None, check=True):
+        """Per-instance PCG: (u, iterations per instance, residual per instance)."""
+        if u is None:
+            u = torch.zeros(3 * self.info.n_nodes, dtype=torch.float64, device=self.device)
+        it, rr, st = rpim_solve_pcg_batched(self.handle, self.n_inst, K, f, u, rtol, max_iter, stream, check)
+        return u, it, rr
+
+    def stress(self, u, xyz, E, nu, stream=None, inst=None):
         sig = torch.empty(xyz.shape[0], 6, dtype=torch.float64, device=self.device)
-        rpim_stress(self.handle, u, xyz, E, nu, sig, stream)
+        if inst is None:
+            rpim_stress(self.handle, u, xyz, E, nu, sig, stream)
+        else:
+            rpim_stress_batched(self.handle, u, xyz, inst, E, nu, sig, stream)
         return sig
 
 

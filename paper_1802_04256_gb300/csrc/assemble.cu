@@ -354,7 +354,7 @@ extern "C" rpim_status rpim_shape_functions(rpim_pattern *p, double *phi, rpim_s
     if (!p || !phi) return fail(RPIM_E_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;
-    RPIM_CHECK(shape_functions(p, p->n_points, p->pts, p->soff, p->sidx, p->max_support, phi, s, "shape"));
+    RPIM_CHECK(shape_functions_all(p, phi, s));
     return check_device_error(p, "shape functions");
 }
 
@@ -366,7 +366,7 @@ extern "C" rpim_status rpim_assemble(rpim_pattern *p, const double *E, const dou
     p->stream = s;
     RPIM_CHECK(ensure_phi(p, s));
     launch("lame", lame_kernel, grid_size(p->sm_count, 4, p->n_points, 256), 256, 0, s, p->n_points, E, nu, p->wj, p->lamw, p->err);
-    RPIM_CHECK(shape_functions(p, p->n_points, p->pts, p->soff, p->sidx, p->max_support, p->phi, s, "shape"));
+    RPIM_CHECK(shape_functions_all(p, p->phi, s));
     launch("row", row_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, 0, s, p->n_nodes, p->toff,
            p->tent, p->entry_pt, p->soff, p->sidx, p->phi, p->lamw, p->wj, nu, body, p->rowptr, p->cols, p->diag,
            K, f, p->err);
@@ -384,7 +384,7 @@ extern "C" rpim_status rpim_grad_material(rpim_pattern *p, const double *u, cons
     p->stream = s;
     if (!p->phi) {
         RPIM_CHECK(ensure_phi(p, s));
-        RPIM_CHECK(shape_functions(p, p->n_points, p->pts, p->soff, p->sidx, p->max_support, p->phi, s, "shape"));
+        RPIM_CHECK(shape_functions_all(p, p->phi, s));
     }
     launch("grad_material", grad_material_kernel, grid_size(p->sm_count, 8, p->n_points * 32, 256), 256, 0, s,
            p->n_points, (const int64_t *)p->soff, (const int32_t *)p->sidx, (const double *)p->phi,
@@ -393,20 +393,39 @@ extern "C" rpim_status rpim_grad_material(rpim_pattern *p, const double *u, cons
     return check_device_error(p, "grad_material");
 }
 
-extern "C" rpim_status rpim_add_point_loads(rpim_pattern *p, int64_t n_pts, const double *xyz,
-                                            const double *force, double *f, rpim_stream_t stream)
+// every instance id of a point list must name an instance of the pattern:
+// the search and shape kernels index the per-instance grids with it
+__global__ void instance_ids_kernel(int64_t n, const int32_t *inst, int32_t n_inst, DevError *err)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        if ((uint32_t)inst[k] >= (uint32_t)n_inst) dev_fail(err, RPIM_E_ARG, k);
+}
+
+static rpim_status check_instance_ids(rpim_pattern *p, int64_t n, const int32_t *inst, cudaStream_t s,
+                                      const char *stage)
+{
+    if (!inst) return RPIM_OK;
+    launch("instance_ids", instance_ids_kernel, grid_size(p->sm_count, 4, n, 256), 256, 0, s, n, inst,
+           (int32_t)p->n_inst, p->err);
+    RPIM_CUDA(cudaGetLastError());
+    return check_device_error(p, stage);
+}
+
+static rpim_status add_point_loads(rpim_pattern *p, int64_t n_pts, const double *xyz, const double *force,
+                                   const int32_t *inst, double *f, cudaStream_t s)
 {
     if (!p || (n_pts > 0 && (!xyz || !force || !f)) || n_pts < 0) return fail(RPIM_E_ARG, "bad argument");
+    if (p->n_inst > 1 && !inst) return fail(RPIM_E_ARG, "a batched pattern needs the instance of every load point");
     if (n_pts == 0) return RPIM_OK;
-    cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;
     int64_t *soff = nullptr, *toff = nullptr, *tent = nullptr, ne = 0;
     int32_t *sidx = nullptr, *ept = nullptr, mx = 0, mn = 0, mi = 0;
     double *phi = nullptr;
-    RPIM_CHECK(search_supports(p, n_pts, xyz, &soff, &sidx, &ne, &mx, &mn, s, "search_loads"));
+    RPIM_CHECK(check_instance_ids(p, n_pts, inst, s, "point loads: instance id"));
+    RPIM_CHECK(search_supports(p, n_pts, xyz, inst, 0, &soff, &sidx, &ne, &mx, &mn, s, "search_loads"));
     rpim_status st = RPIM_OK;
     if ((st = dalloc(&phi, 4 * ne, s)) == RPIM_OK && (st = dalloc(&ept, ne, s)) == RPIM_OK) {
-        st = shape_functions(p, n_pts, xyz, soff, sidx, mx, phi, s, "shape_loads");
+        st = shape_functions(p, n_pts, xyz, inst, 0, (const int32_t *)nullptr, soff, sidx, mx, phi, s, "shape_loads");
         if (st == RPIM_OK) {
             launch("entry_points_loads", entry_points_kernel, grid_size(p->sm_count, 8, n_pts * 32, 256), 256, 0, s, n_pts, soff, ept);
             st = build_incidence(p->n_nodes, ne, sidx, &toff, &tent, &mi, s, p->sm_count);
@@ -421,24 +440,51 @@ extern "C" rpim_status rpim_add_point_loads(rpim_pattern *p, int64_t n_pts, cons
     return st;
 }
 
-extern "C" rpim_status rpim_stress(rpim_pattern *p, const double *u, int64_t n_pts, const double *xyz,
-                                   const double *E, const double *nu, double *sigma, rpim_stream_t stream)
+extern "C" rpim_status rpim_add_point_loads(rpim_pattern *p, int64_t n_pts, const double *xyz,
+                                            const double *force, double *f, rpim_stream_t stream)
+{
+    return add_point_loads(p, n_pts, xyz, force, nullptr, f, (cudaStream_t)stream);
+}
+
+extern "C" rpim_status rpim_add_point_loads_batched(rpim_pattern *p, int64_t n_pts, const double *xyz,
+                                                    const double *force, const int32_t *inst, double *f,
+                                                    rpim_stream_t stream)
+{
+    if (!inst && n_pts > 0) return fail(RPIM_E_ARG, "inst is null");
+    return add_point_loads(p, n_pts, xyz, force, inst, f, (cudaStream_t)stream);
+}
+
+static rpim_status stress(rpim_pattern *p, const double *u, int64_t n_pts, const double *xyz, const int32_t *inst,
+                          const double *E, const double *nu, double *sigma, cudaStream_t s)
 {
     if (!p || n_pts < 0 || (n_pts > 0 && (!u || !xyz || !E || !nu || !sigma))) return fail(RPIM_E_ARG, "bad argument");
+    if (p->n_inst > 1 && !inst) return fail(RPIM_E_ARG, "a batched pattern needs the instance of every stress point");
     if (n_pts == 0) return RPIM_OK;
-    cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;
     int64_t *soff = nullptr, ne = 0;
     int32_t *sidx = nullptr, mx = 0, mn = 0;
     double *phi = nullptr;
-    RPIM_CHECK(search_supports(p, n_pts, xyz, &soff, &sidx, &ne, &mx, &mn, s, "search_stress"));
+    RPIM_CHECK(check_instance_ids(p, n_pts, inst, s, "stress: instance id"));
+    RPIM_CHECK(search_supports(p, n_pts, xyz, inst, 0, &soff, &sidx, &ne, &mx, &mn, s, "search_stress"));
     rpim_status st = dalloc(&phi, 4 * ne, s);
-    if (st == RPIM_OK) st = shape_functions(p, n_pts, xyz, soff, sidx, mx, phi, s, "shape_stress");
-    if (st == RPIM_OK) {
-        launch("stress", stress_kernel, grid_size(p->sm_count, 8, n_pts * 32, 256), 256, 0, s, n_pts, soff, sidx, phi, u, E, nu, sigma, p->err);
-        if (cudaGetLastError() != cudaSuccess) st = fail(RPIM_E_CUDA, "stress kernel launch");
-    }
+    if (st == RPIM_OK)
+        st = shape_functions(p, n_pts, xyz, inst, 0, (const int32_t *)nullptr, soff, sidx, mx, phi, s, "shape_stress");
+    if (st == RPIM_OK) st = launch_stress(p, n_pts, soff, sidx, phi, u, E, nu, sigma, s);
     if (st == RPIM_OK) st = check_device_error(p, "stress");
     dfree(soff, s); dfree(sidx, s); dfree(phi, s);
     return st;
+}
+
+extern "C" rpim_status rpim_stress(rpim_pattern *p, const double *u, int64_t n_pts, const double *xyz,
+                                   const double *E, const double *nu, double *sigma, rpim_stream_t stream)
+{
+    return stress(p, u, n_pts, xyz, nullptr, E, nu, sigma, (cudaStream_t)stream);
+}
+
+extern "C" rpim_status rpim_stress_batched(rpim_pattern *p, const double *u, int64_t n_pts, const double *xyz,
+                                           const int32_t *inst, const double *E, const double *nu, double *sigma,
+                                           rpim_stream_t stream)
+{
+    if (!inst && n_pts > 0) return fail(RPIM_E_ARG, "inst is null");
+    return stress(p, u, n_pts, xyz, inst, E, nu, sigma, (cudaStream_t)stream);
 }

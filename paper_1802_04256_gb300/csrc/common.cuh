@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/rpim.h"
 
@@ -73,12 +74,25 @@ rpim_status build_kernel_series(double alpha_c, double alpha_s, double q, Kernel
 // ---------------------------------------------------------------------------
 // pattern object
 // ---------------------------------------------------------------------------
-struct Grid {
+// One independent instance (node cloud) of a pattern: its own uniform grid
+// (cell edge >= its support radius), support radius and nodal spacing.
+// Instances are consecutive node ranges; a plain pattern has one.
+struct InstGrid {
     double lo[3];
     double inv_edge;     // 1 / cell edge
+    double rs2;          // support radius squared
+    double inv_h;        // 1 / nodal spacing
     int n[3];            // cells per axis
-    int64_t cells;
+    int pad;
+    int64_t cell_off;    // first global cell of the instance
+    int64_t node_begin, node_end;
 };
+
+// instance of point k of a list: inst_of[k >> shift], or 0 without a map
+__device__ __forceinline__ int instance_of(const int32_t *inst_of, int shift, int64_t k)
+{
+    return inst_of ? inst_of[k >> shift] : 0;
+}
 
 struct Workspace {      // PCG vectors and reduction scratch (lazily sized)
     double *buf = nullptr;
@@ -90,16 +104,23 @@ struct Workspace {      // PCG vectors and reduction scratch (lazily sized)
 struct rpim_pattern {
     int device = 0;
     cudaStream_t stream = nullptr;
-    rpim_params prm{};
-    double rs2 = 0.0;      // support radius squared (physical units)
-    double inv_h = 0.0;
+    rpim_params prm{};     // alpha_c, q (common); alpha_s, h of the first instance
+    int n_inst = 1;
+    double series_alpha_s = 0.0;    // support radius the kernel series covers
+    std::vector<rpim::InstGrid> ig_host;
+    rpim::InstGrid *ig = nullptr;   // [n_inst] device copy
+    int32_t *node_inst = nullptr;   // [n_nodes] instance of each node
+    int64_t total_cells = 0;
+    // support-size buckets of the integration points for the shape kernel
+    std::vector<int64_t> bucket_count;   // points per bucket
+    std::vector<int32_t> bucket_nc;      // largest support in the bucket
+    int32_t *bucket_order = nullptr;     // [n_points] point ids grouped by bucket
 
     int64_t n_nodes = 0, n_points = 0, n_entries = 0, nnzb = 0;
     int32_t max_support = 0, min_support = 0, max_row = 0;
     int32_t max_incident = 0;  // largest number of (point, entry) pairs per node
     int32_t max_cell = 0;      // largest node count of a grid cell
 
-    rpim::Grid grid{};
     // nodes
     double *xyz = nullptr;          // [n_nodes*3] copy of the coordinates
     double *sorted_xyz = nullptr;   // [n_nodes*4] coordinates in cell order (x,y,z,pad)
@@ -131,6 +152,14 @@ struct rpim_pattern {
     rpim::KernelSeries *series = nullptr; // device copy
     rpim::KernelSeries series_host{};
     rpim::Workspace ws;
+    // row segments of the batched solver: rows [seg_row[s], seg_row[s+1])
+    // belong to instance seg_inst[s]; instance i owns the segments
+    // [inst_seg[i], inst_seg[i+1]) (built on the first batched solve)
+    cudaStream_t cap_stream = nullptr;   // capture-only stream of the PCG graphs
+    int64_t n_seg = 0;
+    int64_t *seg_row = nullptr;     // [n_seg+1]
+    int32_t *seg_inst = nullptr;    // [n_seg]
+    int32_t *inst_seg = nullptr;    // [n_inst+1]
     int sm_count = 0;
 };
 
@@ -165,24 +194,31 @@ rpim_status exclusive_scan32(int32_t *data, int64_t n, int64_t *tmp, cudaStream_
 rpim_status check_device_error(rpim_pattern *p, const char *stage);
 
 // support search for arbitrary points (count + fill); output offsets/ids
-// are allocated here (stream ordered) and owned by the caller.
-rpim_status search_supports(rpim_pattern *p, int64_t n_pts, const double *pts,
+// are allocated here (stream ordered) and owned by the caller. The instance
+// of point k is inst_of[k >> shift] (inst_of NULL: instance 0).
+rpim_status search_supports(rpim_pattern *p, int64_t n_pts, const double *pts, const int32_t *inst_of, int shift,
                             int64_t **soff, int32_t **sidx, int64_t *n_entries,
                             int32_t *max_n, int32_t *min_n, cudaStream_t s, const char *tag);
 
 // support search into caller-provided buffers (no allocation)
 rpim_status search_supports_into(rpim_pattern *p, int64_t n_pts, const double *pts, int64_t *soff, int64_t *tmp,
                                  int *minmax, int32_t *sidx, int64_t cap, int64_t *n_entries, int32_t *max_n,
-                                 cudaStream_t s, const char *tag);
+                                 cudaStream_t s, const char *tag);  // single-instance patterns
 
 // stress kernel on given supports and shape functions (no allocation)
 rpim_status launch_stress(rpim_pattern *p, int64_t n_pts, const int64_t *soff, const int32_t *sidx, const double *phi,
                           const double *u, const double *E, const double *nu, double *sigma, cudaStream_t s);
 
-// shape functions of n_pts points with given supports -> phi [entries*4]
-rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts,
-                            const int64_t *soff, const int32_t *sidx, int32_t max_n,
+// shape functions of n_pts points with given supports -> phi [entries*4];
+// instance of point k as for search_supports; `order` (optional) lists the
+// points to process (n_pts of them), all with supports <= max_n
+rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, const int32_t *inst_of, int shift,
+                            const int32_t *order, const int64_t *soff, const int32_t *sidx, int32_t max_n,
                             double *phi, cudaStream_t s, const char *tag);
+
+// shape functions of all integration points of a pattern, one launch per
+// support-size bucket
+rpim_status shape_functions_all(rpim_pattern *p, double *phi, cudaStream_t s);
 
 // node -> entries incidence (stable: ascending entry) of a support list
 rpim_status build_incidence(int64_t n_nodes, int64_t n_entries, const int32_t *sidx,
@@ -196,6 +232,9 @@ int grid_size(int sm_count, int blocks_per_sm_hint, int64_t work, int threads);
 // stream so that per-kernel device times can be read back.
 int64_t launch_begin(const char *name, cudaStream_t s);
 void launch_end(int64_t token, cudaStream_t s);
+bool profiling_on();            // per-kernel event timing enabled
+void add_launches(int64_t n);   // kernels run by a replayed CUDA graph
+int64_t launch_count();
 
 template <typename... KArgs, typename... Args>
 inline void launch(const char *name, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,

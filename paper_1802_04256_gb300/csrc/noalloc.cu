@@ -75,6 +75,7 @@ extern "C" rpim_status rpim_stress_noalloc(rpim_pattern *p, const double *u, int
     int dev = 0;
     RPIM_CUDA(cudaGetDevice(&dev));
     if (dev != p->device) return fail(RPIM_E_ARG, "pattern belongs to another device");
+    if (p->n_inst != 1) return fail(RPIM_E_ARG, "the allocation-free variant takes single-instance patterns");
     unsigned char *base = nullptr;
     RPIM_CHECK(scratch_address(dev, &base));
     cudaStream_t s = (cudaStream_t)stream;
@@ -91,7 +92,8 @@ extern "C" rpim_status rpim_stress_noalloc(rpim_pattern *p, const double *u, int
     // the fill pass writes the ids and the shape kernel writes phi
     RPIM_CHECK(search_supports_into(p, n_pts, xyz, soff, tmp, minmax, sidx, kMaxEntries, &ne, &mx, s,
                                     "search_stress_noalloc"));
-    RPIM_CHECK(shape_functions(p, n_pts, xyz, soff, sidx, mx, phi, s, "shape_stress_noalloc"));
+    RPIM_CHECK(shape_functions(p, n_pts, xyz, (const int32_t *)nullptr, 0, (const int32_t *)nullptr, soff, sidx, mx,
+                               phi, s, "shape_stress_noalloc"));
     RPIM_CHECK(launch_stress(p, n_pts, soff, sidx, phi, u, E, nu, sigma, s));
     return check_device_error(p, "stress (no allocation)");
 }

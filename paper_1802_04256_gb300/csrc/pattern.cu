@@ -52,12 +52,14 @@ __device__ __forceinline__ double unordered(unsigned long long u)
     return __longlong_as_double((long long)b);
 }
 
-__global__ void bbox_kernel(int64_t n, const double *xyz, unsigned long long *bb /*6: min xyz, max xyz*/,
+// bounding box of every instance: one block per instance, block reduction
+__global__ void bbox_kernel(const InstGrid *ig, const double *xyz, unsigned long long *bb /*6 per instance*/,
                             int *bad)
 {
+    __shared__ unsigned long long sm[6][32];
+    const InstGrid g = ig[blockIdx.x];
     unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t i = g.node_begin + threadIdx.x; i < g.node_end; i += blockDim.x)
         for (int k = 0; k < 3; k++) {
             double v = xyz[3 * i + k];
             if (!isfinite(v)) atomicExch(bad, 1);
@@ -65,16 +67,31 @@ __global__ void bbox_kernel(int64_t n, const double *xyz, unsigned long long *bb
             mn[k] = min(mn[k], o);
             mx[k] = max(mx[k], o);
         }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int k = 0; k < 3; k++) {
         for (int o = 16; o > 0; o >>= 1) {
             mn[k] = min(mn[k], __shfl_down_sync(0xffffffffu, mn[k], o));
             mx[k] = max(mx[k], __shfl_down_sync(0xffffffffu, mx[k], o));
         }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(&bb[k], mn[k]);
-            atomicMax(&bb[3 + k], mx[k]);
+        if (lane == 0) {
+            sm[k][w] = mn[k];
+            sm[3 + k][w] = mx[k];
         }
     }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        unsigned long long r = k < 3 ? ~0ull : 0ull;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) r = k < 3 ? min(r, sm[k][i]) : max(r, sm[k][i]);
+        bb[6 * blockIdx.x + k] = r;
+    }
+}
+
+// instance of every node: one block per instance
+__global__ void node_inst_kernel(const InstGrid *ig, int32_t *node_inst)
+{
+    const InstGrid g = ig[blockIdx.x];
+    for (int64_t i = g.node_begin + threadIdx.x; i < g.node_end; i += blockDim.x) node_inst[i] = (int32_t)blockIdx.x;
 }
 
 __device__ __forceinline__ int cell_coord(double x, double lo, double inv_edge, int n)
@@ -85,16 +102,17 @@ __device__ __forceinline__ int cell_coord(double x, double lo, double inv_edge, 
     return (int)c;
 }
 
-__global__ void bin_nodes(int64_t n, const double *xyz, Grid g, int32_t *node_cell, uint32_t *node_cpk,
-                          int32_t *cell_count)
+__global__ void bin_nodes(int64_t n, const double *xyz, const InstGrid *ig, const int32_t *node_inst,
+                          int32_t *node_cell, uint32_t *node_cpk, int32_t *cell_count)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+        const InstGrid &g = ig[node_inst[i]];
         int cx = cell_coord(xyz[3 * i], g.lo[0], g.inv_edge, g.n[0]);
         int cy = cell_coord(xyz[3 * i + 1], g.lo[1], g.inv_edge, g.n[1]);
         int cz = cell_coord(xyz[3 * i + 2], g.lo[2], g.inv_edge, g.n[2]);
-        int32_t c = cx + g.n[0] * (cy + g.n[1] * cz);
-        node_cell[i] = c;
+        int64_t c = g.cell_off + cx + (int64_t)g.n[0] * (cy + (int64_t)g.n[1] * cz);
+        node_cell[i] = (int32_t)c;
         node_cpk[i] = (uint32_t)cx | ((uint32_t)cy << 11) | ((uint32_t)cz << 22);
         atomicAdd(&cell_count[c], 1);
     }
@@ -155,10 +173,10 @@ __device__ __forceinline__ double dist2(double4 n, double x, double y, double z)
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(256) search_kernel(int64_t n_pts, const double *pts, Grid g,
-                                                     const int32_t *cell_start,
+__global__ void __launch_bounds__(256) search_kernel(int64_t n_pts, const double *pts, const int32_t *inst_of,
+                                                     int shift, const InstGrid *ig, const int32_t *cell_start,
                                                      const double4 *sorted_xyz,
-                                                     const int32_t *sorted_ids, double rs2,
+                                                     const int32_t *sorted_ids,
                                                      int64_t *cnt_or_off, int32_t *sidx,
                                                      int *minmax, DevError *err)
 {
@@ -168,6 +186,8 @@ __global__ void __launch_bounds__(256) search_kernel(int64_t n_pts, const double
     int mn = 1 << 30, mx = 0;
     for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + w; p < n_pts; p += warps) {
         const double x = pts[3 * p], y = pts[3 * p + 1], z = pts[3 * p + 2];
+        const InstGrid &g = ig[instance_of(inst_of, shift, p)];
+        const double rs2 = g.rs2;
         // cell of the point (may lie outside the grid: clamp the runs)
         int c[3];
         const double xs[3] = {x, y, z};
@@ -185,7 +205,7 @@ __global__ void __launch_bounds__(256) search_kernel(int64_t n_pts, const double
                 if (cy < 0 || cy >= g.n[1]) continue;
                 int xa = max(c[0] - 1, 0), xb = min(c[0] + 1, g.n[0] - 1);
                 if (xa > xb) continue;
-                int64_t row = (int64_t)g.n[0] * (cy + (int64_t)g.n[1] * cz);
+                int64_t row = g.cell_off + (int64_t)g.n[0] * (cy + (int64_t)g.n[1] * cz);
                 int b = cell_start[row + xa], e = cell_start[row + xb + 1];
                 for (int k0 = b; k0 < e; k0 += 32) {
                     int k = k0 + lane;
@@ -244,9 +264,9 @@ __global__ void __launch_bounds__(256) search_kernel(int64_t n_pts, const double
     }
 }
 
-rpim_status search_supports(rpim_pattern *p, int64_t n_pts, const double *pts, int64_t **soff_out,
-                            int32_t **sidx_out, int64_t *n_entries, int32_t *max_n, int32_t *min_n,
-                            cudaStream_t s, const char *tag)
+rpim_status search_supports(rpim_pattern *p, int64_t n_pts, const double *pts, const int32_t *inst_of, int shift,
+                            int64_t **soff_out, int32_t **sidx_out, int64_t *n_entries, int32_t *max_n,
+                            int32_t *min_n, cudaStream_t s, const char *tag)
 {
     int64_t *soff = nullptr, *tmp = nullptr;
     int32_t *sidx = nullptr;
@@ -257,9 +277,9 @@ rpim_status search_supports(rpim_pattern *p, int64_t n_pts, const double *pts, i
     int init[2] = {1 << 30, 0};
     RPIM_CUDA(cudaMemcpyAsync(mm, init, sizeof init, cudaMemcpyHostToDevice, s));
     int grid = grid_size(p->sm_count, 8, n_pts * 32, 256);
-    launch(tag, search_kernel<0>, grid, 256, 0, s, n_pts, pts, p->grid, p->cell_start,
-                                          (const double4 *)p->sorted_xyz, p->sorted_ids, p->rs2,
-                                          soff, nullptr, mm, p->err);
+    launch(tag, search_kernel<0>, grid, 256, 0, s, n_pts, pts, inst_of, shift, (const InstGrid *)p->ig,
+           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const int32_t *)p->sorted_ids, soff,
+           (int32_t *)nullptr, mm, p->err);
     RPIM_CUDA(cudaGetLastError());
     RPIM_CHECK(exclusive_scan(soff, n_pts, tmp, s));
     int hm[2];
@@ -276,9 +296,9 @@ rpim_status search_supports(rpim_pattern *p, int64_t n_pts, const double *pts, i
         return fail(RPIM_E_SUPPORT, buf);
     }
     RPIM_CHECK(dalloc(&sidx, ne, s));
-    launch(tag, search_kernel<1>, grid, 256, 0, s, n_pts, pts, p->grid, p->cell_start,
-                                          (const double4 *)p->sorted_xyz, p->sorted_ids, p->rs2,
-                                          soff, sidx, nullptr, p->err);
+    launch(tag, search_kernel<1>, grid, 256, 0, s, n_pts, pts, inst_of, shift, (const InstGrid *)p->ig,
+           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const int32_t *)p->sorted_ids, soff, sidx,
+           (int *)nullptr, p->err);
     RPIM_CUDA(cudaGetLastError());
     *soff_out = soff;
     *sidx_out = sidx;
@@ -299,8 +319,9 @@ rpim_status search_supports_into(rpim_pattern *p, int64_t n_pts, const double *p
     const int init[2] = {1 << 30, 0};
     RPIM_CUDA(cudaMemcpyAsync(minmax, init, sizeof init, cudaMemcpyHostToDevice, s));
     const int grid = grid_size(p->sm_count, 8, n_pts * 32, 256);
-    launch(tag, search_kernel<0>, grid, 256, 0, s, n_pts, pts, p->grid, p->cell_start,
-           (const double4 *)p->sorted_xyz, p->sorted_ids, p->rs2, soff, (int32_t *)nullptr, minmax, p->err);
+    launch(tag, search_kernel<0>, grid, 256, 0, s, n_pts, pts, (const int32_t *)nullptr, 0, (const InstGrid *)p->ig,
+           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const int32_t *)p->sorted_ids, soff,
+           (int32_t *)nullptr, minmax, p->err);
     RPIM_CUDA(cudaGetLastError());
     RPIM_CHECK(exclusive_scan(soff, n_pts, tmp, s));
     int hm[2];
@@ -319,8 +340,9 @@ rpim_status search_supports_into(rpim_pattern *p, int64_t n_pts, const double *p
                  (long long)cap);
         return fail(RPIM_E_ARG, buf);
     }
-    launch(tag, search_kernel<1>, grid, 256, 0, s, n_pts, pts, p->grid, p->cell_start,
-           (const double4 *)p->sorted_xyz, p->sorted_ids, p->rs2, soff, sidx, (int *)nullptr, p->err);
+    launch(tag, search_kernel<1>, grid, 256, 0, s, n_pts, pts, (const int32_t *)nullptr, 0, (const InstGrid *)p->ig,
+           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const int32_t *)p->sorted_ids, soff, sidx,
+           (int *)nullptr, p->err);
     RPIM_CUDA(cudaGetLastError());
     *n_entries = ne;
     *max_n = hm[1];
@@ -340,134 +362,198 @@ __global__ void entry_points_kernel(int64_t n_pts, const int64_t *soff, int32_t 
 // supports of the points whose support contains I; every such node lies
 // within 2 r_s of I, i.e. in the 5x5x5 cells around I's cell (cell edge >=
 // r_s). Those cells form 25 contiguous runs of the cell-ordered node list;
-// the union is marked in a shared-memory bitmap indexed by the position in
-// these runs, counted (pass 0), then extracted, sorted and written (pass 1).
+// the union is marked in a bitmap indexed by the position in these runs.
+// Pass 0 marks the bitmap in shared memory, counts it and keeps it in global
+// memory; pass 1 extracts the kept bitmap, sorts the ids and writes them.
 // ---------------------------------------------------------------------------
-template <int PASS>
-__global__ void pattern_kernel(int64_t n_nodes, Grid g, const int32_t *cell_start,
-                               const int32_t *node_cell, const uint32_t *node_cpk, const int32_t *node_rank,
-                               const int32_t *sorted_ids, const int64_t *toff, const int64_t *tent,
-                               const int32_t *entry_pt, const int64_t *soff, const int32_t *sidx,
-                               int64_t *rowcnt_or_ptr, int32_t *cols, int64_t *diag, int words,
-                               int list_cap, int *maxrow, DevError *err)
+// the 25 runs of cells (dy, dz in [-2, 2], dx in [-2, 2] contiguous) around
+// I's cell: start in the cell-ordered list and exclusive prefix of lengths
+__device__ __forceinline__ int cell_runs(const InstGrid &g, const int32_t *cell_start, int cx, int cy, int cz,
+                                         int lane, int *run_start, int *run_pre)
+{
+    if (lane < 25) {
+        const int dy = lane % 5 - 2, dz = lane / 5 - 2;
+        const int yy = cy + dy, zz = cz + dz;
+        int st = 0, len = 0;
+        if (yy >= 0 && yy < g.n[1] && zz >= 0 && zz < g.n[2]) {
+            const int xa = max(cx - 2, 0), xb = min(cx + 2, g.n[0] - 1);
+            const int64_t row = g.cell_off + (int64_t)g.n[0] * (yy + (int64_t)g.n[1] * zz);
+            st = cell_start[row + xa];
+            len = cell_start[row + xb + 1] - st;
+        }
+        run_start[lane] = st;
+        run_pre[lane + 1] = len;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        run_pre[0] = 0;
+        for (int r = 0; r < 25; r++) run_pre[r + 1] += run_pre[r];
+    }
+    __syncwarp();
+    return run_pre[25];
+}
+
+// pass 0. The (point, support entry) pairs of row I are walked flat: 32
+// incident points at a time, their supports concatenated and dealt to the
+// lanes, so that every lane has independent loads in flight (walking one
+// point at a time left most lanes idle behind a chain of dependent loads).
+__global__ void pattern_bits_kernel(int64_t n_nodes, const InstGrid *ig, const int32_t *node_inst,
+                                    const int32_t *cell_start, const uint32_t *node_cpk, const int32_t *node_rank,
+                                    const int64_t *toff, const int64_t *tent, const int32_t *entry_pt,
+                                    const int64_t *soff, const int32_t *sidx, int64_t *rowcnt, uint32_t *bm,
+                                    int words, int *maxrow, DevError *err)
 {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     uint32_t *bits = smem + (size_t)w * words;
-    int32_t *list = (int32_t *)(smem + (size_t)nw * words) + (size_t)w * list_cap;
     __shared__ int run_start[8][25], run_pre[8][26];
     const int64_t warps = (int64_t)gridDim.x * nw;
     int mrow = 0;
     for (int64_t I = (int64_t)blockIdx.x * nw + w; I < n_nodes; I += warps) {
-        const int32_t ci = node_cell[I];
-        const int cx = ci % g.n[0], cy = (ci / g.n[0]) % g.n[1], cz = ci / (g.n[0] * g.n[1]);
-        if (lane < 25) {
-            int dy = lane % 5 - 2, dz = lane / 5 - 2;
-            int yy = cy + dy, zz = cz + dz;
-            int st = 0, len = 0;
-            if (yy >= 0 && yy < g.n[1] && zz >= 0 && zz < g.n[2]) {
-                int xa = max(cx - 2, 0), xb = min(cx + 2, g.n[0] - 1);
-                int64_t row = (int64_t)g.n[0] * (yy + (int64_t)g.n[1] * zz);
-                st = cell_start[row + xa];
-                len = cell_start[row + xb + 1] - st;
-            }
-            run_start[w][lane] = st;
-            run_pre[w][lane + 1] = len;
-        }
-        __syncwarp();
-        if (lane == 0) {
-            run_pre[w][0] = 0;
-            for (int r = 0; r < 25; r++) run_pre[w][r + 1] += run_pre[w][r];
-        }
-        __syncwarp();
-        const int total = run_pre[w][25];
+        const InstGrid &g = ig[node_inst[I]];
+        const uint32_t ci = node_cpk[I];
+        const int cx = (int)(ci & 0x7FF), cy = (int)((ci >> 11) & 0x7FF), cz = (int)(ci >> 22);
+        const int total = cell_runs(g, cell_start, cx, cy, cz, lane, run_start[w], run_pre[w]);
         if (total > words * 32) {
             if (lane == 0) dev_fail(err, RPIM_E_SUPPORT, I);
             continue;
         }
-        for (int i = lane; i < (total + 31) / 32; i += 32) bits[i] = 0;
+        const int nwords = (total + 31) / 32;
+        for (int i = lane; i < nwords; i += 32) bits[i] = 0;
         __syncwarp();
-        for (int64_t t = toff[I]; t < toff[I + 1]; t++) {
-            const int32_t pt = entry_pt[tent[t]];
-            for (int64_t f = soff[pt] + lane; f < soff[pt + 1]; f += 32) {
-                const int32_t J = sidx[f];
-                const uint32_t cj = node_cpk[J];
-                const int jx = (int)(cj & 0x7FF), jy = (int)((cj >> 11) & 0x7FF), jz = (int)(cj >> 22);
-                const int dx = jx - cx, dy = jy - cy, dz = jz - cz;
-                if (dx < -2 || dx > 2 || dy < -2 || dy > 2 || dz < -2 || dz > 2) {
-                    dev_fail(err, RPIM_E_ARG, I);
-                    continue;
+        const int64_t t_end = toff[I + 1];
+        for (int64_t t0 = toff[I]; t0 < t_end; t0 += 32) {
+            const int nt = (int)min((int64_t)32, t_end - t0);
+            int64_t s0 = 0;
+            int len = 0;
+            if (lane < nt) {
+                const int32_t pt = entry_pt[tent[t0 + lane]];
+                s0 = soff[pt];
+                len = (int)(soff[pt + 1] - s0);
+            }
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int excl = incl - len;     // lanes >= nt hold the total
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            for (int e0 = 0; e0 < tot; e0 += 32) {
+                const int e = e0 + lane;
+                int q = 0;                   // last point q with excl_q <= e
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int ex = __shfl_sync(0xffffffffu, excl, q + step);
+                    if (ex <= e) q += step;
                 }
-                const int r = (dy + 2) + 5 * (dz + 2);
-                const int b = run_pre[w][r] + (node_rank[J] - run_start[w][r]);
-                atomicOr(&bits[b >> 5], 1u << (b & 31));
+                const int64_t sq = __shfl_sync(0xffffffffu, s0, q);
+                const int eq = __shfl_sync(0xffffffffu, excl, q);
+                if (e < tot) {
+                    const int32_t J = sidx[sq + (e - eq)];
+                    const uint32_t cj = node_cpk[J];
+                    const int dx = (int)(cj & 0x7FF) - cx, dy = (int)((cj >> 11) & 0x7FF) - cy,
+                              dz = (int)(cj >> 22) - cz;
+                    if (dx < -2 || dx > 2 || dy < -2 || dy > 2 || dz < -2 || dz > 2) {
+                        dev_fail(err, RPIM_E_ARG, I);
+                    } else {
+                        const int r = (dy + 2) + 5 * (dz + 2);
+                        const int bi = run_pre[w][r] + (node_rank[J] - run_start[w][r]);
+                        atomicOr(&bits[bi >> 5], 1u << (bi & 31));
+                    }
+                }
             }
         }
         __syncwarp();
-        int nwords = (total + 31) / 32;
-        if (PASS == 0) {
-            int c = 0;
-            for (int i = lane; i < nwords; i += 32) c += __popc(bits[i]);
-            for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-            if (lane == 0) rowcnt_or_ptr[I] = c;
-            mrow = max(mrow, c);
-        } else {
-            // extract in bitmap order: words in chunks of 32 lanes
-            int base = 0;
-            for (int i0 = 0; i0 < nwords; i0 += 32) {
-                int i = i0 + lane;
-                uint32_t word = i < nwords ? bits[i] : 0u;
-                int pc = __popc(word), incl = pc;
-                for (int o = 1; o < 32; o <<= 1) {
-                    int v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                int pos = base + incl - pc;
-                while (word) {
-                    int bit = __ffs(word) - 1;
-                    word &= word - 1;
-                    int b = i * 32 + bit;
-                    int r = 0, hi = 25;  // run_pre[r] <= b < run_pre[r + 1]
-                    while (hi - r > 1) {
-                        const int mid = (r + hi) >> 1;
-                        if (run_pre[w][mid] <= b) r = mid; else hi = mid;
-                    }
-                    int spos = run_start[w][r] + (b - run_pre[w][r]);
-                    if (pos < list_cap) list[pos] = sorted_ids[spos];
-                    pos++;
-                }
-                base += __shfl_sync(0xffffffffu, incl, 31);
-            }
-            const int cnt = base;
-            __syncwarp();
-            int p2 = 1;
-            while (p2 < cnt) p2 <<= 1;
-            for (int i = cnt + lane; i < p2; i += 32) list[i] = INT32_MAX;
-            __syncwarp();
-            for (int k = 2; k <= p2; k <<= 1)
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    for (int i = lane; i < p2; i += 32) {
-                        int ixj = i ^ j;
-                        if (ixj > i) {
-                            int32_t a = list[i], bb = list[ixj];
-                            bool up = (i & k) == 0;
-                            if ((a > bb) == up) { list[i] = bb; list[ixj] = a; }
-                        }
-                    }
-                    __syncwarp();
-                }
-            const int64_t o = rowcnt_or_ptr[I];
-            for (int i = lane; i < cnt; i += 32) {
-                cols[o + i] = list[i];
-                if (list[i] == (int32_t)I) diag[I] = o + i;
-            }
-            __syncwarp();
+        int c = 0;
+        uint32_t *out = bm + (size_t)I * words;
+        for (int i = lane; i < nwords; i += 32) {
+            const uint32_t v = bits[i];
+            c += __popc(v);
+            out[i] = v;
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if (lane == 0) rowcnt[I] = c;
+        mrow = max(mrow, c);
+        __syncwarp();
     }
-    if (PASS == 0) {
-        for (int o = 16; o > 0; o >>= 1) mrow = max(mrow, __shfl_down_sync(0xffffffffu, mrow, o));
-        if (lane == 0) atomicMax(maxrow, mrow);
+    for (int o = 16; o > 0; o >>= 1) mrow = max(mrow, __shfl_down_sync(0xffffffffu, mrow, o));
+    if (lane == 0) atomicMax(maxrow, mrow);
+}
+
+// pass 1: the kept bitmap of row I in bitmap order (cell runs, ids ascending
+// inside a cell), mapped to node ids, sorted (bitonic, shared memory) and
+// written at rowptr[I]
+__global__ void pattern_cols_kernel(int64_t n_nodes, const InstGrid *ig, const int32_t *node_inst,
+                                    const int32_t *cell_start, const uint32_t *node_cpk, const int32_t *sorted_ids,
+                                    const uint32_t *bm, int words, const int64_t *rowptr, int32_t *cols,
+                                    int64_t *diag, int list_cap)
+{
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    int32_t *list = (int32_t *)smem + (size_t)w * list_cap;
+    __shared__ int run_start[8][25], run_pre[8][26];
+    const int64_t warps = (int64_t)gridDim.x * nw;
+    for (int64_t I = (int64_t)blockIdx.x * nw + w; I < n_nodes; I += warps) {
+        const InstGrid &g = ig[node_inst[I]];
+        const uint32_t ci = node_cpk[I];
+        const int cx = (int)(ci & 0x7FF), cy = (int)((ci >> 11) & 0x7FF), cz = (int)(ci >> 22);
+        const int total = cell_runs(g, cell_start, cx, cy, cz, lane, run_start[w], run_pre[w]);
+        const int nwords = (total + 31) / 32;
+        const uint32_t *in = bm + (size_t)I * words;
+        int base = 0;
+        for (int i0 = 0; i0 < nwords; i0 += 32) {
+            const int i = i0 + lane;
+            uint32_t word = i < nwords ? in[i] : 0u;
+            const int pc = __popc(word);
+            int incl = pc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            int pos = base + incl - pc;
+            while (word) {
+                const int bit = __ffs(word) - 1;
+                word &= word - 1;
+                const int bb = i * 32 + bit;
+                int r = 0, hi = 25;  // run_pre[r] <= bb < run_pre[r + 1]
+                while (hi - r > 1) {
+                    const int mid = (r + hi) >> 1;
+                    if (run_pre[w][mid] <= bb) r = mid; else hi = mid;
+                }
+                if (pos < list_cap) list[pos] = sorted_ids[run_start[w][r] + (bb - run_pre[w][r])];
+                pos++;
+            }
+            base += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        const int cnt = min(base, list_cap);
+        __syncwarp();
+        int p2 = 1;
+        while (p2 < cnt) p2 <<= 1;
+        for (int i = cnt + lane; i < p2; i += 32) list[i] = INT32_MAX;
+        __syncwarp();
+        for (int k = 2; k <= p2; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < p2; i += 32) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const int32_t a = list[i], c = list[ixj];
+                        const bool up = (i & k) == 0;
+                        if ((a > c) == up) { list[i] = c; list[ixj] = a; }
+                    }
+                }
+                __syncwarp();
+            }
+        const int64_t o = rowptr[I];
+        for (int i = lane; i < cnt; i += 32) {
+            cols[o + i] = list[i];
+            if (list[i] == (int32_t)I) diag[I] = o + i;
+        }
+        __syncwarp();
     }
 }
 
@@ -484,7 +570,12 @@ static void pattern_release(rpim_pattern *p)
     dfree(p->tent, s); dfree(p->rowptr, s); dfree(p->cols, s); dfree(p->diag, s);
     dfree(p->phi, s); dfree(p->lamw, s); dfree(p->err, s); dfree(p->scal, s); dfree(p->series, s);
     dfree(p->ws.buf, s);
+    dfree(p->ig, s); dfree(p->node_inst, s); dfree(p->bucket_order, s);
+    dfree(p->seg_row, s); dfree(p->seg_inst, s); dfree(p->inst_seg, s);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    p->cap_stream = nullptr;
     p->ws.doubles = 0;
+    p->n_seg = 0;
 }
 
 extern "C" rpim_status rpim_pattern_free(rpim_pattern *p)
@@ -559,11 +650,44 @@ extern "C" rpim_status rpim_pattern_copy_points(const rpim_pattern *p, double *x
     return RPIM_OK;
 }
 
+// support-size bucket of every integration point; buckets group points for
+// the shape kernel, whose shared memory per point grows with the support
+__global__ void bucket_count_kernel(int64_t n_pts, const int64_t *soff, const int32_t *bounds, int nb,
+                                    unsigned long long *count, int *bmax)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_pts;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(soff[g + 1] - soff[g]);
+        int b = 0;
+        while (b < nb - 1 && n > bounds[b]) b++;
+        atomicAdd(&count[b], 1ull);
+        atomicMax(&bmax[b], n);
+    }
+}
+
+__global__ void bucket_fill_kernel(int64_t n_pts, const int64_t *soff, const int32_t *bounds, int nb,
+                                   const int64_t *start, unsigned long long *cursor, int32_t *order)
+{
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_pts;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(soff[g + 1] - soff[g]);
+        int b = 0;
+        while (b < nb - 1 && n > bounds[b]) b++;
+        order[start[b] + (int64_t)atomicAdd(&cursor[b], 1ull)] = (int32_t)g;
+    }
+}
+
+// upper support size of each bucket (the last one is open-ended)
+static const int32_t kBucketBounds[] = {40, 56, 72, 96, 128, 160, 1 << 30};
+static const int kBuckets = 7;
+
 static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, const double *hi)
 {
     cudaStream_t s = p->stream;
     const int64_t n = p->n_nodes;
-    RPIM_CHECK(build_kernel_series(p->prm.alpha_c, p->prm.alpha_s, p->prm.q, &p->series_host));
+    const int ni = p->n_inst;
+    // the series for the largest support radius is valid for all instances
+    RPIM_CHECK(build_kernel_series(p->prm.alpha_c, p->series_alpha_s, p->prm.q, &p->series_host));
     RPIM_CHECK(dalloc(&p->series, 1, s));
     RPIM_CUDA(cudaMemcpyAsync(p->series, &p->series_host, sizeof(KernelSeries), cudaMemcpyHostToDevice, s));
     RPIM_CHECK(dalloc(&p->err, 1, s));
@@ -571,6 +695,10 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     RPIM_CHECK(dalloc(&p->scal, 16, s));
     RPIM_CHECK(dalloc(&p->xyz, 3 * n, s));
     RPIM_CUDA(cudaMemcpyAsync(p->xyz, xyz, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    RPIM_CHECK(dalloc(&p->ig, ni, s));
+    RPIM_CUDA(cudaMemcpyAsync(p->ig, p->ig_host.data(), ni * sizeof(InstGrid), cudaMemcpyHostToDevice, s));
+    RPIM_CHECK(dalloc(&p->node_inst, n, s));
+    launch("node_inst", node_inst_kernel, ni, 256, 0, s, (const InstGrid *)p->ig, p->node_inst);
 
     // integration points
     p->n_points = 8 * n;
@@ -578,57 +706,61 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     RPIM_CHECK(dalloc(&p->wj, p->n_points, s));
     launch("gauss_points", gauss_points_kernel, grid_size(p->sm_count, 8, p->n_points, 256), 256, 0, s, n, lo, hi, p->pts, p->wj);
 
-    // bounding box -> grid with cell edge >= r_s
+    // bounding box of each instance -> its grid, cell edge >= its r_s
     unsigned long long *bb = nullptr;
     int *bad = nullptr;
-    RPIM_CHECK(dalloc(&bb, 6, s));
+    RPIM_CHECK(dalloc(&bb, 6 * ni, s));
     RPIM_CHECK(dalloc(&bad, 1, s));
-    unsigned long long init[6] = {~0ull, ~0ull, ~0ull, 0, 0, 0};
-    RPIM_CUDA(cudaMemcpyAsync(bb, init, sizeof init, cudaMemcpyHostToDevice, s));
     RPIM_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-    launch("bbox", bbox_kernel, grid_size(p->sm_count, 4, n, 256), 256, 0, s, n, xyz, bb, bad);
-    unsigned long long hb[6];
+    launch("bbox", bbox_kernel, ni, 256, 0, s, (const InstGrid *)p->ig, xyz, bb, bad);
+    std::vector<unsigned long long> hb(6 * (size_t)ni);
     int hbad = 0;
-    RPIM_CUDA(cudaMemcpyAsync(hb, bb, sizeof hb, cudaMemcpyDeviceToHost, s));
+    RPIM_CUDA(cudaMemcpyAsync(hb.data(), bb, hb.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     RPIM_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, s));
     RPIM_CUDA(cudaStreamSynchronize(s));
     dfree(bb, s);
     dfree(bad, s);
     if (hbad) return fail(RPIM_E_NONFINITE, "non-finite node coordinate");
-    double bmin[3], bmax[3];
-    for (int k = 0; k < 3; k++) {
-        auto un = [](unsigned long long u) {
-            unsigned long long b = (u & 0x8000000000000000ull) ? (u & 0x7FFFFFFFFFFFFFFFull) : ~u;
-            double d;
-            memcpy(&d, &b, 8);
-            return d;
-        };
-        bmin[k] = un(hb[k]);
-        bmax[k] = un(hb[3 + k]);
-    }
-    const double rs = sqrt(p->rs2);
-    double edge = rs * (1.0 + 1e-9);
-    for (;;) {
-        int64_t cells = 1;
-        bool ok = true;
+    auto un = [](unsigned long long u) {
+        unsigned long long b = (u & 0x8000000000000000ull) ? (u & 0x7FFFFFFFFFFFFFFFull) : ~u;
+        double d;
+        memcpy(&d, &b, 8);
+        return d;
+    };
+    int64_t cell_off = 0;
+    for (int i = 0; i < ni; i++) {
+        InstGrid &g = p->ig_host[i];
+        double bmin[3], bmax[3];
         for (int k = 0; k < 3; k++) {
-            double span = bmax[k] - bmin[k];
-            int64_t nk = (int64_t)floor(span / edge) + 1;
-            if (nk > (k == 2 ? 1023 : 2047)) ok = false;
-            p->grid.n[k] = (int)std::min<int64_t>(nk, 1 << 20);
-            cells *= p->grid.n[k];
+            bmin[k] = un(hb[6 * i + k]);
+            bmax[k] = un(hb[6 * i + 3 + k]);
         }
-        if (ok && cells <= (int64_t)1 << 28) {
-            p->grid.cells = cells;
-            break;
+        double edge = sqrt(g.rs2) * (1.0 + 1e-9);
+        int64_t cells = 1;
+        for (;;) {
+            cells = 1;
+            bool ok = true;
+            for (int k = 0; k < 3; k++) {
+                double span = bmax[k] - bmin[k];
+                int64_t nk = (int64_t)floor(span / edge) + 1;
+                if (nk > (k == 2 ? 1023 : 2047)) ok = false;
+                g.n[k] = (int)std::min<int64_t>(nk, 1 << 20);
+                cells *= g.n[k];
+            }
+            if (ok && cells <= (int64_t)1 << 28) break;
+            edge *= 1.25;
         }
-        edge *= 1.25;
+        for (int k = 0; k < 3; k++) g.lo[k] = bmin[k];
+        g.inv_edge = 1.0 / edge;
+        g.cell_off = cell_off;
+        cell_off += cells;
     }
-    for (int k = 0; k < 3; k++) p->grid.lo[k] = bmin[k];
-    p->grid.inv_edge = 1.0 / edge;
+    if (cell_off > INT32_MAX) return fail(RPIM_E_ARG, "too many grid cells");
+    p->total_cells = cell_off;
+    RPIM_CUDA(cudaMemcpyAsync(p->ig, p->ig_host.data(), ni * sizeof(InstGrid), cudaMemcpyHostToDevice, s));
 
-    // cell list (cell-major order, ids ascending inside a cell)
-    const int64_t cells = p->grid.cells;
+    // cell list (cell-major order per instance, ids ascending inside a cell)
+    const int64_t cells = p->total_cells;
     int32_t *cursor = nullptr;
     int64_t *tmp = nullptr;
     int *dmax = nullptr;
@@ -644,8 +776,8 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     RPIM_CUDA(cudaMemsetAsync(p->cell_start, 0, (cells + 1) * sizeof(int32_t), s));
     RPIM_CUDA(cudaMemsetAsync(cursor, 0, (cells + 1) * sizeof(int32_t), s));
     RPIM_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
-    launch("bin_nodes", bin_nodes, grid_size(p->sm_count, 4, n, 256), 256, 0, s, n, xyz, p->grid, p->node_cell,
-           p->node_cpk, p->cell_start);
+    launch("bin_nodes", bin_nodes, grid_size(p->sm_count, 4, n, 256), 256, 0, s, n, xyz, (const InstGrid *)p->ig,
+           (const int32_t *)p->node_inst, p->node_cell, p->node_cpk, p->cell_start);
     RPIM_CHECK(exclusive_scan32(p->cell_start, cells, tmp, s));
     launch("fill_cells", fill_cells, grid_size(p->sm_count, 4, n, 256), 256, 0, s, n, p->node_cell, p->cell_start, cursor, p->sorted_ids);
     launch("finish_cells", finish_cells, grid_size(p->sm_count, 4, cells, 128), 128, 0, s, cells, p->cell_start, p->sorted_ids, xyz,
@@ -656,12 +788,53 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     dfree(tmp, s);
     dfree(dmax, s);
 
-    // supports of the integration points
-    RPIM_CHECK(search_supports(p, p->n_points, p->pts, &p->soff, &p->sidx, &p->n_entries,
+    // supports of the integration points (point g belongs to node g/8)
+    RPIM_CHECK(search_supports(p, p->n_points, p->pts, p->node_inst, 3, &p->soff, &p->sidx, &p->n_entries,
                                &p->max_support, &p->min_support, s, "search"));
     RPIM_CHECK(dalloc(&p->entry_pt, p->n_entries, s));
     launch("entry_points", entry_points_kernel, grid_size(p->sm_count, 8, p->n_points * 32, 256), 256, 0, s, p->n_points, p->soff, p->entry_pt);
     RPIM_CHECK(build_incidence(n, p->n_entries, p->sidx, &p->toff, &p->tent, &p->max_incident, s, p->sm_count));
+
+    // support-size buckets
+    {
+        int32_t *dbounds = nullptr;
+        unsigned long long *dcount = nullptr;
+        int64_t *dstart = nullptr;
+        int *dbmax = nullptr;
+        RPIM_CHECK(dalloc(&dbounds, kBuckets, s));
+        RPIM_CHECK(dalloc(&dcount, 2 * kBuckets, s));
+        RPIM_CHECK(dalloc(&dstart, kBuckets, s));
+        RPIM_CHECK(dalloc(&dbmax, kBuckets, s));
+        RPIM_CHECK(dalloc(&p->bucket_order, p->n_points, s));
+        RPIM_CUDA(cudaMemcpyAsync(dbounds, kBucketBounds, sizeof kBucketBounds, cudaMemcpyHostToDevice, s));
+        RPIM_CUDA(cudaMemsetAsync(dcount, 0, 2 * kBuckets * sizeof(unsigned long long), s));
+        RPIM_CUDA(cudaMemsetAsync(dbmax, 0, kBuckets * sizeof(int), s));
+        const int gsz = grid_size(p->sm_count, 4, p->n_points, 256);
+        launch("bucket_count", bucket_count_kernel, gsz, 256, 0, s, p->n_points, (const int64_t *)p->soff,
+               (const int32_t *)dbounds, kBuckets, dcount, dbmax);
+        unsigned long long hc[kBuckets];
+        int hm[kBuckets];
+        RPIM_CUDA(cudaMemcpyAsync(hc, dcount, sizeof hc, cudaMemcpyDeviceToHost, s));
+        RPIM_CUDA(cudaMemcpyAsync(hm, dbmax, sizeof hm, cudaMemcpyDeviceToHost, s));
+        RPIM_CUDA(cudaStreamSynchronize(s));
+        int64_t hs[kBuckets], acc = 0;
+        p->bucket_count.assign(kBuckets, 0);
+        p->bucket_nc.assign(kBuckets, 0);
+        for (int b = 0; b < kBuckets; b++) {
+            hs[b] = acc;
+            acc += (int64_t)hc[b];
+            p->bucket_count[b] = (int64_t)hc[b];
+            p->bucket_nc[b] = hm[b];
+        }
+        RPIM_CUDA(cudaMemcpyAsync(dstart, hs, sizeof hs, cudaMemcpyHostToDevice, s));
+        launch("bucket_fill", bucket_fill_kernel, gsz, 256, 0, s, p->n_points, (const int64_t *)p->soff,
+               (const int32_t *)dbounds, kBuckets, (const int64_t *)dstart, dcount + kBuckets, p->bucket_order);
+        RPIM_CUDA(cudaGetLastError());
+        dfree(dbounds, s);
+        dfree(dcount, s);
+        dfree(dstart, s);
+        dfree(dbmax, s);
+    }
 
     // BSR pattern
     const int words = (125 * p->max_cell + 31) / 32 + 1;
@@ -670,14 +843,22 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     RPIM_CHECK(dalloc(&dmax, 1, s));
     RPIM_CHECK(dalloc(&tmp, scan_tmp_size(n), s));
     RPIM_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
+    uint32_t *bm = nullptr;   // kept bitmaps of pass 0, [n][words]
+    RPIM_CHECK(dalloc(&bm, (int64_t)n * words, s));
     {
         const int wpb = 8;
         size_t smem = (size_t)wpb * words * 4;
+        if (smem > 227 * 1024) {
+            dfree(bm, s);
+            return fail(RPIM_E_SUPPORT, "pattern bitmap too large for shared memory (too many nodes per cell)");
+        }
         if (smem > 48 * 1024)
-            RPIM_CUDA(cudaFuncSetAttribute(pattern_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        launch("pattern_count", pattern_kernel<0>, grid_size(p->sm_count, 4, n, wpb), wpb * 32, smem, s, 
-            n, p->grid, p->cell_start, p->node_cell, p->node_cpk, p->node_rank, p->sorted_ids, p->toff, p->tent,
-            p->entry_pt, p->soff, p->sidx, p->rowptr, nullptr, nullptr, words, 0, dmax, p->err);
+            RPIM_CUDA(cudaFuncSetAttribute(pattern_bits_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        launch("pattern_count", pattern_bits_kernel, grid_size(p->sm_count, 4, n, wpb), wpb * 32, smem, s,
+               n, (const InstGrid *)p->ig, (const int32_t *)p->node_inst, (const int32_t *)p->cell_start,
+               (const uint32_t *)p->node_cpk, (const int32_t *)p->node_rank, (const int64_t *)p->toff,
+               (const int64_t *)p->tent, (const int32_t *)p->entry_pt, (const int64_t *)p->soff,
+               (const int32_t *)p->sidx, p->rowptr, bm, words, dmax, p->err);
         RPIM_CUDA(cudaGetLastError());
     }
     RPIM_CHECK(exclusive_scan(p->rowptr, n, tmp, s));
@@ -687,47 +868,79 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     RPIM_CUDA(cudaStreamSynchronize(s));
     dfree(tmp, s);
     dfree(dmax, s);
-    RPIM_CHECK(check_device_error(p, "pattern"));
+    rpim_status st = check_device_error(p, "pattern");
+    if (st != RPIM_OK) {
+        dfree(bm, s);
+        return st;
+    }
     p->max_row = hmax;
-    RPIM_CHECK(dalloc(&p->cols, p->nnzb, s));
-    {
+    st = dalloc(&p->cols, p->nnzb, s);
+    if (st == RPIM_OK) {
         int p2 = 1;
         while (p2 < hmax) p2 <<= 1;
         int wpb = 8;
-        size_t per = (size_t)words * 4 + (size_t)p2 * 4;
+        const size_t per = (size_t)p2 * 4;
         while (wpb > 1 && wpb * per > 200 * 1024) wpb >>= 1;
-        size_t smem = wpb * per;
-        if (smem > 227 * 1024) return fail(RPIM_E_SUPPORT, "pattern row too long for shared memory");
-        RPIM_CUDA(cudaFuncSetAttribute(pattern_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        launch("pattern_fill", pattern_kernel<1>, grid_size(p->sm_count, 4, n, wpb), wpb * 32, smem, s, 
-            n, p->grid, p->cell_start, p->node_cell, p->node_cpk, p->node_rank, p->sorted_ids, p->toff, p->tent,
-            p->entry_pt, p->soff, p->sidx, p->rowptr, p->cols, p->diag, words, p2, nullptr, p->err);
-        RPIM_CUDA(cudaGetLastError());
+        const size_t smem = wpb * per;
+        if (smem > 227 * 1024) st = fail(RPIM_E_SUPPORT, "pattern row too long for shared memory");
+        else if (cudaFuncSetAttribute(pattern_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                 cudaSuccess)
+            st = fail(RPIM_E_CUDA, "pattern: shared memory attribute");
+        else {
+            launch("pattern_fill", pattern_cols_kernel, grid_size(p->sm_count, 4, n, wpb), wpb * 32, smem, s,
+                   n, (const InstGrid *)p->ig, (const int32_t *)p->node_inst, (const int32_t *)p->cell_start,
+                   (const uint32_t *)p->node_cpk, (const int32_t *)p->sorted_ids, (const uint32_t *)bm, words,
+                   (const int64_t *)p->rowptr, p->cols, p->diag, p2);
+            if (cudaGetLastError() != cudaSuccess) st = fail(RPIM_E_CUDA, "pattern fill launch");
+        }
     }
+    dfree(bm, s);
+    RPIM_CHECK(st);
     RPIM_CHECK(check_device_error(p, "pattern"));
     return RPIM_OK;
 }
 
-extern "C" rpim_status rpim_build_pattern(int64_t n_nodes, const double *xyz, const double *cell_lo,
-                                          const double *cell_hi, const rpim_params *params,
-                                          rpim_stream_t stream, rpim_pattern **out,
-                                          int64_t *nnz_blocks)
+static rpim_status create(int32_t n_inst, const rpim_instance *inst, const double *xyz, const double *cell_lo,
+                          const double *cell_hi, double alpha_c, double q, int32_t gauss_order, rpim_stream_t stream,
+                          rpim_pattern **out, int64_t *nnz_blocks)
 {
     if (!out) return fail(RPIM_E_ARG, "out is null");
     *out = nullptr;
-    if (n_nodes < 4 || n_nodes > INT32_MAX / 8 || !xyz || !cell_lo || !cell_hi || !params)
-        return fail(RPIM_E_ARG, "bad node count or null pointer");
-    if (params->gauss_order != 2) return fail(RPIM_E_ARG, "only gauss_order = 2 is implemented");
-    if (!(params->h > 0) || !(params->alpha_s > 0) || !(params->alpha_c > 0) || !(params->q > 0))
-        return fail(RPIM_E_ARG, "non-positive RPIM parameter");
+    if (n_inst < 1 || !inst || !xyz || !cell_lo || !cell_hi) return fail(RPIM_E_ARG, "bad instance list or null pointer");
+    if (gauss_order != 2) return fail(RPIM_E_ARG, "only gauss_order = 2 is implemented");
+    if (!(alpha_c > 0) || !(q > 0)) return fail(RPIM_E_ARG, "non-positive RPIM parameter");
+    int64_t n = 0;
+    double as_max = 0.0;
+    for (int i = 0; i < n_inst; i++) {
+        if (inst[i].n_nodes < 4 || !(inst[i].h > 0) || !(inst[i].alpha_s > 0))
+            return fail(RPIM_E_ARG, "instance with fewer than 4 nodes or a non-positive parameter");
+        n += inst[i].n_nodes;
+        as_max = std::max(as_max, inst[i].alpha_s);
+    }
+    if (n > INT32_MAX / 8) return fail(RPIM_E_ARG, "too many nodes");
     rpim_pattern *p = new (std::nothrow) rpim_pattern();
     if (!p) return fail(RPIM_E_OOM, "host allocation");
     p->stream = (cudaStream_t)stream;
-    p->prm = *params;
-    double rs = params->alpha_s * params->h;
-    p->rs2 = rs * rs;
-    p->inv_h = 1.0 / params->h;
-    p->n_nodes = n_nodes;
+    p->prm.alpha_s = inst[0].alpha_s;
+    p->prm.h = inst[0].h;
+    p->prm.alpha_c = alpha_c;
+    p->prm.q = q;
+    p->prm.gauss_order = gauss_order;
+    p->series_alpha_s = as_max;
+    p->n_inst = n_inst;
+    p->n_nodes = n;
+    p->ig_host.resize(n_inst);
+    int64_t nb = 0;
+    for (int i = 0; i < n_inst; i++) {
+        InstGrid &g = p->ig_host[i];
+        memset(&g, 0, sizeof g);
+        const double rs = inst[i].alpha_s * inst[i].h;
+        g.rs2 = rs * rs;
+        g.inv_h = 1.0 / inst[i].h;
+        g.node_begin = nb;
+        nb += inst[i].n_nodes;
+        g.node_end = nb;
+    }
     cudaGetDevice(&p->device);
     cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
     {
@@ -748,4 +961,26 @@ extern "C" rpim_status rpim_build_pattern(int64_t n_nodes, const double *xyz, co
     if (nnz_blocks) *nnz_blocks = p->nnzb;
     *out = p;
     return RPIM_OK;
+}
+
+extern "C" rpim_status rpim_build_pattern(int64_t n_nodes, const double *xyz, const double *cell_lo,
+                                          const double *cell_hi, const rpim_params *params,
+                                          rpim_stream_t stream, rpim_pattern **out, int64_t *nnz_blocks)
+{
+    if (out) *out = nullptr;
+    if (!params) return fail(RPIM_E_ARG, "params is null");
+    if (n_nodes < 4 || n_nodes > INT32_MAX / 8 || !xyz || !cell_lo || !cell_hi)
+        return fail(RPIM_E_ARG, "bad node count or null pointer");
+    if (!(params->h > 0) || !(params->alpha_s > 0)) return fail(RPIM_E_ARG, "non-positive RPIM parameter");
+    rpim_instance one{n_nodes, params->alpha_s, params->h};
+    return create(1, &one, xyz, cell_lo, cell_hi, params->alpha_c, params->q, params->gauss_order, stream, out,
+                  nnz_blocks);
+}
+
+extern "C" rpim_status rpim_build_pattern_batched(int32_t n_inst, const rpim_instance *inst, const double *xyz,
+                                                  const double *cell_lo, const double *cell_hi, double alpha_c,
+                                                  double q, int32_t gauss_order, rpim_stream_t stream,
+                                                  rpim_pattern **out, int64_t *nnz_blocks)
+{
+    return create(n_inst, inst, xyz, cell_lo, cell_hi, alpha_c, q, gauss_order, stream, out, nnz_blocks);
 }

@@ -195,9 +195,12 @@ __device__ __forceinline__ void tri_decode(int u, int &i, int &j)
 // loop over the group's G*32 threads; the phases are separated by a named
 // barrier of the group. Groups of one block are independent.
 __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double *__restrict__ pts,
+                                                     const int32_t *__restrict__ inst_of, int shift,
+                                                     const InstGrid *__restrict__ ig,
+                                                     const int32_t *__restrict__ order,
                                                      const int64_t *__restrict__ soff,
                                                      const int32_t *__restrict__ sidx,
-                                                     const double *__restrict__ xyz, double inv_h,
+                                                     const double *__restrict__ xyz,
                                                      const KernelSeries *__restrict__ ks_g,
                                                      double *__restrict__ phi, int NC, int G, DevError *err)
 {
@@ -219,7 +222,9 @@ __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double
     const double c2 = ks.c2;
     const int64_t stride = (int64_t)gridDim.x * ppb;
 
-    for (int64_t p = (int64_t)blockIdx.x * ppb + grp; p < n_pts; p += stride) {
+    for (int64_t pk = (int64_t)blockIdx.x * ppb + grp; pk < n_pts; pk += stride) {
+        const int64_t p = order ? (int64_t)order[pk] : pk;
+        const double inv_h = ig[instance_of(inst_of, shift, p)].inv_h;
         const int64_t base = soff[p];
         const int n = (int)(soff[p + 1] - base);
         if (n < 4 || n > NC) {
@@ -548,8 +553,9 @@ __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double
     }
 }
 
-rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, const int64_t *soff,
-                            const int32_t *sidx, int32_t max_n, double *phi, cudaStream_t s, const char *tag)
+rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, const int32_t *inst_of, int shift,
+                            const int32_t *order, const int64_t *soff, const int32_t *sidx, int32_t max_n,
+                            double *phi, cudaStream_t s, const char *tag)
 {
     if (n_pts == 0) return RPIM_OK;
     if (max_n > RPIM_MAX_SUPPORT) return fail(RPIM_E_SUPPORT, "support larger than RPIM_MAX_SUPPORT");
@@ -563,9 +569,23 @@ rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, c
     RPIM_CUDA(cudaFuncSetAttribute(shape_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int64_t blocks = std::min<int64_t>((int64_t)p->sm_count, (n_pts + ppb - 1) / ppb);
     if (blocks < 1) blocks = 1;
-    launch(tag, shape_kernel, (unsigned)blocks, ppb * G * 32, smem, s, n_pts, pts, soff, sidx,
-           (const double *)p->xyz, p->inv_h, (const KernelSeries *)p->series, phi, NC, G, p->err);
+    launch(tag, shape_kernel, (unsigned)blocks, ppb * G * 32, smem, s, n_pts, pts, inst_of, shift,
+           (const InstGrid *)p->ig, order, soff, sidx, (const double *)p->xyz, (const KernelSeries *)p->series, phi,
+           NC, G, p->err);
     RPIM_CUDA(cudaGetLastError());
+    return RPIM_OK;
+}
+
+rpim_status shape_functions_all(rpim_pattern *p, double *phi, cudaStream_t s)
+{
+    int64_t start = 0;
+    for (size_t b = 0; b < p->bucket_count.size(); b++) {
+        const int64_t cnt = p->bucket_count[b];
+        if (cnt > 0)
+            RPIM_CHECK(shape_functions(p, cnt, p->pts, p->node_inst, 3, p->bucket_order + start, p->soff, p->sidx,
+                                       p->bucket_nc[b], phi, s, "shape"));
+        start += cnt;
+    }
     return RPIM_OK;
 }
 

@@ -3,6 +3,8 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -23,29 +25,33 @@ __device__ __forceinline__ double unord(unsigned long long u)
 // penalty: alpha = scale * max_i K_ii; K_dd += alpha, f_d += alpha * value
 // (one thread per constrained DOF, Sec. 2)
 // ---------------------------------------------------------------------------
+// per instance: largest scalar diagonal entry (order-preserving integer max,
+// so the result does not depend on the order of the updates), then alpha
 struct PenaltyState {
     unsigned long long kmax;
     double alpha;
 };
 
-__global__ void max_diag_kernel(int64_t n_nodes, const int64_t *diag, const double *K, PenaltyState *st)
+__global__ void max_diag_kernel(int64_t n_nodes, const int64_t *diag, const int32_t *node_inst, const double *K,
+                                PenaltyState *st)
 {
-    unsigned long long m = 0;
     for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < n_nodes;
          I += (int64_t)gridDim.x * blockDim.x) {
         const double *b = K + 9 * diag[I];
-        m = max(m, max(ord(b[0]), max(ord(b[4]), ord(b[8]))));
+        const unsigned long long m = max(ord(b[0]), max(ord(b[4]), ord(b[8])));
+        atomicMax(&st[node_inst[I]].kmax, m);
     }
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&st->kmax, m);
 }
 
-__global__ void penalty_alpha_kernel(PenaltyState *st, double scale)
+__global__ void penalty_alpha_kernel(PenaltyState *st, int n_inst, double scale)
 {
-    st->alpha = scale * unord(st->kmax);
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) st[i].alpha = scale * unord(st[i].kmax);
 }
 
-__global__ void penalty_fixed_alpha_kernel(PenaltyState *st, double alpha) { st->alpha = alpha; }
+__global__ void penalty_fixed_alpha_kernel(PenaltyState *st, int n_inst, double alpha)
+{
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) st[i].alpha = alpha;
+}
 
 __global__ void dof_count_kernel(int64_t m, const int64_t *dofs, int64_t ndof, int *mark, DevError *err)
 {
@@ -58,15 +64,15 @@ __global__ void dof_count_kernel(int64_t m, const int64_t *dofs, int64_t ndof, i
 }
 
 __global__ void penalty_apply_kernel(int64_t m, const int64_t *dofs, const double *values, int64_t ndof,
-                                     const int *mark, const int64_t *diag, const PenaltyState *st,
-                                     double *K, double *f)
+                                     const int *mark, const int64_t *diag, const int32_t *node_inst,
+                                     const PenaltyState *st, double *K, double *f)
 {
-    const double alpha = st->alpha;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = dofs[i];
         if (d < 0 || d >= ndof || mark[d] != 1) continue;
         const int64_t I = d / 3;
+        const double alpha = st[node_inst[I]].alpha;
         const int a = (int)(d % 3);
         K[9 * diag[I] + 4 * a] += alpha;
         f[d] += alpha * values[i];
@@ -128,7 +134,12 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket)
     return amlast;
 }
 
-// y = K x for the rows of this warp; returns x_I . y_I contribution (lane 0)
+// y_I = (K x)_I for one block row by one warp; returns x_I . y_I (every lane).
+// Lane l multiplies blocks l, l + 32, ... of the row. The product is bound
+// by the FP64 pipe on this chip (9 DFMA per 76-byte block against a 2 DFMA
+// per clock per SM rate), not by HBM: staging the blocks through shared
+// memory for coalesced loads was measured to gain nothing, so the loads
+// stay plain.
 __device__ __forceinline__ double bsr_row(int64_t I, const int64_t *rowptr, const int32_t *cols, const double *K,
                                           const double *x, double *y, int lane)
 {
@@ -284,64 +295,333 @@ __global__ void pcg_direction_kernel(int64_t n, const double *z, double *p, cons
         p[i] = fma(beta, p[i], z[i]);
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched PCG: independent Jacobi-PCG iterations of the instances of a
+// batched pattern (K is block diagonal by instance), with every instance's
+// own alpha, beta and convergence test on its own ||f_i||. Rows are split
+// into segments that never cross an instance; a block reduces each of its
+// segments to one partial, and the last block to finish sums every live
+// instance's partials in segment order, so the scalars are deterministic.
+// Converged instances drop out of the sweeps.
+// ---------------------------------------------------------------------------
+struct PcgInst {
+    double rz, pq, alpha, beta, rr, fnorm, relres, pad;
+    int iters, done, status, pad2;
+};
+
+struct PcgBatch {
+    double rtol;
+    int max_iter, active;
+    unsigned int ticket[2];
+};
+
+constexpr int kSegRows = 64;
+
+// sum of part[b..e) by one warp in a fixed order (valid in every lane)
+__device__ __forceinline__ double warp_sum_range(const double *part, int64_t b, int64_t e, int lane)
+{
+    double t = 0.0;
+    for (int64_t i = b + lane; i < e; i += 32) t += ((volatile const double *)part)[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+}
+
+// instances still iterating, counted by the last block into bst->active
+__device__ __forceinline__ void count_active(const PcgInst *inst, int n_inst, PcgBatch *bst)
+{
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int c = 0;
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) c += ((volatile const PcgInst *)inst)[i].done ? 0 : 1;
+    if (c) atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) bst->active = cnt;
+}
+
+__global__ void __launch_bounds__(kPcgThreads) pcgb_init_kernel(int64_t n_seg, const int64_t *seg_row,
+                                                                const int32_t *inst_seg, int n_inst,
+                                                                const int64_t *rowptr, const int32_t *cols,
+                                                                const double *K, const int64_t *diag,
+                                                                const double *f, const double *x, double *r,
+                                                                double *z, double *p, double *dinv, double *part,
+                                                                PcgInst *inst, PcgBatch *bst, DevError *err)
+{
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t s = blockIdx.x; s < n_seg; s += gridDim.x) {
+        double rz = 0.0, rr = 0.0, ff = 0.0;
+        for (int64_t I = seg_row[s] + warp; I < seg_row[s + 1]; I += nw) {
+            bsr_row(I, rowptr, cols, K, x, r, lane);
+            __syncwarp();
+            if (lane < 3) {
+                const int64_t d = 3 * I + lane;
+                const double kd = K[9 * diag[I] + 4 * lane];
+                if (!(kd > 0.0)) dev_fail(err, RPIM_E_ARG, d);
+                const double di = 1.0 / kd;
+                const double rv = f[d] - r[d];
+                const double zv = di * rv;
+                dinv[d] = di;
+                r[d] = rv;
+                z[d] = zv;
+                p[d] = zv;
+                rz += rv * zv;
+                rr += rv * rv;
+                ff += f[d] * f[d];
+            }
+        }
+        const double b_rz = block_reduce(rz, sh), b_rr = block_reduce(rr, sh), b_ff = block_reduce(ff, sh);
+        if (threadIdx.x == 0) {
+            part[s] = b_rz;
+            part[n_seg + s] = b_rr;
+            part[2 * n_seg + s] = b_ff;
+        }
+    }
+    if (last_block(&bst->ticket[0])) {
+        for (int i = warp; i < n_inst; i += nw) {
+            const double trz = warp_sum_range(part, inst_seg[i], inst_seg[i + 1], lane);
+            const double trr = warp_sum_range(part + n_seg, inst_seg[i], inst_seg[i + 1], lane);
+            const double tff = warp_sum_range(part + 2 * n_seg, inst_seg[i], inst_seg[i + 1], lane);
+            if (lane == 0) {
+                PcgInst &st = inst[i];
+                st.rz = trz;
+                st.rr = trr;
+                st.fnorm = tff > 0.0 ? sqrt(tff) : 1.0;
+                st.relres = sqrt(trr) / st.fnorm;
+                st.iters = 0;
+                st.status = 0;
+                st.done = (st.relres <= bst->rtol || bst->max_iter == 0) ? 1 : 0;
+                if (!isfinite(st.relres)) { st.done = 1; st.status = RPIM_E_NONFINITE; }
+            }
+        }
+        __threadfence_block();
+        count_active(inst, n_inst, bst);
+    }
+}
+
+// q = K p on the live instances; last block: alpha_i = rz_i / (p.q)_i
+__global__ void __launch_bounds__(kPcgThreads) pcgb_spmv_kernel(int64_t n_seg, const int64_t *seg_row,
+                                                                const int32_t *seg_inst, const int32_t *inst_seg,
+                                                                int n_inst, const int64_t *rowptr,
+                                                                const int32_t *cols, const double *K,
+                                                                const double *p, double *q, double *part,
+                                                                PcgInst *inst, PcgBatch *bst)
+{
+    if (bst->active == 0) return;
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t s = blockIdx.x; s < n_seg; s += gridDim.x) {
+        if (inst[seg_inst[s]].done) continue;
+        double pq = 0.0;
+        for (int64_t I = seg_row[s] + warp; I < seg_row[s + 1]; I += nw) {
+            const double v = bsr_row(I, rowptr, cols, K, p, q, lane);
+            if (lane == 0) pq += v;
+        }
+        const double bpq = block_reduce(pq, sh);
+        if (threadIdx.x == 0) part[s] = bpq;
+    }
+    if (last_block(&bst->ticket[0])) {
+        for (int i = warp; i < n_inst; i += nw) {
+            if (inst[i].done) continue;
+            const double t = warp_sum_range(part, inst_seg[i], inst_seg[i + 1], lane);
+            if (lane == 0) {
+                PcgInst &st = inst[i];
+                st.pq = t;
+                st.alpha = st.rz / t;
+                if (!isfinite(st.alpha)) { st.done = 1; st.status = RPIM_E_NONFINITE; }
+            }
+        }
+    }
+}
+
+// x += alpha_i p, r -= alpha_i q, z = Dinv r on the live instances; last
+// block: beta_i, residuals, convergence, count of live instances
+__global__ void __launch_bounds__(kPcgThreads) pcgb_update_kernel(int64_t n_seg, const int64_t *seg_row,
+                                                                  const int32_t *seg_inst, const int32_t *inst_seg,
+                                                                  int n_inst, double *x, double *r, double *z,
+                                                                  const double *p, const double *q,
+                                                                  const double *dinv, double *part, PcgInst *inst,
+                                                                  PcgBatch *bst)
+{
+    if (bst->active == 0) return;
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t s = blockIdx.x; s < n_seg; s += gridDim.x) {
+        const PcgInst &st = inst[seg_inst[s]];
+        if (st.done) continue;
+        const double alpha = st.alpha;
+        double rz = 0.0, rr = 0.0;
+        for (int64_t i = 3 * seg_row[s] + threadIdx.x; i < 3 * seg_row[s + 1]; i += blockDim.x) {
+            x[i] = fma(alpha, p[i], x[i]);
+            const double rv = fma(-alpha, q[i], r[i]);
+            const double zv = dinv[i] * rv;
+            r[i] = rv;
+            z[i] = zv;
+            rz = fma(rv, zv, rz);
+            rr = fma(rv, rv, rr);
+        }
+        const double b_rz = block_reduce(rz, sh), b_rr = block_reduce(rr, sh);
+        if (threadIdx.x == 0) {
+            part[s] = b_rz;
+            part[n_seg + s] = b_rr;
+        }
+    }
+    if (last_block(&bst->ticket[1])) {
+        for (int i = warp; i < n_inst; i += nw) {
+            if (inst[i].done) continue;
+            const double trz = warp_sum_range(part, inst_seg[i], inst_seg[i + 1], lane);
+            const double trr = warp_sum_range(part + n_seg, inst_seg[i], inst_seg[i + 1], lane);
+            if (lane == 0) {
+                PcgInst &st = inst[i];
+                st.beta = trz / st.rz;
+                st.rz = trz;
+                st.rr = trr;
+                st.relres = sqrt(trr) / st.fnorm;
+                st.iters += 1;
+                if (st.relres <= bst->rtol || st.iters >= bst->max_iter) st.done = 1;
+                if (!isfinite(st.relres)) { st.done = 1; st.status = RPIM_E_NONFINITE; }
+            }
+        }
+        __threadfence_block();
+        count_active(inst, n_inst, bst);
+    }
+}
+
+// p = z + beta_i p on the live instances (an instance that converged in the
+// update above is skipped: its p is no longer used)
+__global__ void __launch_bounds__(kPcgThreads) pcgb_direction_kernel(int64_t n_seg, const int64_t *seg_row,
+                                                                     const int32_t *seg_inst, const double *z,
+                                                                     double *p, const PcgInst *inst,
+                                                                     const PcgBatch *bst)
+{
+    if (bst->active == 0) return;
+    for (int64_t s = blockIdx.x; s < n_seg; s += gridDim.x) {
+        const PcgInst &st = inst[seg_inst[s]];
+        if (st.done) continue;
+        const double beta = st.beta;
+        for (int64_t i = 3 * seg_row[s] + threadIdx.x; i < 3 * seg_row[s + 1]; i += blockDim.x)
+            p[i] = fma(beta, p[i], z[i]);
+    }
+}
+
+
+// The launches of one chunk of PCG iterations as a CUDA graph: captured once
+// per solve on the pattern's capture stream (capturing runs nothing), then
+// replayed on the caller's stream, which removes the per-launch host cost
+// from the many short iterations of small systems. With per-kernel timing
+// on, the launches are issued directly so that every kernel keeps its events.
+class ChunkGraph {
+public:
+    ChunkGraph() = default;
+    ChunkGraph(const ChunkGraph &) = delete;
+    ChunkGraph &operator=(const ChunkGraph &) = delete;
+    ~ChunkGraph()
+    {
+        if (exec_) cudaGraphExecDestroy(exec_);
+    }
+    template <class F>
+    rpim_status run(rpim_pattern *p, cudaStream_t s, F issue)
+    {
+        if (profiling_on()) {
+            issue(s);
+            RPIM_CUDA(cudaGetLastError());
+            return RPIM_OK;
+        }
+        if (!exec_) {
+            if (!p->cap_stream) RPIM_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+            const int64_t before = launch_count();
+            RPIM_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+            issue(p->cap_stream);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+            kernels_ = launch_count() - before;
+            add_launches(-kernels_);   // counted when the graph runs
+            if (e != cudaSuccess) return fail(RPIM_E_CUDA, std::string("pcg graph capture: ") + cudaGetErrorString(e));
+            const cudaError_t ei = cudaGraphInstantiate(&exec_, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                exec_ = nullptr;
+                return fail(RPIM_E_CUDA, std::string("pcg graph instantiate: ") + cudaGetErrorString(ei));
+            }
+        }
+        add_launches(kernels_);
+        RPIM_CUDA(cudaGraphLaunch(exec_, s));
+        return RPIM_OK;
+    }
+
+private:
+    cudaGraphExec_t exec_ = nullptr;
+    int64_t kernels_ = 0;
+};
+
 } // namespace rpim
 
 using namespace rpim;
+
+// alpha_in < 0: alpha = scale * max diag per instance; otherwise alpha_in
+static rpim_status apply_penalty(rpim_pattern *p, double *K, double *f, int64_t m, const int64_t *dofs,
+                                 const double *values, double scale, double alpha_in, double *alpha_out,
+                                 cudaStream_t s)
+{
+    if (!p || !K || !f || m < 0 || (m > 0 && (!dofs || !values))) return fail(RPIM_E_ARG, "bad argument");
+    p->stream = s;
+    const int64_t ndof = 3 * p->n_nodes;
+    const int ni = p->n_inst;
+    PenaltyState *st = nullptr;
+    int *mark = nullptr;
+    RPIM_CHECK(dalloc(&st, ni, s));
+    RPIM_CHECK(dalloc(&mark, ndof, s));
+    RPIM_CUDA(cudaMemsetAsync(st, 0, ni * sizeof(PenaltyState), s));
+    RPIM_CUDA(cudaMemsetAsync(mark, 0, ndof * sizeof(int), s));
+    if (alpha_in < 0) {
+        launch("max_diag", max_diag_kernel, grid_size(p->sm_count, 4, p->n_nodes, 256), 256, 0, s, p->n_nodes,
+               (const int64_t *)p->diag, (const int32_t *)p->node_inst, (const double *)K, st);
+        launch("penalty_alpha", penalty_alpha_kernel, 1, 256, 0, s, st, ni, scale);
+    } else {
+        launch("penalty_alpha", penalty_fixed_alpha_kernel, 1, 256, 0, s, st, ni, alpha_in);
+    }
+    if (m > 0) {
+        launch("dof_count", dof_count_kernel, grid_size(p->sm_count, 4, m, 256), 256, 0, s, m, dofs, ndof, mark, p->err);
+        launch("penalty_apply", penalty_apply_kernel, grid_size(p->sm_count, 4, m, 256), 256, 0, s, m, dofs, values,
+               ndof, (const int *)mark, (const int64_t *)p->diag, (const int32_t *)p->node_inst,
+               (const PenaltyState *)st, K, f);
+    }
+    RPIM_CUDA(cudaGetLastError());
+    std::vector<PenaltyState> hs(ni);
+    RPIM_CUDA(cudaMemcpyAsync(hs.data(), st, ni * sizeof(PenaltyState), cudaMemcpyDeviceToHost, s));
+    dfree(st, s);
+    dfree(mark, s);
+    rpim_status r = check_device_error(p, "penalty");
+    if (alpha_out)
+        for (int i = 0; i < ni; i++) alpha_out[i] = hs[i].alpha;
+    return r;
+}
 
 extern "C" rpim_status rpim_apply_penalty_bc(rpim_pattern *p, double *K, double *f, int64_t m, const int64_t *dofs,
                                              const double *values, double scale, double *alpha_out,
                                              rpim_stream_t stream)
 {
-    if (!p || !K || !f || m < 0 || (m > 0 && (!dofs || !values))) return fail(RPIM_E_ARG, "bad argument");
-    cudaStream_t s = (cudaStream_t)stream;
-    p->stream = s;
-    const int64_t ndof = 3 * p->n_nodes;
-    PenaltyState *st = nullptr;
-    int *mark = nullptr;
-    RPIM_CHECK(dalloc(&st, 1, s));
-    RPIM_CHECK(dalloc(&mark, ndof, s));
-    RPIM_CUDA(cudaMemsetAsync(st, 0, sizeof(PenaltyState), s));
-    RPIM_CUDA(cudaMemsetAsync(mark, 0, ndof * sizeof(int), s));
-    launch("max_diag", max_diag_kernel, grid_size(p->sm_count, 4, p->n_nodes, 256), 256, 0, s, p->n_nodes, p->diag, K, st);
-    launch("penalty_alpha", penalty_alpha_kernel, 1, 1, 0, s, st, scale);
-    if (m > 0) {
-        launch("dof_count", dof_count_kernel, grid_size(p->sm_count, 4, m, 256), 256, 0, s, m, dofs, ndof, mark, p->err);
-        launch("penalty_apply", penalty_apply_kernel, grid_size(p->sm_count, 4, m, 256), 256, 0, s, m, dofs, values, ndof, mark,
-                                                                                 p->diag, st, K, f);
-    }
-    RPIM_CUDA(cudaGetLastError());
-    double alpha = 0.0;
-    RPIM_CUDA(cudaMemcpyAsync(&alpha, &st->alpha, sizeof(double), cudaMemcpyDeviceToHost, s));
-    dfree(st, s);
-    dfree(mark, s);
-    rpim_status r = check_device_error(p, "penalty");
-    if (alpha_out) *alpha_out = alpha;
-    return r;
+    if (!p) return fail(RPIM_E_ARG, "null pattern");
+    std::vector<double> a(p->n_inst);
+    rpim_status st = apply_penalty(p, K, f, m, dofs, values, scale, -1.0, a.data(), (cudaStream_t)stream);
+    if (alpha_out) *alpha_out = a[0];
+    return st;
+}
+
+extern "C" rpim_status rpim_apply_penalty_bc_batched(rpim_pattern *p, double *K, double *f, int64_t m,
+                                                     const int64_t *dofs, const double *values, double scale,
+                                                     double *alpha_out, rpim_stream_t stream)
+{
+    return apply_penalty(p, K, f, m, dofs, values, scale, -1.0, alpha_out, (cudaStream_t)stream);
 }
 
 extern "C" rpim_status rpim_apply_penalty_alpha(rpim_pattern *p, double *K, double *f, int64_t m, const int64_t *dofs,
                                                 const double *values, double alpha, rpim_stream_t stream)
 {
-    if (!p || !K || !f || m < 0 || (m > 0 && (!dofs || !values)) || !(alpha >= 0.0))
-        return fail(RPIM_E_ARG, "bad argument");
-    cudaStream_t s = (cudaStream_t)stream;
-    p->stream = s;
-    const int64_t ndof = 3 * p->n_nodes;
-    PenaltyState *st = nullptr;
-    int *mark = nullptr;
-    RPIM_CHECK(dalloc(&st, 1, s));
-    RPIM_CHECK(dalloc(&mark, ndof, s));
-    RPIM_CUDA(cudaMemsetAsync(mark, 0, ndof * sizeof(int), s));
-    launch("penalty_alpha", penalty_fixed_alpha_kernel, 1, 1, 0, s, st, alpha);
-    if (m > 0) {
-        launch("dof_count", dof_count_kernel, grid_size(p->sm_count, 4, m, 256), 256, 0, s, m, dofs, ndof, mark, p->err);
-        launch("penalty_apply", penalty_apply_kernel, grid_size(p->sm_count, 4, m, 256), 256, 0, s, m, dofs, values, ndof,
-               (const int *)mark, (const int64_t *)p->diag, (const PenaltyState *)st, K, f);
-    }
-    RPIM_CUDA(cudaGetLastError());
-    dfree(st, s);
-    dfree(mark, s);
-    return check_device_error(p, "penalty");
+    if (!(alpha >= 0.0)) return fail(RPIM_E_ARG, "negative penalty");
+    return apply_penalty(p, K, f, m, dofs, values, 0.0, alpha, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" rpim_status rpim_solve_pcg(rpim_pattern *p, const double *K, const double *f, double *u, double rtol,
@@ -370,13 +650,16 @@ extern "C" rpim_status rpim_solve_pcg(rpim_pattern *p, const double *K, const do
     RPIM_CUDA(cudaGetLastError());
     const int chunk = 32;
     int it = 0;
-    for (;;) {
+    ChunkGraph graph;
+    auto issue = [&](cudaStream_t cs) {
         for (int k = 0; k < chunk; k++) {
-            launch("pcg_spmv", pcg_spmv_kernel, nb, tpb, 0, s, p->n_nodes, p->rowptr, p->cols, K, pp, q, part, st);
-            launch("pcg_update", pcg_update_kernel, nb, tpb, 0, s, n, u, r, z, pp, q, dinv, part, st);
-            launch("pcg_direction", pcg_direction_kernel, nb, tpb, 0, s, n, z, pp, st);
+            launch("pcg_spmv", pcg_spmv_kernel, nb, tpb, 0, cs, p->n_nodes, p->rowptr, p->cols, K, pp, q, part, st);
+            launch("pcg_update", pcg_update_kernel, nb, tpb, 0, cs, n, u, r, z, pp, q, dinv, part, st);
+            launch("pcg_direction", pcg_direction_kernel, nb, tpb, 0, cs, n, z, pp, st);
         }
-        RPIM_CUDA(cudaGetLastError());
+    };
+    for (;;) {
+        RPIM_CHECK(graph.run(p, s, issue));
         RPIM_CUDA(cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, s));
         RPIM_CUDA(cudaStreamSynchronize(s));
         it += chunk;
@@ -390,6 +673,117 @@ extern "C" rpim_status rpim_solve_pcg(rpim_pattern *p, const double *K, const do
         char buf[128];
         snprintf(buf, sizeof buf, "pcg: relative residual %.3e after %d iterations", hs.relres, hs.iters);
         return fail(RPIM_E_NOCONV, buf);
+    }
+    return RPIM_OK;
+}
+
+// segments that never cross an instance: 64 rows (8 per warp), or up to
+// 512 when the rows are plentiful enough to give every block of the grid
+// several segments (fewer block-wide reductions and barrier waits)
+static rpim_status build_segments(rpim_pattern *p, cudaStream_t s)
+{
+    if (p->seg_row) return RPIM_OK;
+    const int64_t nb = (int64_t)p->sm_count * 4;
+    int64_t rows = kSegRows;
+    while (rows < 512 && p->n_nodes >= 8 * nb * (2 * rows)) rows *= 2;
+    std::vector<int64_t> row;
+    std::vector<int32_t> sinst, iseg;
+    for (int i = 0; i < p->n_inst; i++) {
+        iseg.push_back((int32_t)sinst.size());
+        const rpim::InstGrid &g = p->ig_host[i];
+        for (int64_t r = g.node_begin; r < g.node_end; r += rows) {
+            row.push_back(r);
+            sinst.push_back(i);
+        }
+    }
+    iseg.push_back((int32_t)sinst.size());
+    row.push_back(p->n_nodes);
+    const int64_t ns = (int64_t)sinst.size();
+    RPIM_CHECK(dalloc(&p->seg_row, ns + 1, s));
+    RPIM_CHECK(dalloc(&p->seg_inst, ns, s));
+    RPIM_CHECK(dalloc(&p->inst_seg, p->n_inst + 1, s));
+    RPIM_CUDA(cudaMemcpyAsync(p->seg_row, row.data(), (ns + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    if (ns) RPIM_CUDA(cudaMemcpyAsync(p->seg_inst, sinst.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    RPIM_CUDA(cudaMemcpyAsync(p->inst_seg, iseg.data(), iseg.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    RPIM_CUDA(cudaStreamSynchronize(s));   // host vectors go out of scope
+    p->n_seg = ns;
+    return RPIM_OK;
+}
+
+extern "C" rpim_status rpim_solve_pcg_batched(rpim_pattern *p, const double *K, const double *f, double *u,
+                                              double rtol, int32_t max_iter, int32_t *iters, double *relres,
+                                              rpim_stream_t stream)
+{
+    if (!p || !K || !f || !u || max_iter < 0 || !(rtol >= 0)) return fail(RPIM_E_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    RPIM_CHECK(build_segments(p, s));
+    const int64_t n = 3 * p->n_nodes, ns = p->n_seg;
+    const int ni = p->n_inst;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(ns, (int64_t)p->sm_count * 4));
+    const int64_t inst_doubles = (ni * (int64_t)sizeof(PcgInst) + sizeof(PcgBatch) + 7) / 8;
+    const int64_t need = 5 * n + 3 * ns + inst_doubles;
+    if (p->ws.doubles < need) {
+        dfree(p->ws.buf, s);
+        RPIM_CHECK(dalloc(&p->ws.buf, need, s));
+        p->ws.doubles = need;
+    }
+    double *r = p->ws.buf, *z = r + n, *pp = z + n, *q = pp + n, *dinv = q + n, *part = dinv + n;
+    PcgBatch *bst = (PcgBatch *)(part + 3 * ns);
+    PcgInst *inst = (PcgInst *)(bst + 1);
+    static_assert(sizeof(PcgBatch) % 8 == 0 && sizeof(PcgInst) % 8 == 0, "8-byte state records");
+    PcgBatch hb{};
+    hb.rtol = rtol;
+    hb.max_iter = max_iter;
+    hb.active = ni;
+    RPIM_CUDA(cudaMemcpyAsync(bst, &hb, sizeof hb, cudaMemcpyHostToDevice, s));
+    const int tpb = kPcgThreads;
+    launch("pcgb_init", pcgb_init_kernel, nb, tpb, 0, s, ns, (const int64_t *)p->seg_row,
+           (const int32_t *)p->inst_seg, ni, (const int64_t *)p->rowptr, (const int32_t *)p->cols, K,
+           (const int64_t *)p->diag, f, (const double *)u, r, z, pp, dinv, part, inst, bst, p->err);
+    RPIM_CUDA(cudaGetLastError());
+    const int chunk = 32;
+    int it = 0;
+    ChunkGraph graph;
+    auto issue = [&](cudaStream_t cs) {
+        for (int k = 0; k < chunk; k++) {
+            launch("pcgb_spmv", pcgb_spmv_kernel, nb, tpb, 0, cs, ns, (const int64_t *)p->seg_row,
+                   (const int32_t *)p->seg_inst, (const int32_t *)p->inst_seg, ni, (const int64_t *)p->rowptr,
+                   (const int32_t *)p->cols, K, (const double *)pp, q, part, inst, bst);
+            launch("pcgb_update", pcgb_update_kernel, nb, tpb, 0, cs, ns, (const int64_t *)p->seg_row,
+                   (const int32_t *)p->seg_inst, (const int32_t *)p->inst_seg, ni, u, r, z, (const double *)pp,
+                   (const double *)q, (const double *)dinv, part, inst, bst);
+            launch("pcgb_direction", pcgb_direction_kernel, nb, tpb, 0, cs, ns, (const int64_t *)p->seg_row,
+                   (const int32_t *)p->seg_inst, (const double *)z, pp, (const PcgInst *)inst,
+                   (const PcgBatch *)bst);
+        }
+    };
+    for (;;) {
+        RPIM_CHECK(graph.run(p, s, issue));
+        RPIM_CUDA(cudaMemcpyAsync(&hb, bst, sizeof hb, cudaMemcpyDeviceToHost, s));
+        RPIM_CUDA(cudaStreamSynchronize(s));
+        it += chunk;
+        if (hb.active == 0 || it > max_iter + chunk) break;
+    }
+    std::vector<PcgInst> hi(ni);
+    RPIM_CUDA(cudaMemcpyAsync(hi.data(), inst, ni * sizeof(PcgInst), cudaMemcpyDeviceToHost, s));
+    RPIM_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < ni; i++) {
+        if (iters) iters[i] = hi[i].iters;
+        if (relres) relres[i] = hi[i].relres;
+    }
+    RPIM_CHECK(check_device_error(p, "pcg batched"));
+    for (int i = 0; i < ni; i++) {
+        char buf[160];
+        if (hi[i].status) {
+            snprintf(buf, sizeof buf, "pcg batched: non-finite value in instance %d", i);
+            return fail((rpim_status)hi[i].status, buf);
+        }
+        if (!(hi[i].relres <= rtol)) {
+            snprintf(buf, sizeof buf, "pcg batched: instance %d at relative residual %.3e after %d iterations", i,
+                     hi[i].relres, hi[i].iters);
+            return fail(RPIM_E_NOCONV, buf);
+        }
     }
     return RPIM_OK;
 }

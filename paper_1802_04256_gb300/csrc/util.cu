@@ -71,6 +71,12 @@ int64_t launch_begin(const char *name, cudaStream_t s)
     return (int64_t)g_pending.size() - 1;
 }
 
+bool profiling_on() { return g_profile.load() != 0; }
+
+void add_launches(int64_t n) { g_launches.fetch_add(n); }
+
+int64_t launch_count() { return g_launches.load(); }
+
 void launch_end(int64_t tok, cudaStream_t s)
 {
     if (tok < 0) return;

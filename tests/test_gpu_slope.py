@@ -1,0 +1,133 @@
+"""The layered slope at scale: 590,500 nodes of a 100^3 lattice clipped to a
+45-degree face, 4,724,000 integration points, support radius 3h, three
+layers, gravity, rollers on the sides, base fixed.
+
+The oracle cannot assemble the whole K (about 36 GB), so the checks are the
+sampled ones (supports, shape functions and whole rows of K against the
+oracle, with the tolerance rule of the parity tests) and properties that hold
+at any size, evaluated on the device with plain PyTorch ops: six rigid-body
+null modes of K, the total body force, and after the solve the vertical
+equilibrium of the base reactions with the weight.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+from gpu_util import GpuRun, t
+
+pytestmark = pytest.mark.gpu
+
+TOL_K_LD = 1e-10
+GAIN = 0.05
+
+
+@pytest.fixture(scope="module")
+def slope():
+    p = gen.slope_config()
+    g = GpuRun(p)
+    rowptr, cols = g.pat.csr()
+    return p, g, rowptr, cols
+
+
+def _matvec(rowptr, cols, K, u, chunk=1 << 25):
+    """y = K u for the device BSR matrix (plain PyTorch, chunked)."""
+    n = rowptr.numel() - 1
+    rows = torch.repeat_interleave(torch.arange(n, device=u.device), rowptr[1:] - rowptr[:-1])
+    Kb = K.view(-1, 3, 3)
+    uu = u.view(-1, 3)
+    y = torch.zeros(n, 3, dtype=torch.float64, device=u.device)
+    for a in range(0, cols.numel(), chunk):
+        b = min(a + chunk, cols.numel())
+        y.index_add_(0, rows[a:b], torch.einsum("tab,tb->ta", Kb[a:b], uu[cols[a:b].long()]))
+    return y.view(-1)
+
+
+def test_sampled_supports_and_shape_functions(slope):
+    p, g, rowptr, cols = slope
+    xyz, wj, soff, sidx = g.pat.points()
+    rs2 = oracle.support_radius2(p.alpha_s, p.h)
+    scale = np.array([1.0, p.h, p.h, p.h])
+    rng = np.random.default_rng(11)
+    phi_all = g.pat.shape_functions()
+    worst = e64 = 0.0
+    for k in rng.choice(p.n_points, 24, replace=False):
+        x = xyz[k].cpu().numpy()
+        a, b = int(soff[k]), int(soff[k + 1])
+        s = oracle.support(p.xyz, x, rs2)
+        assert np.array_equal(s, sidx[a:b].cpu().numpy())
+        mine = phi_all[a:b].cpu().numpy().T * scale[:, None]
+        ld = oracle.shape(p.xyz, s, x, p.h, p.alpha_c, p.q, "ld") * scale[:, None]
+        f64 = oracle.shape(p.xyz, s, x, p.h, p.alpha_c, p.q, "f64") * scale[:, None]
+        worst = max(worst, np.abs(mine - ld).max())
+        e64 = max(e64, np.abs(f64 - ld).max())
+    tol = max(1e-9, GAIN * e64)
+    print("phi: |gpu - ld| %.3e (tol %.1e), |f64 - ld| %.3e" % (worst, tol, e64))
+    assert worst < tol
+
+
+def test_sampled_rows_vs_oracle(slope):
+    """Rows at the base, in the middle of each layer and on the slope face,
+    assembled by the oracle from the points whose support holds the row's node."""
+    p, g, rowptr, cols = slope
+    pts, wj = oracle.gauss_points(p.cell_lo, p.cell_hi)
+    rs2 = oracle.support_radius2(p.alpha_s, p.h)
+    kmax = float(g.K.abs().max())
+    targets = [(0.5, 0.5, 0.0), (0.3, 0.5, 0.17), (0.3, 0.5, 0.5), (0.2, 0.5, 0.83), (0.7, 0.3, 0.4)]
+    e64 = dld = d64 = 0.0
+    for tx in targets:
+        I = int(np.argmin(((p.nominal - tx) ** 2).sum(1)))
+        near = np.nonzero(((pts - p.xyz[I]) ** 2).sum(1) <= rs2 * 1.01)[0]
+        sel = [k for k in near if I in oracle.support(p.xyz, pts[k], rs2)]
+        r0, r1 = int(rowptr[I]), int(rowptr[I + 1])
+        mine = g.K.view(-1, 9)[r0:r1].cpu().numpy()
+        mc = cols[r0:r1].cpu().numpy()
+        rows = {}
+        for kind in ("f64", "ld"):
+            m = oracle.assemble(p.xyz, pts[sel], wj[sel], p.E[sel], p.nu[sel], p.alpha_s, p.alpha_c, p.q, p.h,
+                                kind=kind)
+            assert np.array_equal(m.cols[m.rowptr[I]:m.rowptr[I + 1]], mc)
+            rows[kind] = m.vals[m.rowptr[I]:m.rowptr[I + 1]].reshape(-1, 9)
+        e64 = max(e64, np.abs(rows["f64"] - rows["ld"]).max() / kmax)
+        dld = max(dld, np.abs(mine - rows["ld"]).max() / kmax)
+        d64 = max(d64, np.abs(mine - rows["f64"]).max() / kmax)
+        print("row %d (%s): %d points, %d blocks" % (I, tx, len(sel), r1 - r0))
+    tol = max(TOL_K_LD, GAIN * e64)
+    print("K rows: |gpu - ld| %.3e (tol %.1e), |f64 - ld| %.3e, |gpu - f64| %.3e" % (dld, tol, e64, d64))
+    assert dld < tol
+    assert d64 < e64 + tol
+
+
+def test_rigid_body_modes_and_weight(slope):
+    p, g, rowptr, cols = slope
+    X = torch.as_tensor(p.xyz, device="cuda")
+    kf = float(torch.linalg.norm(g.K))
+    for k in range(3):
+        e = torch.zeros(3, dtype=torch.float64, device="cuda")
+        e[k] = 1.0
+        for u in (e.repeat(p.n_nodes), torch.linalg.cross(e.expand_as(X), X).reshape(-1)):
+            r = float(torch.linalg.norm(_matvec(rowptr, cols, g.K, u))) / (kf * float(torch.linalg.norm(u)))
+            assert r < 1e-10, r
+    fz = g.f.view(-1, 3).sum(0).cpu().numpy()
+    V = float(g.pat.points()[1].sum())
+    print("sum f = %s, -gamma V = %.9f" % (fz, -20.0 * V))
+    assert abs(fz[2] + 20.0 * V) < 1e-10 * 20.0 * V
+    assert np.abs(fz[:2]).max() < 1e-10 * 20.0 * V
+
+
+def test_solve_base_reaction_balances_weight(slope):
+    """After the solve the penalty forces on the fixed vertical DOFs (the base
+    reactions) carry the whole weight: 1_z^T K0 = 0 by translation invariance,
+    so sum_base alpha u_z = sum f_z up to the solver residual."""
+    p, g, rowptr, cols = slope
+    u, it, rr, alpha, K, f = g.solve(rtol=1e-10)
+    res = float(torch.linalg.norm(f - _matvec(rowptr, cols, K, u))) / float(torch.linalg.norm(f))
+    fd = torch.as_tensor(p.fixed_dofs, device="cuda")
+    base = fd[fd % 3 == 2]
+    reaction = float(alpha * u[base].sum())
+    weight = float(g.f.view(-1, 3)[:, 2].sum())
+    print("PCG %d iterations, relres %.2e, true %.2e; base reaction %.9f, weight %.9f"
+          % (it, rr, res, reaction, weight))
+    assert res < 1e-9
+    assert abs(reaction - weight) < 1e-6 * abs(weight)
