@@ -178,6 +178,31 @@ rpim_status rpim_assemble(rpim_pattern *pattern, const double *E, const double *
                           const double *body, double *K_vals, double *f, rpim_stream_t stream);
 
 /*
+ * Autotuner of the shape-function kernel's launch shape (points per block,
+ * warps per point) for every support-size bucket of a pattern (the batched
+ * workloads' tile and bucket choice): each admissible shape is timed on up
+ * to max_points points of the bucket (CUDA events on `stream`), and the
+ * fastest is used from then on, by every pattern of the process, for
+ * supports of that bucket's size. The shape functions, hence K, are bitwise
+ * the same for every launch shape, so tuning changes speed only.
+ *   table   host int32 [3*16], optional: (largest support, warps per point,
+ *           points per block) of each tuned bucket
+ *   n_table host, optional: number of tuned buckets
+ * Synchronises. Errors: RPIM_E_ARG, RPIM_E_CUDA.
+ */
+rpim_status rpim_autotune_shape(rpim_pattern *pattern, int64_t max_points, int32_t *table,
+                                int32_t *n_table, rpim_stream_t stream);
+
+/* Sets the launch shape for buckets whose largest support is max_support
+ * (as rpim_autotune_shape would). Errors: RPIM_E_ARG when the shape is not
+ * admissible (1-4 warps per point, 1-15 points per block, at most 1024
+ * threads, the points' shared memory within 216 KB). */
+rpim_status rpim_autotune_set(int32_t max_support, int32_t warps_per_point, int32_t points_per_block);
+
+/* Forgets every tuned launch shape (back to the built-in rule). */
+rpim_status rpim_autotune_reset(void);
+
+/*
  * Shape functions only: writes, for every support entry e of every
  * integration point, phi[4e .. 4e+3] = (phi, dphi/dx, dphi/dy, dphi/dz)
  * in the order of rpim_pattern_points' support lists. Synchronises.

@@ -30,7 +30,8 @@ EXPORTED = [
     "rpim_stress", "rpim_stress_noalloc", "rpim_last_error", "rpim_version",
     "rpim_apply_penalty_alpha", "rpim_grad_material", "rpim_build_pattern_batched",
     "rpim_add_point_loads_batched", "rpim_apply_penalty_bc_batched", "rpim_stress_batched",
-    "rpim_solve_pcg_batched", "rpim_probe_dfma", "rpim_probe_dmma", "rpim_probe_fp64_mixed",
+    "rpim_solve_pcg_batched", "rpim_autotune_shape", "rpim_autotune_reset",
+    "rpim_autotune_set", "rpim_probe_dfma", "rpim_probe_dmma", "rpim_probe_fp64_mixed",
     "rpim_kernel_launches", "rpim_profile_enable", "rpim_profile_read", "rpim_kernel_series_info",
 ]
 
@@ -97,6 +98,9 @@ def lib():
         "rpim_apply_penalty_bc_batched": [vp, vp, vp, i64, vp, vp, dbl, C.POINTER(dbl), vp],
         "rpim_stress_batched": [vp, vp, i64, vp, vp, vp, vp, vp, vp],
         "rpim_solve_pcg_batched": [vp, vp, vp, vp, dbl, i32, C.POINTER(i32), C.POINTER(dbl), vp],
+        "rpim_autotune_shape": [vp, i64, C.POINTER(i32), C.POINTER(i32), vp],
+        "rpim_autotune_reset": [],
+        "rpim_autotune_set": [i32, i32, i32],
         "rpim_probe_dfma": [i32, C.POINTER(dbl)],
         "rpim_probe_dmma": [i32, C.POINTER(dbl)],
         "rpim_probe_fp64_mixed": [i32, C.POINTER(dbl)],
@@ -267,6 +271,23 @@ def rpim_solve_pcg_batched(handle, n_inst, K_vals, f, u, rtol=1e-10, max_iter=10
     return list(it), list(rr), st
 
 
+def rpim_autotune_shape(handle, max_points=20000, stream=None):
+    """Tunes the shape kernel's launch shape per support-size bucket of the
+    pattern; returns [(largest support, warps per point, points per block)]."""
+    table = (C.c_int32 * 48)()
+    n = C.c_int32(0)
+    _check(lib().rpim_autotune_shape(handle, max_points, table, C.byref(n), _stream(stream)), "rpim_autotune_shape")
+    return [tuple(table[3 * i:3 * i + 3]) for i in range(min(n.value, 16))]
+
+
+def rpim_autotune_set(max_support, warps_per_point, points_per_block):
+    _check(lib().rpim_autotune_set(max_support, warps_per_point, points_per_block), "rpim_autotune_set")
+
+
+def rpim_autotune_reset():
+    _check(lib().rpim_autotune_reset(), "rpim_autotune_reset")
+
+
 def rpim_stress(handle, u, xyz, E, nu, sigma, stream=None):
     _check(lib().rpim_stress(handle, _dev(u, torch.float64), xyz.shape[0], _dev(xyz, torch.float64),
                              _dev(E, torch.float64), _dev(nu, torch.float64),
@@ -423,6 +444,9 @@ class Pattern:
             u = torch.zeros(3 * self.info.n_nodes, dtype=torch.float64, device=self.device)
         it, rr, st = rpim_solve_pcg(self.handle, K, f, u, rtol, max_iter, stream, check)
         return u, it, rr
+
+    def autotune(self, max_points=20000, stream=None):
+        return rpim_autotune_shape(self.handle, max_points, stream)
 
     def solve_pcg_batched(self, K, f, u=None, rtol=1e-10, max_iter=100000, stream=None, check=True):
         """Per-instance PCG: (u, iterations per instance, residual per instance)."""

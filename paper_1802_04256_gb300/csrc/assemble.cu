@@ -3,10 +3,10 @@
 // K_IJ = sum_g w_g B_I^T D_g B_J. For an isotropic D this 3x3 block is
 //   K_ab = sum_g [ lambda_g w_g dI_a dJ_b + mu_g w_g (dI_b dJ_a + delta_ab dI . dJ) ]
 // with dI = grad phi_I(x_g). Assembly is row-owner: one warp owns row I, walks
-// the points whose support contains I in ascending order and accumulates, in
-// shared memory, the blocks (I, J) for J >= I of each such point. Every block
-// is therefore a fixed-order sum (no atomics, bitwise reproducible). The
-// lower blocks are copied, transposed, from the upper ones.
+// the points whose support contains I in ascending order and accumulates the
+// blocks (I, J) for J >= I of each such point in place in K. Every block is
+// therefore a fixed-order sum (no atomics, bitwise reproducible). The lower
+// blocks are copied, transposed, from the upper ones.
 #include <math.h>
 
 #include <algorithm>
@@ -46,9 +46,14 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t 
 
 // Row kernel. One warp owns row I and accumulates the upper blocks (J >= I)
 // of its row in place in K (L2-resident read-modify-write; every block is
-// touched by one lane at a time, in ascending point order). Per-point scalars
+// touched by one lane at a time, in ascending point order). Accumulating in
+// shared memory instead was measured slower: the buffers leave room for
+// half as many warps, and the kernel needs them to cover its load latency. Per-point scalars
 // are prefetched 32 points at a time, one point per lane, and broadcast by
-// shuffles.
+// shuffles. The block slot of a column J is looked up in a per-warp shared
+// table indexed by J's position in the 25 cell runs around I (the same
+// positions as the pattern's bitmap), filled from the row's upper columns:
+// one table read per pair instead of a binary search over the row.
 //
 // Uniform rows (all points of the row have the same nu, hence the same
 // kappa = lambda/mu = 2 nu / (1 - 2 nu)) accumulate only
@@ -69,10 +74,17 @@ __global__ void __launch_bounds__(256) row_kernel(int64_t n_nodes, const int64_t
                                                   const double *__restrict__ body,
                                                   const int64_t *__restrict__ rowptr,
                                                   const int32_t *__restrict__ cols,
-                                                  const int64_t *__restrict__ diag, double *K,
+                                                  const int64_t *__restrict__ diag, const InstGrid *__restrict__ ig,
+                                                  const int32_t *__restrict__ node_inst,
+                                                  const int32_t *__restrict__ cell_start,
+                                                  const uint32_t *__restrict__ node_cpk,
+                                                  const int32_t *__restrict__ node_rank, int nbits, double *K,
                                                   double *__restrict__ f, DevError *err)
 {
-    const int lane = threadIdx.x & 31;
+    extern __shared__ int16_t slot_tab[];
+    __shared__ int run_start[8][25], run_pre[8][26];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    int16_t *tab = slot_tab + (size_t)wi * nbits;
     double b0 = 0.0, b1 = 0.0, b2 = 0.0;
     if (body) { b0 = body[0]; b1 = body[1]; b2 = body[2]; }
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -82,6 +94,20 @@ __global__ void __launch_bounds__(256) row_kernel(int64_t n_nodes, const int64_t
         const int32_t *ucols = cols + sd;
         double *Ku = K + 9 * sd;
         for (int64_t i = lane; i < 9 * (int64_t)U; i += 32) Ku[i] = 0.0;
+        const uint32_t ci = node_cpk[I];
+        const int cx = (int)(ci & 0x7FF), cy = (int)((ci >> 11) & 0x7FF), cz = (int)(ci >> 22);
+        const int total = cell_runs(ig[node_inst[I]], cell_start, cx, cy, cz, lane, run_start[wi], run_pre[wi]);
+        if (total > nbits) {
+            if (lane == 0) dev_fail(err, RPIM_E_ARG, I);
+            continue;
+        }
+        for (int i = lane; i < total; i += 32) tab[i] = -1;
+        __syncwarp();
+        for (int s = lane; s < U; s += 32) {
+            const int bi = run_bit(node_cpk, node_rank, ucols[s], cx, cy, cz, run_start[wi], run_pre[wi]);
+            if (bi >= 0 && bi < total) tab[bi] = (int16_t)s;
+        }
+        __syncwarp();
         const int64_t t0 = toff[I], t1 = toff[I + 1];
         // uniform Poisson ratio over the row's points?
         const double nu0 = nu[entry_pt[tent[t0]]];
@@ -117,9 +143,9 @@ __global__ void __launch_bounds__(256) row_kernel(int64_t n_nodes, const int64_t
                 f2 = fma(w, b2, f2);
                 if (uni) {
                     for (int64_t q = e + lane; q < end; q += 32) {
-                        const int32_t J = sidx[q];
-                        const int slot = lower_bound_i32(ucols, U, J);
-                        if (slot >= U || ucols[slot] != J) { dev_fail(err, RPIM_E_ARG, I); continue; }
+                        const int bi = run_bit(node_cpk, node_rank, sidx[q], cx, cy, cz, run_start[wi], run_pre[wi]);
+                        const int slot = bi >= 0 && bi < total ? tab[bi] : -1;
+                        if (slot < 0) { dev_fail(err, RPIM_E_ARG, I); continue; }
                         const double2 qa = *(const double2 *)(phi + 4 * q);
                         const double2 qb = *(const double2 *)(phi + 4 * q + 2);
                         const double d0 = qa.y, d1 = qb.x, d2 = qb.y;
@@ -132,9 +158,9 @@ __global__ void __launch_bounds__(256) row_kernel(int64_t n_nodes, const int64_t
                     const double A0 = __shfl_sync(0xffffffffu, pA0, k), A1 = __shfl_sync(0xffffffffu, pA1, k),
                                  A2 = __shfl_sync(0xffffffffu, pA2, k);
                     for (int64_t q = e + lane; q < end; q += 32) {
-                        const int32_t J = sidx[q];
-                        const int slot = lower_bound_i32(ucols, U, J);
-                        if (slot >= U || ucols[slot] != J) { dev_fail(err, RPIM_E_ARG, I); continue; }
+                        const int bi = run_bit(node_cpk, node_rank, sidx[q], cx, cy, cz, run_start[wi], run_pre[wi]);
+                        const int slot = bi >= 0 && bi < total ? tab[bi] : -1;
+                        if (slot < 0) { dev_fail(err, RPIM_E_ARG, I); continue; }
                         const double2 qa = *(const double2 *)(phi + 4 * q);
                         const double2 qb = *(const double2 *)(phi + 4 * q + 2);
                         const double d0 = qa.y, d1 = qb.x, d2 = qb.y;
@@ -367,9 +393,15 @@ extern "C" rpim_status rpim_assemble(rpim_pattern *p, const double *E, const dou
     RPIM_CHECK(ensure_phi(p, s));
     launch("lame", lame_kernel, grid_size(p->sm_count, 4, p->n_points, 256), 256, 0, s, p->n_points, E, nu, p->wj, p->lamw, p->err);
     RPIM_CHECK(shape_functions_all(p, p->phi, s));
-    launch("row", row_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, 0, s, p->n_nodes, p->toff,
+    // per warp: the slot table (int16 per bitmap position)
+    const int nbits = 32 * p->bit_words;
+    const size_t smem = (size_t)8 * nbits * sizeof(int16_t);
+    if (nbits > 32767 || smem > 216 * 1024) return fail(RPIM_E_SUPPORT, "row slot table too large (too many nodes per cell)");
+    RPIM_CUDA(cudaFuncSetAttribute(row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    launch("row", row_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, smem, s, p->n_nodes, p->toff,
            p->tent, p->entry_pt, p->soff, p->sidx, p->phi, p->lamw, p->wj, nu, body, p->rowptr, p->cols, p->diag,
-           K, f, p->err);
+           (const InstGrid *)p->ig, (const int32_t *)p->node_inst, (const int32_t *)p->cell_start,
+           (const uint32_t *)p->node_cpk, (const int32_t *)p->node_rank, nbits, K, f, p->err);
     RPIM_CUDA(cudaGetLastError());
     launch("mirror", mirror_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, 0, s, p->n_nodes, p->rowptr, p->cols, K);
     RPIM_CUDA(cudaGetLastError());

@@ -88,6 +88,45 @@ struct InstGrid {
     int64_t node_begin, node_end;
 };
 
+// the 25 runs of cells (dy, dz in [-2, 2], dx in [-2, 2] contiguous) around
+// I's cell: start in the cell-ordered list and exclusive prefix of lengths
+__device__ __forceinline__ int cell_runs(const InstGrid &g, const int32_t *cell_start, int cx, int cy, int cz,
+                                         int lane, int *run_start, int *run_pre)
+{
+    if (lane < 25) {
+        const int dy = lane % 5 - 2, dz = lane / 5 - 2;
+        const int yy = cy + dy, zz = cz + dz;
+        int st = 0, len = 0;
+        if (yy >= 0 && yy < g.n[1] && zz >= 0 && zz < g.n[2]) {
+            const int xa = max(cx - 2, 0), xb = min(cx + 2, g.n[0] - 1);
+            const int64_t row = g.cell_off + (int64_t)g.n[0] * (yy + (int64_t)g.n[1] * zz);
+            st = cell_start[row + xa];
+            len = cell_start[row + xb + 1] - st;
+        }
+        run_start[lane] = st;
+        run_pre[lane + 1] = len;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        run_pre[0] = 0;
+        for (int r = 0; r < 25; r++) run_pre[r + 1] += run_pre[r];
+    }
+    __syncwarp();
+    return run_pre[25];
+}
+
+// position of node J in the 25 runs around the cell (cx, cy, cz) (the bit
+// of J in a row's bitmap), or -1 when J lies outside the 5x5x5 cells
+__device__ __forceinline__ int run_bit(const uint32_t *node_cpk, const int32_t *node_rank, int32_t J, int cx, int cy,
+                                       int cz, const int *run_start, const int *run_pre)
+{
+    const uint32_t cj = node_cpk[J];
+    const int dx = (int)(cj & 0x7FF) - cx, dy = (int)((cj >> 11) & 0x7FF) - cy, dz = (int)(cj >> 22) - cz;
+    if (dx < -2 || dx > 2 || dy < -2 || dy > 2 || dz < -2 || dz > 2) return -1;
+    const int r = (dy + 2) + 5 * (dz + 2);
+    return run_pre[r] + (node_rank[J] - run_start[r]);
+}
+
 // instance of point k of a list: inst_of[k >> shift], or 0 without a map
 __device__ __forceinline__ int instance_of(const int32_t *inst_of, int shift, int64_t k)
 {
@@ -120,6 +159,7 @@ struct rpim_pattern {
     int32_t max_support = 0, min_support = 0, max_row = 0;
     int32_t max_incident = 0;  // largest number of (point, entry) pairs per node
     int32_t max_cell = 0;      // largest node count of a grid cell
+    int32_t bit_words = 0;     // 32-bit words of a row bitmap over the 5x5x5 cells around a node
 
     // nodes
     double *xyz = nullptr;          // [n_nodes*3] copy of the coordinates

@@ -366,33 +366,6 @@ __global__ void entry_points_kernel(int64_t n_pts, const int64_t *soff, int32_t 
 // Pass 0 marks the bitmap in shared memory, counts it and keeps it in global
 // memory; pass 1 extracts the kept bitmap, sorts the ids and writes them.
 // ---------------------------------------------------------------------------
-// the 25 runs of cells (dy, dz in [-2, 2], dx in [-2, 2] contiguous) around
-// I's cell: start in the cell-ordered list and exclusive prefix of lengths
-__device__ __forceinline__ int cell_runs(const InstGrid &g, const int32_t *cell_start, int cx, int cy, int cz,
-                                         int lane, int *run_start, int *run_pre)
-{
-    if (lane < 25) {
-        const int dy = lane % 5 - 2, dz = lane / 5 - 2;
-        const int yy = cy + dy, zz = cz + dz;
-        int st = 0, len = 0;
-        if (yy >= 0 && yy < g.n[1] && zz >= 0 && zz < g.n[2]) {
-            const int xa = max(cx - 2, 0), xb = min(cx + 2, g.n[0] - 1);
-            const int64_t row = g.cell_off + (int64_t)g.n[0] * (yy + (int64_t)g.n[1] * zz);
-            st = cell_start[row + xa];
-            len = cell_start[row + xb + 1] - st;
-        }
-        run_start[lane] = st;
-        run_pre[lane + 1] = len;
-    }
-    __syncwarp();
-    if (lane == 0) {
-        run_pre[0] = 0;
-        for (int r = 0; r < 25; r++) run_pre[r + 1] += run_pre[r];
-    }
-    __syncwarp();
-    return run_pre[25];
-}
-
 // pass 0. The (point, support entry) pairs of row I are walked flat: 32
 // incident points at a time, their supports concatenated and dealt to the
 // lanes, so that every lane has independent loads in flight (walking one
@@ -843,6 +816,7 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     RPIM_CHECK(dalloc(&dmax, 1, s));
     RPIM_CHECK(dalloc(&tmp, scan_tmp_size(n), s));
     RPIM_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
+    p->bit_words = words;
     uint32_t *bm = nullptr;   // kept bitmaps of pass 0, [n][words]
     RPIM_CHECK(dalloc(&bm, (int64_t)n * words, s));
     {

@@ -32,6 +32,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -126,12 +127,13 @@ struct PointSmem {
     float *redv;    // [4 passes][4 warps] argmax values
     int *redj;      // [4 passes][4 warps] argmax indices
     int *r2o;       // [NC] rest index -> original index
+    double *piv;    // [2] reciprocal of the next LDL' pivot (0 when not positive)
 };
 
 __host__ __device__ inline int64_t point_smem_doubles(int NC)
 {
     return 3 * NC + (3 * NC + 1) / 2 + 4 * NC + 4 * NC + 4 * NC + (int64_t)NC * (NC + 1) / 2 + 32 + 64 + 8 + 8 +
-           (NC + 1) / 2 + 2;
+           (NC + 1) / 2 + 2 + 2;
 }
 
 __device__ __forceinline__ PointSmem carve(double *base, int NC)
@@ -149,7 +151,8 @@ __device__ __forceinline__ PointSmem carve(double *base, int NC)
     w.red = p; p += 64;
     w.redv = (float *)p; p += 8;
     w.redj = (int *)p; p += 8;
-    w.r2o = (int *)p;
+    w.r2o = (int *)p; p += (NC + 1) / 2;
+    w.piv = p;
     return w;
 }
 
@@ -436,6 +439,7 @@ __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double
                     a = fma(-W.C[k * NC + i], W.Y[k * NC + j], a);
                 }
                 W.S[u] = a;
+                if (u == 0) W.piv[0] = positive_normal(a) ? recip_nr(a) : 0.0;  // first pivot
             }
         }
         for (int t = gt; t < 4 * (m + 4); t += GT) {
@@ -457,11 +461,13 @@ __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double
         const int M2 = m + 4;
         double *col = W.v;
         bool ok = true;
+        //    The reciprocal of each pivot is computed once, by the thread
+        //    that finishes the pivot (u == 0 of the previous update), and read
+        //    from shared memory by the group: replicated in every warp it
+        //    would cost each warp a full FP64 issue slot per instruction.
         for (int k = 0; k < m; k++) {
-            const int kb = k * (k + 1) / 2;
-            const double dkk = W.S[kb + k];
-            if (!positive_normal(dkk)) { ok = false; break; }
-            const double iv = recip_nr(dkk);
+            const double iv = W.piv[0];
+            if (!(iv > 0.0)) { ok = false; break; }
             for (int i = k + 1 + gt; i < M2; i += GT) {
                 const int ik = i * (i + 1) / 2 + k;
                 const double a = W.S[ik];
@@ -476,7 +482,9 @@ __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double
                 tri_decode(u, ri, rj);
                 const int i = k + 1 + ri, j = k + 1 + rj;
                 const int ib = i * (i + 1) / 2;
-                W.S[ib + j] = fma(-W.S[ib + k], col[j], W.S[ib + j]);
+                const double nv = fma(-W.S[ib + k], col[j], W.S[ib + j]);
+                W.S[ib + j] = nv;
+                if (u == 0 && k + 1 < m) W.piv[0] = positive_normal(nv) ? recip_nr(nv) : 0.0;
             }
             group_sync(bar, GT);
         }
@@ -498,35 +506,39 @@ __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double
             group_sync(bar, GT);
         }
 
-        // 9. pivot values a_p = d - C a_r: 16 sums over the rest rows,
-        //    reduce-scattered inside each warp (lane l ends with sum l >> 1),
-        //    then summed over the group's warps in order
-        double v[16];
+        // 9. pivot values a_p = d - C a_r: 16 sums over the rest rows, by the
+        //    group's first warp alone (lane-strided partial sums, then
+        //    reduce-scattered so that lane l ends with sum l >> 1). The
+        //    summation order is therefore the same for every group width G,
+        //    and the other warps issue no FP64 work here.
+        if (wig == 0) {
+            double v[16];
 #pragma unroll
-        for (int k = 0; k < 16; k++) v[k] = 0.0;
-        for (int r = gt; r < m; r += GT) {
-            double ar[4];
+            for (int k = 0; k < 16; k++) v[k] = 0.0;
+            for (int r = lane; r < m; r += 32) {
+                double ar[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) ar[q] = Z0[q * m + q * (q + 1) / 2 + r];
+                for (int q = 0; q < 4; q++) ar[q] = Z0[q * m + q * (q + 1) / 2 + r];
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const double c = W.C[k * NC + r];
+                for (int k = 0; k < 4; k++) {
+                    const double c = W.C[k * NC + r];
 #pragma unroll
-                for (int q = 0; q < 4; q++) v[4 * k + q] = fma(c, ar[q], v[4 * k + q]);
+                    for (int q = 0; q < 4; q++) v[4 * k + q] = fma(c, ar[q], v[4 * k + q]);
+                }
             }
-        }
 #pragma unroll
-        for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
-            const bool up = (lane & bit) != 0;
+            for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
+                const bool up = (lane & bit) != 0;
 #pragma unroll
-            for (int i = 0; i < half; i++) {
-                const double mine = up ? v[i + half] : v[i];
-                const double theirs = up ? v[i] : v[i + half];
-                v[i] = mine + __shfl_xor_sync(0xffffffffu, theirs, bit);
+                for (int i = 0; i < half; i++) {
+                    const double mine = up ? v[i + half] : v[i];
+                    const double theirs = up ? v[i] : v[i + half];
+                    v[i] = mine + __shfl_xor_sync(0xffffffffu, theirs, bit);
+                }
             }
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+            if ((lane & 1) == 0) W.red[lane >> 1] = v[0];
         }
-        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-        if ((lane & 1) == 0) W.red[16 * wig + (lane >> 1)] = v[0];
 
         double *out = phi + 4 * base;
         bool finite = true;
@@ -540,10 +552,8 @@ __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double
         }
         group_sync(bar, GT);
         if (gt < 16) {
-            double sum = W.red[gt];
-            for (int w = 1; w < G; w++) sum += W.red[16 * w + gt];
             const int k = gt >> 2, q = gt & 3;
-            double val = W.M[4 * k + q] - sum;
+            double val = W.M[4 * k + q] - W.red[gt];
             if (q) val *= inv_h;
             finite &= isfinite(val);
             out[4 * pivot(k) + q] = val;
@@ -553,6 +563,58 @@ __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double
     }
 }
 
+// Launch shape of the shape kernel for supports up to NC: ppb point groups
+// of G warps per block. The results do not depend on it (every value is
+// computed by one thread with a fixed formula, the argmax passes break ties
+// by index, and the one reduction runs in the first warp alone), so it is a
+// pure speed choice: a default rule, or what rpim_autotune_shape measured.
+struct ShapeCfg {
+    int ppb = 0, G = 0;
+};
+
+static std::mutex g_tune_mu;
+static ShapeCfg g_tuned[RPIM_MAX_SUPPORT + 1];
+
+static size_t point_bytes(int NC) { return (size_t)point_smem_doubles(NC) * sizeof(double); }
+
+constexpr size_t kShapeSmemBudget = 216 * 1024;
+
+static bool cfg_valid(int NC, ShapeCfg c)
+{
+    return c.G >= 1 && c.G <= 4 && c.ppb >= 1 && c.ppb <= 15 && c.ppb * c.G * 32 <= 1024 &&
+           (size_t)c.ppb * point_bytes(NC) <= kShapeSmemBudget;
+}
+
+static ShapeCfg default_cfg(int NC)
+{
+    ShapeCfg c;
+    c.ppb = (int)std::min<size_t>(15, kShapeSmemBudget / point_bytes(NC));  // points (groups) per block
+    c.G = std::max(1, std::min(4, 32 / std::max(1, c.ppb)));               // warps per point
+    return c;
+}
+
+static ShapeCfg shape_cfg(int NC)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const ShapeCfg t = g_tuned[std::min(NC, RPIM_MAX_SUPPORT)];
+    return cfg_valid(NC, t) ? t : default_cfg(NC);
+}
+
+static rpim_status launch_shape(rpim_pattern *p, int64_t n_pts, const double *pts, const int32_t *inst_of, int shift,
+                                const int32_t *order, const int64_t *soff, const int32_t *sidx, int NC, ShapeCfg c,
+                                double *phi, cudaStream_t s, const char *tag)
+{
+    const size_t smem = (size_t)c.ppb * point_bytes(NC);
+    RPIM_CUDA(cudaFuncSetAttribute(shape_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t blocks = std::min<int64_t>((int64_t)p->sm_count, (n_pts + c.ppb - 1) / c.ppb);
+    if (blocks < 1) blocks = 1;
+    launch(tag, shape_kernel, (unsigned)blocks, c.ppb * c.G * 32, smem, s, n_pts, pts, inst_of, shift,
+           (const InstGrid *)p->ig, order, soff, sidx, (const double *)p->xyz, (const KernelSeries *)p->series, phi,
+           NC, c.G, p->err);
+    RPIM_CUDA(cudaGetLastError());
+    return RPIM_OK;
+}
+
 rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, const int32_t *inst_of, int shift,
                             const int32_t *order, const int64_t *soff, const int32_t *sidx, int32_t max_n,
                             double *phi, cudaStream_t s, const char *tag)
@@ -560,20 +622,8 @@ rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, c
     if (n_pts == 0) return RPIM_OK;
     if (max_n > RPIM_MAX_SUPPORT) return fail(RPIM_E_SUPPORT, "support larger than RPIM_MAX_SUPPORT");
     const int NC = std::max(8, (int)max_n);
-    const size_t per = (size_t)point_smem_doubles(NC) * sizeof(double);
-    const size_t budget = 216 * 1024;
-    int ppb = (int)std::min<size_t>(15, budget / per);  // points (groups) per block
-    if (ppb < 1) return fail(RPIM_E_SUPPORT, "support too large for shared memory");
-    const int G = std::max(1, std::min(4, 32 / ppb));  // warps per point, <= 1024 threads per block
-    const size_t smem = (size_t)ppb * per;
-    RPIM_CUDA(cudaFuncSetAttribute(shape_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int64_t blocks = std::min<int64_t>((int64_t)p->sm_count, (n_pts + ppb - 1) / ppb);
-    if (blocks < 1) blocks = 1;
-    launch(tag, shape_kernel, (unsigned)blocks, ppb * G * 32, smem, s, n_pts, pts, inst_of, shift,
-           (const InstGrid *)p->ig, order, soff, sidx, (const double *)p->xyz, (const KernelSeries *)p->series, phi,
-           NC, G, p->err);
-    RPIM_CUDA(cudaGetLastError());
-    return RPIM_OK;
+    if (point_bytes(NC) > kShapeSmemBudget) return fail(RPIM_E_SUPPORT, "support too large for shared memory");
+    return launch_shape(p, n_pts, pts, inst_of, shift, order, soff, sidx, NC, shape_cfg(NC), phi, s, tag);
 }
 
 rpim_status shape_functions_all(rpim_pattern *p, double *phi, cudaStream_t s)
@@ -590,3 +640,84 @@ rpim_status shape_functions_all(rpim_pattern *p, double *phi, cudaStream_t s)
 }
 
 } // namespace rpim
+
+using namespace rpim;
+
+extern "C" rpim_status rpim_autotune_shape(rpim_pattern *p, int64_t max_points, int32_t *table, int32_t *n_table,
+                                           rpim_stream_t stream)
+{
+    if (!p || max_points < 1) return fail(RPIM_E_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    if (!p->phi) RPIM_CHECK(dalloc(&p->phi, 4 * p->n_entries, s));
+    cudaEvent_t e0, e1;
+    RPIM_CUDA(cudaEventCreate(&e0));
+    RPIM_CUDA(cudaEventCreate(&e1));
+    int nt = 0;
+    int64_t start = 0;
+    rpim_status st = RPIM_OK;
+    for (size_t bk = 0; bk < p->bucket_count.size() && st == RPIM_OK; bk++) {
+        const int64_t cnt = std::min<int64_t>(p->bucket_count[bk], max_points);
+        const int NC = std::max(8, (int)p->bucket_nc[bk]);
+        const int32_t *order = p->bucket_order + start;
+        start += p->bucket_count[bk];
+        if (cnt == 0 || point_bytes(NC) > kShapeSmemBudget) continue;
+        ShapeCfg best = default_cfg(NC);
+        float best_ms = 1e30f;
+        for (int G = 1; G <= 4 && st == RPIM_OK; G++)
+            for (int ppb = 1; ppb <= 15 && st == RPIM_OK; ppb++) {
+                const ShapeCfg c{ppb, G};
+                if (!cfg_valid(NC, c)) continue;
+                // skip launch shapes that cannot fill the SMs' warp slots
+                if (ppb * G < 4 && !(ppb == default_cfg(NC).ppb && G == default_cfg(NC).G)) continue;
+                float ms = 1e30f;
+                for (int rep = 0; rep < 3 && st == RPIM_OK; rep++) {
+                    if (cudaEventRecord(e0, s) != cudaSuccess) { st = fail(RPIM_E_CUDA, "tune: event"); break; }
+                    st = launch_shape(p, cnt, p->pts, p->node_inst, 3, order, p->soff, p->sidx, NC, c, p->phi, s, "tune");
+                    if (st != RPIM_OK) break;
+                    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                        st = fail(RPIM_E_CUDA, "tune: event");
+                        break;
+                    }
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    if (rep > 0) ms = std::min(ms, t);   // the first run warms up
+                }
+                if (ms < best_ms) { best_ms = ms; best = c; }
+            }
+        if (st != RPIM_OK) break;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[std::min(NC, RPIM_MAX_SUPPORT)] = best;
+        }
+        if (table && nt < 16) {
+            table[3 * nt] = NC;
+            table[3 * nt + 1] = best.G;
+            table[3 * nt + 2] = best.ppb;
+        }
+        nt++;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_table) *n_table = nt;
+    RPIM_CHECK(st);
+    return check_device_error(p, "autotune");
+}
+
+extern "C" rpim_status rpim_autotune_set(int32_t max_support, int32_t warps_per_point, int32_t points_per_block)
+{
+    const int NC = std::max(8, (int)max_support);
+    const ShapeCfg c{points_per_block, warps_per_point};
+    if (max_support < 1 || max_support > RPIM_MAX_SUPPORT || !cfg_valid(NC, c))
+        return fail(RPIM_E_ARG, "launch shape not admissible for this support size");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[NC] = c;
+    return RPIM_OK;
+}
+
+extern "C" rpim_status rpim_autotune_reset(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &c : g_tuned) c = ShapeCfg{};
+    return RPIM_OK;
+}

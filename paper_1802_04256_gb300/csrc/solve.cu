@@ -134,12 +134,13 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket)
     return amlast;
 }
 
-// y_I = (K x)_I for one block row by one warp; returns x_I . y_I (every lane).
-// Lane l multiplies blocks l, l + 32, ... of the row. The product is bound
-// by the FP64 pipe on this chip (9 DFMA per 76-byte block against a 2 DFMA
-// per clock per SM rate), not by HBM: staging the blocks through shared
-// memory for coalesced loads was measured to gain nothing, so the loads
-// stay plain.
+// y_I = (K x)_I for one block row by one warp; returns x_I . y_I (valid in
+// lane 0). Lane l multiplies blocks l, l + 32, ... of the row. The product
+// is bound by the FP64 pipe on this chip (9 DFMA per 76-byte block against a
+// 2 DFMA per clock per SM rate), not by HBM: staging the blocks through
+// shared memory for coalesced loads was measured to gain nothing, so the
+// loads stay plain, and the three row sums are reduce-scattered (6 FP64
+// additions per row instead of 15 for three butterfly reductions).
 __device__ __forceinline__ double bsr_row(int64_t I, const int64_t *rowptr, const int32_t *cols, const double *K,
                                           const double *x, double *y, int lane)
 {
@@ -153,18 +154,28 @@ __device__ __forceinline__ double bsr_row(int64_t I, const int64_t *rowptr, cons
         a1 = fma(b[3], x0, fma(b[4], x1, fma(b[5], x2, a1)));
         a2 = fma(b[6], x0, fma(b[7], x1, fma(b[8], x2, a2)));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    // lanes 0-15 keep components (0, 1), lanes 16-31 keep (2, -)
+    const bool hi16 = (lane & 16) != 0;
+    double s0 = hi16 ? a2 : a0, s1 = hi16 ? 0.0 : a1;
+    s0 += __shfl_xor_sync(0xffffffffu, hi16 ? a0 : a2, 16);
+    s1 += __shfl_xor_sync(0xffffffffu, hi16 ? a1 : 0.0, 16);
+    // lanes with bit 3 clear keep the first of the two, the others the second
+    const bool hi8 = (lane & 8) != 0;
+    double v = hi8 ? s1 : s0;
+    v += __shfl_xor_sync(0xffffffffu, hi8 ? s0 : s1, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    // lanes 0, 8, 16 now hold components 0, 1, 2 of the row (lanes 24-31: 0)
+    const int c = lane >> 3;
+    double d = 0.0;
+    if ((lane & 7) == 0 && c < 3) {
+        y[3 * I + c] = v;
+        d = v * x[3 * I + c];
     }
-    if (lane == 0) {
-        y[3 * I] = a0;
-        y[3 * I + 1] = a1;
-        y[3 * I + 2] = a2;
-    }
-    return a0 * x[3 * I] + a1 * x[3 * I + 1] + a2 * x[3 * I + 2];
+    d += __shfl_xor_sync(0xffffffffu, d, 8);
+    d += __shfl_xor_sync(0xffffffffu, d, 16);
+    return d;
 }
 
 // r = f - K x, z = Dinv r, p = z; partials of r.z, r.r, f.f
