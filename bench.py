@@ -317,7 +317,7 @@ def _backanalysis(dev, stream, rtol=1e-10):
 
 
 # --------------------------------------------------------------------------- batched vs per-instance
-def _batched(n_sel, dev, stream, reps=1):
+def _batched(n_sel, dev, stream, reps=1, warm=1):
     """Blocks of the 512-instance batched workload (node counts log-uniform in
     500-20,000, alpha_s uniform in [2, 3.5]), every (512 / n_sel)-th one:
     one batched pattern + assembly + loads + per-instance penalty + batched
@@ -392,8 +392,9 @@ def _batched(n_sel, dev, stream, reps=1):
     tp = R.Pattern(bx, blo, bhi, None, sel[0].alpha_c, sel[0].q, None, instances=inst)
     tp.autotune(max_points=20000)
     tp.free()
-    run_batched()
-    run_single()
+    for _ in range(warm):
+        run_batched()
+        run_single()
     l0 = R.rpim_kernel_launches()
     bres = [run_batched() for _ in range(reps)]
     lb = (R.rpim_kernel_launches() - l0) / reps
@@ -565,7 +566,7 @@ def run_ours(args, rank, world, local_rank):
 
     batched = None
     if args.batched_instances > 0:
-        batched = _batched(args.batched_instances, dev, stream)
+        batched = _batched(args.batched_instances, dev, stream, warm=args.batched_warmup)
     grad = None
     if not args.no_grad:
         grad = _backanalysis(dev, stream)
@@ -602,6 +603,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the penalty + PCG measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the back-analysis gradient measurement")
+    ap.add_argument("--batched-warmup", type=int, default=1,
+                    help="untimed runs of each arm of the batched comparison before the timed one")
     ap.add_argument("--no-autotune", action="store_true", help="use the built-in launch shapes of the shape kernel")
     ap.add_argument("--solve-iters", type=int, default=0,
                     help="run the solve for exactly this many PCG iterations (profiling; 0 = to rtol 1e-10)")
