@@ -154,6 +154,24 @@ def _traffic_for(kernel, source):
     return None
 
 
+# --------------------------------------------------------------------------- ranks
+def max_over_ranks(x, dist, device):
+    """The largest value of a per-rank host float over all ranks (the
+    slowest replica sets the time); the value itself with one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second, every rank doing
+    `units_per_rank` in `ms` milliseconds (weak scaling: replicas)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 # --------------------------------------------------------------------------- CPU baseline
 def cpu_baseline(p, budget_s=15.0):
     """The oracle (FP64, OpenMP over points on all host cores) on the first M
@@ -484,12 +502,8 @@ def run_ours(args, rank, world, local_rank):
     R.rpim_profile_enable(False)
     prof = R.rpim_profile_read(reset=True)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        tms = torch.tensor([ms], device=dev)
-        dist.all_reduce(tms, op=dist.ReduceOp.MAX)
-        ms = float(tms.item())
-    value = world * p.n_points / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+    value = whole_job_rate(p.n_points, world, ms)
 
     # ---- roofline of the dominant kernel (largest device time)
     pat = R.Pattern(xyz, lo, hi, p.alpha_s, p.alpha_c, p.q, p.h)
@@ -556,12 +570,8 @@ def run_ours(args, rank, world, local_rank):
             d2h = e2e_step()
         torch.cuda.synchronize()
         barrier()
-        e2e_ms = 1e3 * (time.perf_counter() - t0) / n_e2e
-        if dist is not None:
-            tms = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(tms, op=dist.ReduceOp.MAX)
-            e2e_ms = float(tms.item())
-        e2e = {"value": world * p.n_points / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / n_e2e, dist, dev)
+        e2e = {"value": whole_job_rate(p.n_points, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
     batched = None

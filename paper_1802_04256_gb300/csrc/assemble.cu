@@ -46,9 +46,12 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t 
 
 // Row kernel. One warp owns row I and accumulates the upper blocks (J >= I)
 // of its row in place in K (L2-resident read-modify-write; every block is
-// touched by one lane at a time, in ascending point order). Accumulating in
-// shared memory instead was measured slower: the buffers leave room for
-// half as many warps, and the kernel needs them to cover its load latency. Per-point scalars
+// touched by one lane at a time, in ascending point order). The warps of a
+// wave keep their rows' upper blocks (about 19 KB a row on the cantilever)
+// in L2, so the number of resident warps is a trade: 16 per SM (2 blocks,
+// 100 registers) measured 27 ms on the cantilever; 8 (shared-memory
+// accumulators) 34 ms; 32 (a 64-register split into uniform and general
+// kernels) 94 ms, the L2 thrashing on 92 MB of blocks in flight. Per-point scalars
 // are prefetched 32 points at a time, one point per lane, and broadcast by
 // shuffles. The block slot of a column J is looked up in a per-warp shared
 // table indexed by J's position in the 25 cell runs around I (the same
