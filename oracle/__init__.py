@@ -65,6 +65,10 @@ def lib(kind: str = "f64"):
     L.orc_support_radius2.restype = dbl
     L.orc_shape.argtypes = [_D, _I32, i32, _D, dbl, dbl, dbl, _D]
     L.orc_shape.restype = i32
+    L.orc_shape_mls.argtypes = [_D, _I32, i32, _D, dbl, dbl, _D]
+    L.orc_shape_mls.restype = i32
+    L.orc_set_shape.argtypes = [i32]
+    L.orc_get_shape.restype = i32
     L.orc_assemble.argtypes = [i64, _D, i64, _D, _D, _D, _D, vp, dbl, dbl, dbl, dbl, i32]
     L.orc_assemble.restype = vp
     L.orc_free.argtypes = [vp]
@@ -102,6 +106,30 @@ class OracleError(RuntimeError):
 
 def set_threads(t: int, kind: str = "f64") -> None:
     lib(kind).orc_set_threads(int(t))
+
+
+SHAPES = {"rpim": 0, "mls": 1}
+
+
+class shape_kind:
+    """Context manager selecting the shape functions of every assembly-level
+    oracle function (assemble, point_loads, stress, grad_material, and the
+    *_problem helpers) in every registered build:
+    ``with oracle.shape_kind("mls"): ...``"""
+
+    def __init__(self, name: str):
+        self.code = SHAPES[name]
+
+    def __enter__(self):
+        self.saved = {k: lib(k).orc_get_shape() for k in LIBS}
+        for k in LIBS:
+            lib(k).orc_set_shape(self.code)
+        return self
+
+    def __exit__(self, *exc):
+        for k, v in self.saved.items():
+            lib(k).orc_set_shape(v)
+        return False
 
 
 def gauss_points(cell_lo, cell_hi, kind="f64"):
@@ -161,6 +189,17 @@ class Model:
         np.add.at(out, rows, y)
         return out.ravel()
 
+
+
+def shape_mls(xyz, supp, x, h, alpha_s, kind="f64"):
+    """MLS shape functions (linear basis, cubic-spline weight of radius
+    alpha_s h) at x: array [4, n] (phi, dphi/dx, dphi/dy, dphi/dz)."""
+    xyz, s = _c(xyz), _c(supp, np.int32)
+    out = np.zeros(4 * len(s))
+    st = lib(kind).orc_shape_mls(xyz, s, len(s), _c(x), h, alpha_s, out)
+    if st != 0:
+        raise OracleError(st, "shape_mls")
+    return out.reshape(4, len(s))
 
 def assemble(xyz, pts, wj, E, nu, alpha_s, alpha_c, q, h, body=None, kind="f64",
              max_support=MAX_SUPPORT):

@@ -24,6 +24,14 @@
  *        P[i] = [1, xi_i],
  *    solve G z = [R(x); p(x)] and its derivatives; phi = the first n entries.
  *    Own Gaussian elimination with partial pivoting.
+ *  - Shape functions, MLS variant (the paper names moving least squares only
+ *    as future work, Sec. 4; selected with orc_set_shape(1)): textbook MLS
+ *    with the linear basis p = [1, xi] and the cubic-spline weight
+ *    w(r / r_s) on the same support radius. A(x) = sum_i w_i p_i p_i^T,
+ *    gamma = A^-1 p(x), phi_i = w_i p_i^T gamma, and for the derivatives
+ *    dgamma/dx_k = A^-1 (dp/dx_k - dA/dx_k gamma),
+ *    dphi_i/dx_k = dw_i/dx_k p_i^T gamma + w_i p_i^T dgamma/dx_k.
+ *    Own Gaussian elimination with partial pivoting on the 4x4 system.
  *  - Point stiffness: K_IJ += w |J| B_I^T D B_J with the 6x3 strain matrix B_I
  *    (Voigt xx, yy, zz, yz, xz, xy; engineering shear strains) and isotropic
  *    D(E, nu). Every block (I, J) is formed on its own (no mirroring), and
@@ -66,9 +74,12 @@ enum { ORC_OK = 0, ORC_E_ARG = 1, ORC_E_OOM = 3, ORC_E_SUPPORT = 4, ORC_E_SINGUL
        ORC_E_NOCONV = 6 };
 
 static int g_threads = 1;
+static int g_shape = 0;   /* 0: RPIM, 1: MLS */
 
 int orc_real_bytes(void) { return (int)sizeof(real); }
 void orc_set_threads(int t) { g_threads = t > 0 ? t : 1; }
+void orc_set_shape(int kind) { g_shape = kind == 1 ? 1 : 0; }
+int orc_get_shape(void) { return g_shape; }
 
 /* ---------------------------------------------------------------------------
  * Integration points: 2x2x2 Gauss-Legendre rule on every node cell.
@@ -133,8 +144,8 @@ double orc_support_radius2(double alpha_s, double h)
  * 0, n, 2n, 3n.  Returns ORC_E_SINGULAR when a pivot falls below
  * 1e-13 * max|G|.
  * ------------------------------------------------------------------------- */
-static int shape_real(const double *xyz, const int32_t *supp, int n, const double *x,
-                      double h, double alpha_c, double q, real *phi_out /* 4*n */)
+static int shape_rpim_real(const double *xyz, const int32_t *supp, int n, const double *x,
+                           double h, double alpha_c, double q, real *phi_out /* 4*n */)
 {
     const int N = n + 4;
     real *G = (real *)calloc((size_t)N * N, sizeof(real));
@@ -228,11 +239,151 @@ int orc_shape(const double *xyz, const int32_t *supp, int n, const double *x, do
     if (n < 1) return ORC_E_SUPPORT;
     real *tmp = (real *)malloc((size_t)4 * n * sizeof(real));
     if (!tmp) return ORC_E_OOM;
-    int st = shape_real(xyz, supp, n, x, h, alpha_c, q, tmp);
+    int st = shape_rpim_real(xyz, supp, n, x, h, alpha_c, q, tmp);
     if (st == ORC_OK)
         for (int t = 0; t < 4 * n; t++) phi[t] = (double)tmp[t];
     free(tmp);
     return st;
+}
+
+/* ---------------------------------------------------------------------------
+ * MLS shape functions at x (the variant; see the header). Cubic spline
+ * weight of sb = |x_i - x| / r_s:
+ *   w = 2/3 - 4 sb^2 + 4 sb^3             (sb <= 1/2)
+ *   w = 4/3 - 4 sb + 4 sb^2 - 4/3 sb^3    (1/2 < sb <= 1),  0 beyond,
+ * and w'(sb) its derivative. Output layout as for RPIM. Returns
+ * ORC_E_SINGULAR when a pivot of A falls below 1e-13 * max|A|.
+ * ------------------------------------------------------------------------- */
+static void spline(real sb, real *w, real *dw)
+{
+    if (sb <= (real)0.5) {
+        *w = (real)2 / 3 - 4 * sb * sb + 4 * sb * sb * sb;
+        *dw = -8 * sb + 12 * sb * sb;
+    } else if (sb <= 1) {
+        *w = (real)4 / 3 - 4 * sb + 4 * sb * sb - (real)4 / 3 * sb * sb * sb;
+        *dw = -4 + 8 * sb - 4 * sb * sb;
+    } else {
+        *w = 0;
+        *dw = 0;
+    }
+}
+
+/* solve the 4x4 system M y = r for 4 right-hand sides (columns of R, 4x4,
+ * overwritten with the solutions); partial pivoting, lowest row on ties */
+static int solve4(real M[4][4], real R[4][4])
+{
+    real amax = 0;
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) if (RABS(M[i][j]) > amax) amax = RABS(M[i][j]);
+    for (int k = 0; k < 4; k++) {
+        int p = k;
+        for (int i = k + 1; i < 4; i++) if (RABS(M[i][k]) > RABS(M[p][k])) p = i;
+        if (RABS(M[p][k]) < (real)1e-13 * amax) return ORC_E_SINGULAR;
+        for (int j = 0; j < 4; j++) {
+            real t = M[k][j]; M[k][j] = M[p][j]; M[p][j] = t;
+            t = R[k][j]; R[k][j] = R[p][j]; R[p][j] = t;
+        }
+        for (int i = k + 1; i < 4; i++) {
+            real l = M[i][k] / M[k][k];
+            for (int j = k; j < 4; j++) M[i][j] -= l * M[k][j];
+            for (int j = 0; j < 4; j++) R[i][j] -= l * R[k][j];
+        }
+    }
+    for (int k = 3; k >= 0; k--)
+        for (int j = 0; j < 4; j++) {
+            real s = R[k][j];
+            for (int i = k + 1; i < 4; i++) s -= M[k][i] * R[i][j];
+            R[k][j] = s / M[k][k];
+        }
+    return ORC_OK;
+}
+
+static int shape_mls_real(const double *xyz, const int32_t *supp, int n, const double *x, double h,
+                          double alpha_s, real *phi_out /* 4*n */)
+{
+    real *xi = (real *)malloc((size_t)n * 3 * sizeof(real));
+    real *w = (real *)malloc((size_t)n * 4 * sizeof(real)); /* w_i, dw_i/dx_k */
+    if (!xi || !w) { free(xi); free(w); return ORC_E_OOM; }
+    const real hr = (real)h, as = (real)alpha_s;
+    real A[4][4], dA[3][4][4];
+    memset(A, 0, sizeof A);
+    memset(dA, 0, sizeof dA);
+    for (int i = 0; i < n; i++) {
+        real d2 = 0;
+        for (int k = 0; k < 3; k++) {
+            xi[3 * i + k] = ((real)xyz[3 * (int64_t)supp[i] + k] - (real)x[k]) / hr;
+            d2 += xi[3 * i + k] * xi[3 * i + k];
+        }
+        const real d = RSQRT(d2), sb = d / as;
+        real wv, dws;
+        spline(sb, &wv, &dws);
+        w[4 * i] = wv;
+        for (int k = 0; k < 3; k++) /* d sb / d x_k = -xi_k / (alpha_s h |xi|) */
+            w[4 * i + 1 + k] = d > 0 ? dws * (-xi[3 * i + k]) / (as * hr * d) : 0;
+        const real p[4] = {1, xi[3 * i], xi[3 * i + 1], xi[3 * i + 2]};
+        for (int a = 0; a < 4; a++)
+            for (int c = 0; c < 4; c++) {
+                A[a][c] += wv * p[a] * p[c];
+                for (int k = 0; k < 3; k++) dA[k][a][c] += w[4 * i + 1 + k] * p[a] * p[c];
+            }
+    }
+    /* gamma = A^-1 p(x), p(x) = e0 (x is the origin of xi) */
+    real M[4][4], R[4][4];
+    memcpy(M, A, sizeof M);
+    memset(R, 0, sizeof R);
+    R[0][0] = 1;
+    int st = solve4(M, R);
+    real gam[4], dgam[3][4];
+    if (st == ORC_OK) {
+        for (int a = 0; a < 4; a++) gam[a] = R[a][0];
+        /* dgamma/dx_k = A^-1 (dp/dx_k - dA/dx_k gamma), dp/dx_k = e_{k+1} / h */
+        memcpy(M, A, sizeof M);
+        memset(R, 0, sizeof R);
+        for (int k = 0; k < 3; k++)
+            for (int a = 0; a < 4; a++) {
+                real s = (a == k + 1) ? 1 / hr : 0;
+                for (int c = 0; c < 4; c++) s -= dA[k][a][c] * gam[c];
+                R[a][k] = s;
+            }
+        st = solve4(M, R);
+        for (int k = 0; k < 3; k++)
+            for (int a = 0; a < 4; a++) dgam[k][a] = R[a][k];
+    }
+    if (st == ORC_OK)
+        for (int i = 0; i < n; i++) {
+            const real p[4] = {1, xi[3 * i], xi[3 * i + 1], xi[3 * i + 2]};
+            real pg = 0;
+            for (int a = 0; a < 4; a++) pg += p[a] * gam[a];
+            phi_out[i] = w[4 * i] * pg;
+            for (int k = 0; k < 3; k++) {
+                real pdg = 0;
+                for (int a = 0; a < 4; a++) pdg += p[a] * dgam[k][a];
+                phi_out[(size_t)(1 + k) * n + i] = w[4 * i + 1 + k] * pg + w[4 * i] * pdg;
+            }
+        }
+    free(xi); free(w);
+    return st;
+}
+
+int orc_shape_mls(const double *xyz, const int32_t *supp, int n, const double *x, double h,
+                  double alpha_s, double *phi)
+{
+    if (n < 1) return ORC_E_SUPPORT;
+    real *tmp = (real *)malloc((size_t)4 * n * sizeof(real));
+    if (!tmp) return ORC_E_OOM;
+    int st = shape_mls_real(xyz, supp, n, x, h, alpha_s, tmp);
+    if (st == ORC_OK)
+        for (int t = 0; t < 4 * n; t++) phi[t] = (double)tmp[t];
+    free(tmp);
+    return st;
+}
+
+/* the shape functions selected by orc_set_shape */
+static int shape_real(const double *xyz, const int32_t *supp, int n, const double *x, double h,
+                      double alpha_s, double alpha_c, double q, real *phi_out)
+{
+    if (g_shape == 1) return shape_mls_real(xyz, supp, n, x, h, alpha_s, phi_out);
+    return shape_rpim_real(xyz, supp, n, x, h, alpha_c, q, phi_out);
 }
 
 /* ---------------------------------------------------------------------------
@@ -392,7 +543,7 @@ orc_model *orc_assemble(int64_t n_nodes, const double *xyz, int64_t n_pts, const
 #pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
     for (int64_t g = 0; g < n_pts; g++) {
         int n = (int)(m->soff[g + 1] - m->soff[g]);
-        int st = shape_real(xyz, m->sidx + m->soff[g], n, pts + 3 * g, h, alpha_c, q,
+        int st = shape_real(xyz, m->sidx + m->soff[g], n, pts + 3 * g, h, alpha_s, alpha_c, q,
                             phis + 4 * m->soff[g]);
         if (st != ORC_OK) {
 #pragma omp critical
@@ -476,7 +627,7 @@ int orc_point_loads(int64_t n_nodes, const double *xyz, int64_t n, const double 
     for (int64_t p = 0; p < n && st == ORC_OK; p++) {
         int64_t c = orc_support(n_nodes, xyz, pts + 3 * p, rs2, s, max_support);
         if (c < 4 || c > max_support) { st = ORC_E_SUPPORT; break; }
-        st = shape_real(xyz, s, (int)c, pts + 3 * p, h, alpha_c, q, ph);
+        st = shape_real(xyz, s, (int)c, pts + 3 * p, h, alpha_s, alpha_c, q, ph);
         if (st != ORC_OK) break;
         for (int64_t a = 0; a < c; a++)
             for (int k = 0; k < 3; k++) acc[3 * (int64_t)s[a] + k] += ph[a] * (real)force[3 * p + k];
@@ -632,7 +783,7 @@ int orc_grad_material(int64_t n_nodes, const double *xyz, int64_t n_pts, const d
     for (int64_t p = 0; p < n_pts; p++) {
         int64_t c = orc_support(n_nodes, xyz, pts + 3 * p, rs2, s, max_support);
         if (c < 4 || c > max_support) { st = ORC_E_SUPPORT; break; }
-        st = shape_real(xyz, s, (int)c, pts + 3 * p, h, alpha_c, q, ph);
+        st = shape_real(xyz, s, (int)c, pts + 3 * p, h, alpha_s, alpha_c, q, ph);
         if (st != ORC_OK) break;
         real eu[6] = {0, 0, 0, 0, 0, 0}, el[6] = {0, 0, 0, 0, 0, 0};
         for (int64_t a = 0; a < c; a++) {
@@ -676,7 +827,7 @@ int orc_stress(int64_t n_nodes, const double *xyz, const double *u, int64_t n_pt
     for (int64_t p = 0; p < n_pts; p++) {
         int64_t c = orc_support(n_nodes, xyz, pts + 3 * p, rs2, s, max_support);
         if (c < 4 || c > max_support) { st = ORC_E_SUPPORT; break; }
-        st = shape_real(xyz, s, (int)c, pts + 3 * p, h, alpha_c, q, ph);
+        st = shape_real(xyz, s, (int)c, pts + 3 * p, h, alpha_s, alpha_c, q, ph);
         if (st != ORC_OK) break;
         real eps[6] = {0, 0, 0, 0, 0, 0};
         for (int64_t a = 0; a < c; a++) {
