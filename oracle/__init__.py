@@ -67,6 +67,8 @@ def lib(kind: str = "f64"):
     L.orc_shape.restype = i32
     L.orc_shape_mls.argtypes = [_D, _I32, i32, _D, dbl, dbl, _D]
     L.orc_shape_mls.restype = i32
+    L.orc_shape_shepard.argtypes = [_D, _I32, i32, _D, dbl, dbl, _D]
+    L.orc_shape_shepard.restype = i32
     L.orc_set_shape.argtypes = [i32]
     L.orc_get_shape.restype = i32
     L.orc_assemble.argtypes = [i64, _D, i64, _D, _D, _D, _D, vp, dbl, dbl, dbl, dbl, i32]
@@ -108,7 +110,7 @@ def set_threads(t: int, kind: str = "f64") -> None:
     lib(kind).orc_set_threads(int(t))
 
 
-SHAPES = {"rpim": 0, "mls": 1}
+SHAPES = {"rpim": 0, "mls": 1, "shepard": 2}
 
 
 class shape_kind:
@@ -199,6 +201,17 @@ def shape_mls(xyz, supp, x, h, alpha_s, kind="f64"):
     st = lib(kind).orc_shape_mls(xyz, s, len(s), _c(x), h, alpha_s, out)
     if st != 0:
         raise OracleError(st, "shape_mls")
+    return out.reshape(4, len(s))
+
+
+def shape_shepard(xyz, supp, x, h, alpha_s, kind="f64"):
+    """Shepard shape functions (constant basis, the same cubic-spline weight)
+    at x: array [4, n] (phi, dphi/dx, dphi/dy, dphi/dz)."""
+    xyz, s = _c(xyz), _c(supp, np.int32)
+    out = np.zeros(4 * len(s))
+    st = lib(kind).orc_shape_shepard(xyz, s, len(s), _c(x), h, alpha_s, out)
+    if st != 0:
+        raise OracleError(st, "shape_shepard")
     return out.reshape(4, len(s))
 
 def assemble(xyz, pts, wj, E, nu, alpha_s, alpha_c, q, h, body=None, kind="f64",

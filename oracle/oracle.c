@@ -32,6 +32,10 @@
  *    dgamma/dx_k = A^-1 (dp/dx_k - dA/dx_k gamma),
  *    dphi_i/dx_k = dw_i/dx_k p_i^T gamma + w_i p_i^T dgamma/dx_k.
  *    Own Gaussian elimination with partial pivoting on the 4x4 system.
+ *  - Shape functions, Shepard variant (also named as future work, Sec. 4;
+ *    orc_set_shape(2)): inverse-distance weighting with the same cubic-spline
+ *    weight, phi_i = w_i / sum_j w_j, i.e. moving least squares with the
+ *    constant basis p = [1]; reproduces constants only.
  *  - Point stiffness: K_IJ += w |J| B_I^T D B_J with the 6x3 strain matrix B_I
  *    (Voigt xx, yy, zz, yz, xz, xy; engineering shear strains) and isotropic
  *    D(E, nu). Every block (I, J) is formed on its own (no mirroring), and
@@ -74,11 +78,11 @@ enum { ORC_OK = 0, ORC_E_ARG = 1, ORC_E_OOM = 3, ORC_E_SUPPORT = 4, ORC_E_SINGUL
        ORC_E_NOCONV = 6 };
 
 static int g_threads = 1;
-static int g_shape = 0;   /* 0: RPIM, 1: MLS */
+static int g_shape = 0;   /* 0: RPIM, 1: MLS, 2: Shepard */
 
 int orc_real_bytes(void) { return (int)sizeof(real); }
 void orc_set_threads(int t) { g_threads = t > 0 ? t : 1; }
-void orc_set_shape(int kind) { g_shape = kind == 1 ? 1 : 0; }
+void orc_set_shape(int kind) { g_shape = (kind == 1 || kind == 2) ? kind : 0; }
 int orc_get_shape(void) { return g_shape; }
 
 /* ---------------------------------------------------------------------------
@@ -378,11 +382,61 @@ int orc_shape_mls(const double *xyz, const int32_t *supp, int n, const double *x
     return st;
 }
 
+/* ---------------------------------------------------------------------------
+ * Shepard shape functions at x: phi_i = w_i / W with W = sum_j w_j and the
+ * cubic-spline weights of the MLS variant; by the quotient rule
+ *   dphi_i/dx_k = (dw_i/dx_k - phi_i dW/dx_k) / W.
+ * Returns ORC_E_SINGULAR when no node carries a positive weight.
+ * ------------------------------------------------------------------------- */
+static int shape_shepard_real(const double *xyz, const int32_t *supp, int n, const double *x, double h,
+                              double alpha_s, real *phi_out /* 4*n */)
+{
+    const real hr = (real)h, as = (real)alpha_s;
+    real W = 0, dW[3] = {0, 0, 0};
+    for (int pass = 0; pass < 2; pass++) {
+        for (int i = 0; i < n; i++) {
+            real xi[3], d2 = 0;
+            for (int k = 0; k < 3; k++) {
+                xi[k] = ((real)xyz[3 * (int64_t)supp[i] + k] - (real)x[k]) / hr;
+                d2 += xi[k] * xi[k];
+            }
+            const real d = RSQRT(d2), sb = d / as;
+            real wv, dws, dw[3];
+            spline(sb, &wv, &dws);
+            for (int k = 0; k < 3; k++) dw[k] = d > 0 ? dws * (-xi[k]) / (as * hr * d) : 0;
+            if (pass == 0) {
+                W += wv;
+                for (int k = 0; k < 3; k++) dW[k] += dw[k];
+            } else {
+                const real ph = wv / W;
+                phi_out[i] = ph;
+                for (int k = 0; k < 3; k++) phi_out[(size_t)(1 + k) * n + i] = (dw[k] - ph * dW[k]) / W;
+            }
+        }
+        if (pass == 0 && !(W > 0)) return ORC_E_SINGULAR;
+    }
+    return ORC_OK;
+}
+
+int orc_shape_shepard(const double *xyz, const int32_t *supp, int n, const double *x, double h,
+                      double alpha_s, double *phi)
+{
+    if (n < 1) return ORC_E_SUPPORT;
+    real *tmp = (real *)malloc((size_t)4 * n * sizeof(real));
+    if (!tmp) return ORC_E_OOM;
+    int st = shape_shepard_real(xyz, supp, n, x, h, alpha_s, tmp);
+    if (st == ORC_OK)
+        for (int t = 0; t < 4 * n; t++) phi[t] = (double)tmp[t];
+    free(tmp);
+    return st;
+}
+
 /* the shape functions selected by orc_set_shape */
 static int shape_real(const double *xyz, const int32_t *supp, int n, const double *x, double h,
                       double alpha_s, double alpha_c, double q, real *phi_out)
 {
     if (g_shape == 1) return shape_mls_real(xyz, supp, n, x, h, alpha_s, phi_out);
+    if (g_shape == 2) return shape_shepard_real(xyz, supp, n, x, h, alpha_s, phi_out);
     return shape_rpim_real(xyz, supp, n, x, h, alpha_c, q, phi_out);
 }
 
