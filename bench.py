@@ -287,6 +287,52 @@ def _solve(pat, p, E, nu, lxyz, lf, tt, stream, peak_gflops, fixed_iters=0):
     return out
 
 
+# --------------------------------------------------------------------------- MLS variant
+def _mls(p, xyz, lo, hi, E, nu, lxyz, lf, stream, peak_gflops, steps=3):
+    """The same assembly step with MLS shape functions (linear basis,
+    cubic-spline weight; the variant Sec. 4 plans): rpim_build_pattern +
+    rpim_pattern_set_shape(MLS) + rpim_assemble + rpim_add_point_loads,
+    device-resident inputs, CUDA events on the launching stream, per-kernel
+    device times from the library's own event timing."""
+    import torch
+    import paper_1802_04256_gb300 as R
+
+    def step():
+        pat = R.Pattern(xyz, lo, hi, p.alpha_s, p.alpha_c, p.q, p.h, shape="mls")
+        K, f = pat.assemble(E, nu)
+        pat.add_point_loads(lxyz, lf, f)
+        pat.free()
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    R.rpim_profile_read(reset=True)
+    R.rpim_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    R.rpim_profile_enable(False)
+    prof = R.rpim_profile_read(reset=True)
+    ms = e0.elapsed_time(e1) / steps
+    pat = R.Pattern(xyz, lo, hi, p.alpha_s, p.alpha_c, p.q, p.h)
+    nsup = np.diff(pat.points()[2].cpu().numpy())
+    pat.free()
+    roof = None
+    if "row" in prof:
+        nl, tot = prof["row"]
+        ach = pair_flops(nsup).sum() / (tot / steps / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "row", "achieved": ach, "peak": peak_gflops / 1e3, "unit": "TFLOP/s",
+                "frac": ach * 1e3 / peak_gflops, "peak_source": "FP64 DFMA throughput measured in this run"}
+    return {"step": "rpim_build_pattern + rpim_pattern_set_shape(MLS) + rpim_assemble + rpim_add_point_loads",
+            "workload": WORKLOAD.replace("MQ alpha_c 4.0 q 1.03", "MLS linear basis, cubic-spline weight"),
+            "steps": steps, "ms_per_step": ms, "pts_per_s": p.n_points / (ms / 1e3),
+            "kernel_ms_per_step": {k: round(v[1] / steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "roofline_row_kernel": roof}
+
+
 # --------------------------------------------------------------------------- differentiable solve
 def _backanalysis(dev, stream, rtol=1e-10):
     """One gradient of the back-analysis misfit L = 1/2 sum |u - u_obs|^2 at
@@ -405,9 +451,10 @@ def _batched(n_sel, dev, stream, reps=1, warm=1):
             its.append(it)
         return ta, ts, us, its
 
-    # setup, untimed: tune the shape kernel's launch shapes on this batch's
-    # support-size buckets (the table is shared by both arms)
+    # setup, untimed: tune the bucket bounds and the shape kernel's launch
+    # shapes on this batch's support sizes (process-wide: both arms use them)
     tp = R.Pattern(bx, blo, bhi, None, sel[0].alpha_c, sel[0].q, None, instances=inst)
+    bounds = tp.autotune_buckets(max_points=200000)
     tp.autotune(max_points=20000)
     tp.free()
     for _ in range(warm):
@@ -426,6 +473,47 @@ def _batched(n_sel, dev, stream, reps=1, warm=1):
     du = max(float(torch.linalg.norm(ub[3 * offs[k]:3 * offs[k + 1]] - us[k]) / torch.linalg.norm(us[k]))
              for k in range(len(sel)))
     npts = int(sum(p.n_points for p in sel))
+
+    # re-assembly with new material, patterns built beforehand (the repeated
+    # assembly of a parameter study or a back-analysis): the batched pattern
+    # replays its captured graph (one persistent shape launch over all
+    # buckets); the per-instance arm calls rpim_assemble on each instance's
+    # own pattern. Only the assembly calls are timed.
+    pat = R.Pattern(bx, blo, bhi, None, sel[0].alpha_c, sel[0].q, None, instances=inst)
+    Kb, fb = pat.assemble_graphed(bE, bnu)
+    l0 = R.rpim_kernel_launches()
+    rb = [timed(lambda: pat.assemble_graphed(bE, bnu, K=Kb, f=fb))[0] for _ in range(2)]
+    lrb = (R.rpim_kernel_launches() - l0) / 2
+    # per-kernel device times of one more assembly (plain launches while
+    # timing is on) and the algorithmic flops of the batch's supports
+    R.rpim_profile_read(reset=True)
+    R.rpim_profile_enable(True)
+    pat.assemble_graphed(bE, bnu, K=Kb, f=fb)
+    R.rpim_profile_enable(False)
+    kprof = R.rpim_profile_read(reset=True)
+    nsup = np.diff(pat.points()[2].cpu().numpy())
+    fl_shape, fl_pair = float(shape_flops(nsup).sum()), float(pair_flops(nsup).sum())
+    pat.free()
+    del Kb, fb
+    rs, lrs = 0.0, 0
+    for p, d in zip(sel, single):
+        pt = R.Pattern(d["x"], d["lo"], d["hi"], p.alpha_s, p.alpha_c, p.q, p.h)
+        K1, f1 = pt.assemble(d["E"], d["nu"])
+        l0 = R.rpim_kernel_launches()
+        rs += min(timed(lambda: pt.assemble(d["E"], d["nu"], K=K1, f=f1))[0] for _ in range(2))
+        lrs += (R.rpim_kernel_launches() - l0) / 2
+        pt.free()
+        del K1, f1
+    reasm = {"batched_graph_ms": min(rb), "per_instance_ms": rs, "speedup": rs / min(rb),
+             "batched_pts_per_s": npts / (min(rb) / 1e3), "per_instance_pts_per_s": npts / (rs / 1e3),
+             "kernel_launches": {"batched": lrb, "per_instance": lrs},
+             "kernel_ms": {k: round(v[1] / v[0], 3) for k, v in sorted(kprof.items(), key=lambda kv: -kv[1][1])},
+             "algorithmic_flops": {"shape": fl_shape, "pair": fl_pair},
+             "assembly_tflops": (fl_shape + fl_pair) / (min(rb) / 1e3) / 1e12,
+             "shape_tflops": fl_shape / (kprof["shape"][1] / 1e3) / 1e12 if "shape" in kprof else None,
+             "support_sizes": {"min": int(nsup.min()), "max": int(nsup.max()), "mean": float(nsup.mean())},
+             "step": "rpim_assemble_graphed on the batched pattern vs rpim_assemble per instance "
+                     "(patterns built beforehand, not timed)"}
     return {"instances": len(sel), "of": len(allp), "selection": "every %d-th block of the 512-block workload"
             % max(1, len(allp) // n_sel), "n_nodes": int(offs[-1]), "n_points": npts,
             "node_range": [int(min(p.n_nodes for p in sel)), int(max(p.n_nodes for p in sel))],
@@ -435,6 +523,7 @@ def _batched(n_sel, dev, stream, reps=1, warm=1):
                       "iterations_max": int(max(itb)), "iterations_sum_per_instance": int(sum(its))},
             "end_to_end": {"batched_ms": ba + bs, "per_instance_ms": sa + ss, "speedup": (sa + ss) / (ba + bs)},
             "kernel_launches": {"batched": lb, "per_instance": ls},
+            "reassembly": reasm, "bucket_bounds": bounds,
             "u_max_rel_diff_batched_vs_per_instance": du,
             "step": "build pattern + assemble + surface loads (assembly); penalty + Jacobi-PCG to 1e-10 (solve)"}
 
@@ -470,9 +559,10 @@ def run_ours(args, rank, world, local_rank):
     # setup, untimed: launch shapes of the shape kernel picked by the
     # autotuner on this workload's support-size buckets (results are bitwise
     # independent of the launch shape)
-    tuned = None
+    tuned = bounds = None
     if not args.no_autotune:
         tp = R.Pattern(xyz, lo, hi, p.alpha_s, p.alpha_c, p.q, p.h)
+        bounds = tp.autotune_buckets(max_points=100000)
         tuned = tp.autotune(max_points=20000)
         tp.free()
     for _ in range(args.warmup):
@@ -574,6 +664,10 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": whole_job_rate(p.n_points, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
+    mls = None
+    if not args.no_mls:
+        mls = _mls(p, xyz, lo, hi, E, nu, lxyz, lf, stream, peak_gflops)
+
     batched = None
     if args.batched_instances > 0:
         batched = _batched(args.batched_instances, dev, stream, warm=args.batched_warmup)
@@ -596,9 +690,9 @@ def run_ours(args, rank, world, local_rank):
                           "parallelism": "replicas" if world > 1 else "single GPU"},
                "roofline": roof, "kernel_ms_per_step": kernel_ms, "kernel_time_share": kernel_share,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-               "solve": solve, "batched": batched, "backanalysis": grad,
+               "solve": solve, "batched": batched, "backanalysis": grad, "mls": mls,
                "autotune": [{"max_support": a, "warps_per_point": g, "points_per_block": c} for a, g, c in tuned]
-               if tuned else None,
+               if tuned else None, "bucket_bounds": bounds,
                "fp64_peak_gflops_measured": peak_gflops}
         print(json.dumps(out))
 
@@ -613,6 +707,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the penalty + PCG measurement")
     ap.add_argument("--no-grad", action="store_true", help="skip the back-analysis gradient measurement")
+    ap.add_argument("--no-mls", action="store_true", help="skip the MLS-variant assembly measurement")
     ap.add_argument("--batched-warmup", type=int, default=1,
                     help="untimed runs of each arm of the batched comparison before the timed one")
     ap.add_argument("--no-autotune", action="store_true", help="use the built-in launch shapes of the shape kernel")

@@ -127,6 +127,30 @@ rpim_status rpim_build_pattern_batched(int32_t n_inst, const rpim_instance *inst
                                        double q, int32_t gauss_order, rpim_stream_t stream,
                                        rpim_pattern **out, int64_t *nnz_blocks);
 
+/*
+ * Shape functions used by every later stage of a pattern (assembly, point
+ * loads, stresses, gradients). RPIM_SHAPE_RPIM (the default) is the radial
+ * point interpolation of Sec. 1. RPIM_SHAPE_MLS is moving least squares, one
+ * of the alternatives the paper plans (Sec. 4): linear basis [1, (y - x)/h],
+ * cubic-spline weight w(|x_i - x| / r_s) on the same support radius,
+ *   phi_i(x) = w_i p_i^T A(x)^-1 p(x),  A(x) = sum_i w_i p_i p_i^T,
+ * and its exact x-derivatives. RPIM_SHAPE_SHEPARD is the constant-basis
+ * member of the same family (also named in Sec. 4): phi_i = w_i / sum_j w_j
+ * with the same weights; it reproduces constants but not linear fields.
+ * MLS and Shepard shape functions do not interpolate (phi_i(x_j) !=
+ * delta_ij), so penalty values act on nodal parameters.
+ * The kind is stored in the pattern; set it before the stage that should use
+ * it. rpim_autotune_shape tunes the RPIM kernel only (MLS has no launch
+ * shape to tune) and leaves an MLS pattern untouched.
+ * Errors: RPIM_E_ARG (null pattern, unknown kind). MLS assembly reports
+ * RPIM_E_SINGULAR when the 4x4 moment matrix has a pivot below
+ * 1e-13 max|A| (fewer than four non-coplanar weighted nodes); Shepard when
+ * no support node lies strictly inside the radius.
+ */
+typedef enum { RPIM_SHAPE_RPIM = 0, RPIM_SHAPE_MLS = 1, RPIM_SHAPE_SHEPARD = 2 } rpim_shape_kind;
+rpim_status rpim_pattern_set_shape(rpim_pattern *pattern, int32_t kind);
+rpim_status rpim_pattern_get_shape(const rpim_pattern *pattern, int32_t *kind);
+
 /* Releases the pattern and all device memory it owns (stream-ordered on the
  * stream of the last call that used it). NULL is accepted. */
 rpim_status rpim_pattern_free(rpim_pattern *pattern);
@@ -178,6 +202,20 @@ rpim_status rpim_assemble(rpim_pattern *pattern, const double *E, const double *
                           const double *body, double *K_vals, double *f, rpim_stream_t stream);
 
 /*
+ * rpim_assemble replayed from a CUDA graph (same arguments, same results,
+ * bit for bit). The first call captures the assembly's launches (Lame
+ * factors, the shape kernel, the row kernel, the mirror copy) on a stream
+ * the pattern owns; capturing runs nothing. Later calls with the same
+ * argument pointers, shape kind and launch plan (buckets, tuned shapes,
+ * schedule) replay the graph with one launch; any change recaptures. The
+ * caller may change the contents of E, nu and body between calls. With
+ * per-kernel timing on (rpim_profile_enable) the launches are issued
+ * directly. Synchronises `stream`. Errors as rpim_assemble.
+ */
+rpim_status rpim_assemble_graphed(rpim_pattern *pattern, const double *E, const double *nu,
+                                  const double *body, double *K_vals, double *f, rpim_stream_t stream);
+
+/*
  * Autotuner of the shape-function kernel's launch shape (points per block,
  * warps per point) for every support-size bucket of a pattern (the batched
  * workloads' tile and bucket choice): each admissible shape is timed on up
@@ -193,13 +231,55 @@ rpim_status rpim_assemble(rpim_pattern *pattern, const double *E, const double *
 rpim_status rpim_autotune_shape(rpim_pattern *pattern, int64_t max_points, int32_t *table,
                                 int32_t *n_table, rpim_stream_t stream);
 
+/*
+ * Support-size buckets of a pattern's integration points. The RPIM shape
+ * kernel sizes each point's shared-memory buffers to the largest support of
+ * its bucket, so the bounds trade buffer waste against the number of
+ * distinct layouts. Bucket b holds the points with
+ * bounds[b-1] < n <= bounds[b]; a final open-ended bucket is added.
+ *   n_bounds 1..31, bounds host int32 [n_bounds], strictly increasing.
+ * Re-groups on the device; synchronises. Results do not depend on the
+ * bounds (every point's shape functions come from one group with a fixed
+ * formula). Errors: RPIM_E_ARG.
+ */
+rpim_status rpim_pattern_set_buckets(rpim_pattern *pattern, int32_t n_bounds, const int32_t *bounds,
+                                     rpim_stream_t stream);
+
+/* Current buckets (host outputs, each optional, up to `capacity` entries):
+ * upper bound, largest support and point count of every bucket. */
+rpim_status rpim_pattern_get_buckets(const rpim_pattern *pattern, int32_t *n_buckets, int32_t *bounds,
+                                     int32_t *max_support, int64_t *counts, int32_t capacity);
+
+/*
+ * Autotuner of the bucket bounds: applies each candidate set (the built-in
+ * bounds 40/56/72/96/128/160 and uniform widths of 4, 8, 12, 16, 24 and 32
+ * support sizes from the pattern's smallest to its largest support), times
+ * the persistent shape pass on a sample of about max_points points spread
+ * over the buckets (CUDA events on `stream`) and keeps the fastest set, for
+ * this pattern and as the bounds every pattern built later in the process
+ * starts with (like the launch shapes of rpim_autotune_shape).
+ *   bounds host int32 [31], optional; n_bounds host, optional.
+ * Synchronises. An MLS pattern is left as it is (n_bounds = 0).
+ */
+rpim_status rpim_autotune_buckets(rpim_pattern *pattern, int64_t max_points, int32_t *bounds,
+                                  int32_t *n_bounds, rpim_stream_t stream);
+
+/*
+ * Schedule of the RPIM shape kernel over the buckets, process-wide:
+ * 1 (default) one persistent launch in which blocks take tiles of a bucket
+ * (largest supports first) from a device counter; 0 one launch per bucket.
+ * The shape functions are bitwise the same either way. Errors: RPIM_E_ARG.
+ */
+rpim_status rpim_set_shape_schedule(int32_t persistent);
+
 /* Sets the launch shape for buckets whose largest support is max_support
  * (as rpim_autotune_shape would). Errors: RPIM_E_ARG when the shape is not
- * admissible (1-4 warps per point, 1-15 points per block, at most 1024
+ * admissible (1-16 warps per point, 1-15 points per block, at most 1024
  * threads, the points' shared memory within 216 KB). */
 rpim_status rpim_autotune_set(int32_t max_support, int32_t warps_per_point, int32_t points_per_block);
 
-/* Forgets every tuned launch shape (back to the built-in rule). */
+/* Forgets every tuned launch shape and the tuned bucket bounds (back to the
+ * built-in rules for patterns built from now on). */
 rpim_status rpim_autotune_reset(void);
 
 /*

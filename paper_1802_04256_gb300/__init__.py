@@ -33,7 +33,11 @@ EXPORTED = [
     "rpim_solve_pcg_batched", "rpim_autotune_shape", "rpim_autotune_reset",
     "rpim_autotune_set", "rpim_probe_dfma", "rpim_probe_dmma", "rpim_probe_fp64_mixed",
     "rpim_kernel_launches", "rpim_profile_enable", "rpim_profile_read", "rpim_kernel_series_info",
+    "rpim_pattern_set_shape", "rpim_pattern_get_shape", "rpim_assemble_graphed", "rpim_pattern_set_buckets",
+    "rpim_pattern_get_buckets", "rpim_autotune_buckets", "rpim_set_shape_schedule",
 ]
+
+SHAPE_KINDS = {"rpim": 0, "mls": 1, "shepard": 2}
 
 
 class RpimError(RuntimeError):
@@ -108,6 +112,13 @@ def lib():
         "rpim_profile_read": [C.c_char_p, i64, i32],
         "rpim_kernel_series_info": [dbl, dbl, dbl, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                     C.POINTER(dbl)],
+        "rpim_pattern_set_shape": [vp, i32],
+        "rpim_assemble_graphed": [vp, vp, vp, vp, vp, vp, vp],
+        "rpim_pattern_set_buckets": [vp, i32, C.POINTER(i32), vp],
+        "rpim_pattern_get_buckets": [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), i32],
+        "rpim_autotune_buckets": [vp, i64, C.POINTER(i32), C.POINTER(i32), vp],
+        "rpim_set_shape_schedule": [i32],
+        "rpim_pattern_get_shape": [vp, C.POINTER(i32)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -190,6 +201,18 @@ def rpim_stress_batched(handle, u, xyz, inst, E, nu, sigma, stream=None):
                                      _dev(sigma, torch.float64), _stream(stream)), "rpim_stress_batched")
 
 
+def rpim_pattern_set_shape(handle, kind):
+    """kind: "rpim", "mls" or "shepard" (or the integer of rpim_shape_kind)."""
+    k = SHAPE_KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().rpim_pattern_set_shape(handle, k), "rpim_pattern_set_shape")
+
+
+def rpim_pattern_get_shape(handle) -> str:
+    k = C.c_int32(0)
+    _check(lib().rpim_pattern_get_shape(handle, C.byref(k)), "rpim_pattern_get_shape")
+    return {v: n for n, v in SHAPE_KINDS.items()}[k.value]
+
+
 def rpim_pattern_free(handle):
     lib().rpim_pattern_free(handle)
 
@@ -215,6 +238,38 @@ def rpim_assemble(handle, E, nu, body, K_vals, f, stream=None):
                                None if body is None else _dev(body, torch.float64),
                                _dev(K_vals, torch.float64), _dev(f, torch.float64), _stream(stream)),
            "rpim_assemble")
+
+
+def rpim_assemble_graphed(handle, E, nu, body, K_vals, f, stream=None):
+    _check(lib().rpim_assemble_graphed(handle, _dev(E, torch.float64), _dev(nu, torch.float64),
+                                       None if body is None else _dev(body, torch.float64),
+                                       _dev(K_vals, torch.float64), _dev(f, torch.float64), _stream(stream)),
+           "rpim_assemble_graphed")
+
+
+def rpim_pattern_set_buckets(handle, bounds, stream=None):
+    arr = (C.c_int32 * len(bounds))(*[int(b) for b in bounds])
+    _check(lib().rpim_pattern_set_buckets(handle, len(bounds), arr, _stream(stream)), "rpim_pattern_set_buckets")
+
+
+def rpim_pattern_get_buckets(handle):
+    """[(upper bound, largest support, points)] of every bucket."""
+    nb = C.c_int32(0)
+    b, m, c = (C.c_int32 * 64)(), (C.c_int32 * 64)(), (C.c_int64 * 64)()
+    _check(lib().rpim_pattern_get_buckets(handle, C.byref(nb), b, m, c, 64), "rpim_pattern_get_buckets")
+    return [(b[i], m[i], c[i]) for i in range(min(nb.value, 64))]
+
+
+def rpim_autotune_buckets(handle, max_points=200000, stream=None):
+    """Picks the bucket bounds (see include/rpim.h); returns them."""
+    b = (C.c_int32 * 32)()
+    n = C.c_int32(0)
+    _check(lib().rpim_autotune_buckets(handle, max_points, b, C.byref(n), _stream(stream)), "rpim_autotune_buckets")
+    return list(b[:n.value])
+
+
+def rpim_set_shape_schedule(persistent: bool):
+    _check(lib().rpim_set_shape_schedule(1 if persistent else 0), "rpim_set_shape_schedule")
 
 
 def rpim_shape_functions(handle, phi, stream=None):
@@ -357,7 +412,7 @@ class Pattern:
     """Owns an ``rpim_pattern``: integration points, supports and the BSR
     pattern of K for one node cloud."""
 
-    def __init__(self, xyz, cell_lo, cell_hi, alpha_s, alpha_c, q, h, stream=None, instances=None):
+    def __init__(self, xyz, cell_lo, cell_hi, alpha_s, alpha_c, q, h, stream=None, instances=None, shape="rpim"):
         self.device = xyz.device
         if instances is None:
             self.params = Params(alpha_s, alpha_c, q, h, 2)
@@ -369,6 +424,16 @@ class Pattern:
                                                                       stream)
             self.n_inst = len(instances)
         self.info = rpim_pattern_get_info(self.handle)
+        if shape != "rpim":
+            rpim_pattern_set_shape(self.handle, shape)
+
+    def set_shape(self, kind):
+        """Shape functions of the later stages: "rpim", "mls" or "shepard"."""
+        rpim_pattern_set_shape(self.handle, kind)
+
+    @property
+    def shape(self):
+        return rpim_pattern_get_shape(self.handle)
 
     @classmethod
     def batched(cls, problems, device="cuda", stream=None):
@@ -383,9 +448,9 @@ class Pattern:
         return cls(t(xyz), t(lo), t(hi), None, problems[0].alpha_c, problems[0].q, None, stream, inst), offs
 
     @classmethod
-    def from_problem(cls, p, device="cuda", stream=None):
+    def from_problem(cls, p, device="cuda", stream=None, shape="rpim"):
         t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()
-        return cls(t(p.xyz), t(p.cell_lo), t(p.cell_hi), p.alpha_s, p.alpha_c, p.q, p.h, stream)
+        return cls(t(p.xyz), t(p.cell_lo), t(p.cell_hi), p.alpha_s, p.alpha_c, p.q, p.h, stream, shape=shape)
 
     def free(self):
         if self.handle:
@@ -425,6 +490,22 @@ class Pattern:
             f = torch.empty(3 * self.info.n_nodes, dtype=torch.float64, device=self.device)
         rpim_assemble(self.handle, E, nu, body, K, f, stream)
         return K, f
+
+    def assemble_graphed(self, E, nu, body=None, K=None, f=None, stream=None):
+        """assemble() replayed from the pattern's captured CUDA graph (the
+        output buffers must stay the same between calls to reuse it)."""
+        if K is None:
+            K = torch.empty(self.nnz_blocks, 9, dtype=torch.float64, device=self.device)
+        if f is None:
+            f = torch.empty(3 * self.info.n_nodes, dtype=torch.float64, device=self.device)
+        rpim_assemble_graphed(self.handle, E, nu, body, K, f, stream)
+        return K, f
+
+    def autotune_buckets(self, max_points=200000, stream=None):
+        return rpim_autotune_buckets(self.handle, max_points, stream)
+
+    def buckets(self):
+        return rpim_pattern_get_buckets(self.handle)
 
     def add_point_loads(self, xyz, force, f, stream=None, inst=None):
         if inst is None:

@@ -371,6 +371,7 @@ static rpim_status ensure_phi(rpim_pattern *p, cudaStream_t s)
 {
     if (!p->phi) RPIM_CHECK(dalloc(&p->phi, 4 * p->n_entries, s));
     if (!p->lamw) RPIM_CHECK(dalloc(&p->lamw, 2 * p->n_points, s));
+    if (!p->tile_counter) RPIM_CHECK(dalloc(&p->tile_counter, 32, s));   // one work counter per bucket
     return RPIM_OK;
 }
 
@@ -387,13 +388,10 @@ extern "C" rpim_status rpim_shape_functions(rpim_pattern *p, double *phi, rpim_s
     return check_device_error(p, "shape functions");
 }
 
-extern "C" rpim_status rpim_assemble(rpim_pattern *p, const double *E, const double *nu, const double *body,
-                                     double *K, double *f, rpim_stream_t stream)
+// The launches of one assembly (no allocation, no synchronisation).
+static rpim_status assemble_issue(rpim_pattern *p, const double *E, const double *nu, const double *body, double *K,
+                                  double *f, cudaStream_t s)
 {
-    if (!p || !E || !nu || !K || !f) return fail(RPIM_E_ARG, "null argument");
-    cudaStream_t s = (cudaStream_t)stream;
-    p->stream = s;
-    RPIM_CHECK(ensure_phi(p, s));
     launch("lame", lame_kernel, grid_size(p->sm_count, 4, p->n_points, 256), 256, 0, s, p->n_points, E, nu, p->wj, p->lamw, p->err);
     RPIM_CHECK(shape_functions_all(p, p->phi, s));
     // per warp: the slot table (int16 per bitmap position)
@@ -408,7 +406,67 @@ extern "C" rpim_status rpim_assemble(rpim_pattern *p, const double *E, const dou
     RPIM_CUDA(cudaGetLastError());
     launch("mirror", mirror_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, 0, s, p->n_nodes, p->rowptr, p->cols, K);
     RPIM_CUDA(cudaGetLastError());
+    return RPIM_OK;
+}
+
+extern "C" rpim_status rpim_assemble(rpim_pattern *p, const double *E, const double *nu, const double *body,
+                                     double *K, double *f, rpim_stream_t stream)
+{
+    if (!p || !E || !nu || !K || !f) return fail(RPIM_E_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    RPIM_CHECK(ensure_phi(p, s));
+    RPIM_CHECK(assemble_issue(p, E, nu, body, K, f, s));
     return check_device_error(p, "assemble");
+}
+
+// rpim_assemble from a CUDA graph: the launches are captured once on the
+// pattern's capture stream (capturing runs nothing) for a given set of
+// argument pointers and launch plan, then replayed with one graph launch.
+extern "C" rpim_status rpim_assemble_graphed(rpim_pattern *p, const double *E, const double *nu, const double *body,
+                                             double *K, double *f, rpim_stream_t stream)
+{
+    if (!p || !E || !nu || !K || !f) return fail(RPIM_E_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    RPIM_CHECK(ensure_phi(p, s));
+    if (profiling_on()) {   // per-kernel event timing needs plain launches
+        RPIM_CHECK(assemble_issue(p, E, nu, body, K, f, s));
+        return check_device_error(p, "assemble (graphed)");
+    }
+    std::vector<unsigned char> key;
+    RPIM_CHECK(shape_launch_key(p, &key));
+    const void *ptrs[5] = {E, nu, body, K, f};
+    key.insert(key.end(), (const unsigned char *)ptrs, (const unsigned char *)ptrs + sizeof ptrs);
+    if (!p->asm_exec || key != p->asm_key) {
+        if (p->asm_exec) {
+            cudaGraphExecDestroy(p->asm_exec);
+            p->asm_exec = nullptr;
+        }
+        if (!p->cap_stream) RPIM_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+        const int64_t before = launch_count();
+        RPIM_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const rpim_status st = assemble_issue(p, E, nu, body, K, f, p->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+        p->asm_kernels = launch_count() - before;
+        add_launches(-p->asm_kernels);   // counted when the graph runs
+        if (st != RPIM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(RPIM_E_CUDA, std::string("assembly graph capture: ") + cudaGetErrorString(e));
+        const cudaError_t ei = cudaGraphInstantiate(&p->asm_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            p->asm_exec = nullptr;
+            return fail(RPIM_E_CUDA, std::string("assembly graph instantiate: ") + cudaGetErrorString(ei));
+        }
+        p->asm_key = key;
+    }
+    add_launches(p->asm_kernels);
+    RPIM_CUDA(cudaGraphLaunch(p->asm_exec, s));
+    return check_device_error(p, "assemble (graphed)");
 }
 
 extern "C" rpim_status rpim_grad_material(rpim_pattern *p, const double *u, const double *lam, const double *E,

@@ -145,6 +145,7 @@ struct rpim_pattern {
     cudaStream_t stream = nullptr;
     rpim_params prm{};     // alpha_c, q (common); alpha_s, h of the first instance
     int n_inst = 1;
+    int shape_kind = RPIM_SHAPE_RPIM;   // shape functions of every stage (rpim_pattern_set_shape)
     double series_alpha_s = 0.0;    // support radius the kernel series covers
     std::vector<rpim::InstGrid> ig_host;
     rpim::InstGrid *ig = nullptr;   // [n_inst] device copy
@@ -154,6 +155,8 @@ struct rpim_pattern {
     std::vector<int64_t> bucket_count;   // points per bucket
     std::vector<int32_t> bucket_nc;      // largest support in the bucket
     int32_t *bucket_order = nullptr;     // [n_points] point ids grouped by bucket
+    std::vector<int32_t> bucket_bounds;  // upper support size of each bucket (last open-ended)
+    unsigned long long *tile_counter = nullptr;  // [32] per-bucket work counters of the persistent shape kernel
 
     int64_t n_nodes = 0, n_points = 0, n_entries = 0, nnzb = 0;
     int32_t max_support = 0, min_support = 0, max_row = 0;
@@ -195,7 +198,10 @@ struct rpim_pattern {
     // row segments of the batched solver: rows [seg_row[s], seg_row[s+1])
     // belong to instance seg_inst[s]; instance i owns the segments
     // [inst_seg[i], inst_seg[i+1]) (built on the first batched solve)
-    cudaStream_t cap_stream = nullptr;   // capture-only stream of the PCG graphs
+    cudaStream_t cap_stream = nullptr;   // capture-only stream of the PCG and assembly graphs
+    cudaGraphExec_t asm_exec = nullptr;  // captured assembly (rpim_assemble_graphed)
+    std::vector<unsigned char> asm_key;  // what the captured assembly was built for
+    int64_t asm_kernels = 0;             // kernels in the captured assembly
     int64_t n_seg = 0;
     int64_t *seg_row = nullptr;     // [n_seg+1]
     int32_t *seg_inst = nullptr;    // [n_seg]
@@ -259,6 +265,17 @@ rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, c
 // shape functions of all integration points of a pattern, one launch per
 // support-size bucket
 rpim_status shape_functions_all(rpim_pattern *p, double *phi, cudaStream_t s);
+
+// bucket bounds that new patterns start with (empty: the built-in ones)
+void set_default_buckets(const std::vector<int32_t> &bounds);
+
+// key of what shape_functions_all launches for this pattern (see shape.cu)
+rpim_status shape_launch_key(const rpim_pattern *p, std::vector<unsigned char> *key);
+
+// MLS variant of shape_functions (one thread per point, any support size)
+rpim_status mls_shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, const int32_t *inst_of, int shift,
+                                const int32_t *order, const int64_t *soff, const int32_t *sidx, double *phi,
+                                cudaStream_t s, const char *tag);
 
 // node -> entries incidence (stable: ascending entry) of a support list
 rpim_status build_incidence(int64_t n_nodes, int64_t n_entries, const int32_t *sidx,

@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <string>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace rpim {
@@ -543,8 +545,10 @@ static void pattern_release(rpim_pattern *p)
     dfree(p->tent, s); dfree(p->rowptr, s); dfree(p->cols, s); dfree(p->diag, s);
     dfree(p->phi, s); dfree(p->lamw, s); dfree(p->err, s); dfree(p->scal, s); dfree(p->series, s);
     dfree(p->ws.buf, s);
-    dfree(p->ig, s); dfree(p->node_inst, s); dfree(p->bucket_order, s);
+    dfree(p->ig, s); dfree(p->node_inst, s); dfree(p->bucket_order, s); dfree(p->tile_counter, s);
     dfree(p->seg_row, s); dfree(p->seg_inst, s); dfree(p->inst_seg, s);
+    if (p->asm_exec) cudaGraphExecDestroy(p->asm_exec);
+    p->asm_exec = nullptr;
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     p->cap_stream = nullptr;
     p->ws.doubles = 0;
@@ -650,9 +654,84 @@ __global__ void bucket_fill_kernel(int64_t n_pts, const int64_t *soff, const int
     }
 }
 
-// upper support size of each bucket (the last one is open-ended)
+// upper support size of each bucket (the last one is open-ended): the
+// built-in bounds, or the process-wide choice of rpim_autotune_buckets
 static const int32_t kBucketBounds[] = {40, 56, 72, 96, 128, 160, 1 << 30};
 static const int kBuckets = 7;
+static std::mutex g_bounds_mu;
+static std::vector<int32_t> g_bounds(kBucketBounds, kBucketBounds + kBuckets);
+
+namespace rpim {
+void set_default_buckets(const std::vector<int32_t> &b)
+{
+    std::lock_guard<std::mutex> lk(g_bounds_mu);
+    g_bounds = b.empty() ? std::vector<int32_t>(kBucketBounds, kBucketBounds + kBuckets) : b;
+}
+} // namespace rpim
+
+static std::vector<int32_t> default_buckets()
+{
+    std::lock_guard<std::mutex> lk(g_bounds_mu);
+    return g_bounds;
+}
+
+// Groups the integration points by support size: bucket b holds the
+// points with bounds[b-1] < n <= bounds[b] (the last bound is open-ended).
+// Recomputes the point order, counts and largest support of every bucket.
+static rpim_status make_buckets(rpim_pattern *p, const std::vector<int32_t> &bounds_in, cudaStream_t s)
+{
+    std::vector<int32_t> bounds = bounds_in;
+    if (bounds.empty() || bounds.back() < (1 << 30)) bounds.push_back(1 << 30);
+    const int nb = (int)bounds.size();
+    int32_t *dbounds = nullptr;
+    unsigned long long *dcount = nullptr;
+    int64_t *dstart = nullptr;
+    int *dbmax = nullptr;
+    rpim_status st = RPIM_OK;
+    if ((st = dalloc(&dbounds, nb, s)) != RPIM_OK || (st = dalloc(&dcount, 2 * nb, s)) != RPIM_OK ||
+        (st = dalloc(&dstart, nb, s)) != RPIM_OK || (st = dalloc(&dbmax, nb, s)) != RPIM_OK) {
+        dfree(dbounds, s); dfree(dcount, s); dfree(dstart, s); dfree(dbmax, s);
+        return st;
+    }
+    if (!p->bucket_order) RPIM_CHECK(dalloc(&p->bucket_order, p->n_points, s));
+    std::vector<unsigned long long> hc(nb);
+    std::vector<int> hm(nb);
+    std::vector<int64_t> hs(nb);
+    cudaError_t e = cudaMemcpyAsync(dbounds, bounds.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dcount, 0, 2 * nb * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dbmax, 0, nb * sizeof(int), s);
+    const int gsz = grid_size(p->sm_count, 4, p->n_points, 256);
+    if (e == cudaSuccess) {
+        launch("bucket_count", bucket_count_kernel, gsz, 256, 0, s, p->n_points, (const int64_t *)p->soff,
+               (const int32_t *)dbounds, nb, dcount, dbmax);
+        e = cudaMemcpyAsync(hc.data(), dcount, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), dbmax, nb * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        int64_t acc = 0;
+        p->bucket_count.assign(nb, 0);
+        p->bucket_nc.assign(nb, 0);
+        for (int b = 0; b < nb; b++) {
+            hs[b] = acc;
+            acc += (int64_t)hc[b];
+            p->bucket_count[b] = (int64_t)hc[b];
+            p->bucket_nc[b] = hm[b];
+        }
+        p->bucket_bounds = bounds;
+        e = cudaMemcpyAsync(dstart, hs.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) {
+        launch("bucket_fill", bucket_fill_kernel, gsz, 256, 0, s, p->n_points, (const int64_t *)p->soff,
+               (const int32_t *)dbounds, nb, (const int64_t *)dstart, dcount + nb, p->bucket_order);
+        e = cudaGetLastError();
+    }
+    // the host arrays above must outlive the copies that read them
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(dbounds, s); dfree(dcount, s); dfree(dstart, s); dfree(dbmax, s);
+    if (e != cudaSuccess) return cuda_fail(e, "support-size buckets");
+    return RPIM_OK;
+}
 
 static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, const double *hi)
 {
@@ -769,45 +848,7 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     RPIM_CHECK(build_incidence(n, p->n_entries, p->sidx, &p->toff, &p->tent, &p->max_incident, s, p->sm_count));
 
     // support-size buckets
-    {
-        int32_t *dbounds = nullptr;
-        unsigned long long *dcount = nullptr;
-        int64_t *dstart = nullptr;
-        int *dbmax = nullptr;
-        RPIM_CHECK(dalloc(&dbounds, kBuckets, s));
-        RPIM_CHECK(dalloc(&dcount, 2 * kBuckets, s));
-        RPIM_CHECK(dalloc(&dstart, kBuckets, s));
-        RPIM_CHECK(dalloc(&dbmax, kBuckets, s));
-        RPIM_CHECK(dalloc(&p->bucket_order, p->n_points, s));
-        RPIM_CUDA(cudaMemcpyAsync(dbounds, kBucketBounds, sizeof kBucketBounds, cudaMemcpyHostToDevice, s));
-        RPIM_CUDA(cudaMemsetAsync(dcount, 0, 2 * kBuckets * sizeof(unsigned long long), s));
-        RPIM_CUDA(cudaMemsetAsync(dbmax, 0, kBuckets * sizeof(int), s));
-        const int gsz = grid_size(p->sm_count, 4, p->n_points, 256);
-        launch("bucket_count", bucket_count_kernel, gsz, 256, 0, s, p->n_points, (const int64_t *)p->soff,
-               (const int32_t *)dbounds, kBuckets, dcount, dbmax);
-        unsigned long long hc[kBuckets];
-        int hm[kBuckets];
-        RPIM_CUDA(cudaMemcpyAsync(hc, dcount, sizeof hc, cudaMemcpyDeviceToHost, s));
-        RPIM_CUDA(cudaMemcpyAsync(hm, dbmax, sizeof hm, cudaMemcpyDeviceToHost, s));
-        RPIM_CUDA(cudaStreamSynchronize(s));
-        int64_t hs[kBuckets], acc = 0;
-        p->bucket_count.assign(kBuckets, 0);
-        p->bucket_nc.assign(kBuckets, 0);
-        for (int b = 0; b < kBuckets; b++) {
-            hs[b] = acc;
-            acc += (int64_t)hc[b];
-            p->bucket_count[b] = (int64_t)hc[b];
-            p->bucket_nc[b] = hm[b];
-        }
-        RPIM_CUDA(cudaMemcpyAsync(dstart, hs, sizeof hs, cudaMemcpyHostToDevice, s));
-        launch("bucket_fill", bucket_fill_kernel, gsz, 256, 0, s, p->n_points, (const int64_t *)p->soff,
-               (const int32_t *)dbounds, kBuckets, (const int64_t *)dstart, dcount + kBuckets, p->bucket_order);
-        RPIM_CUDA(cudaGetLastError());
-        dfree(dbounds, s);
-        dfree(dcount, s);
-        dfree(dstart, s);
-        dfree(dbmax, s);
-    }
+    RPIM_CHECK(make_buckets(p, default_buckets(), s));
 
     // BSR pattern
     const int words = (125 * p->max_cell + 31) / 32 + 1;
@@ -957,4 +998,29 @@ extern "C" rpim_status rpim_build_pattern_batched(int32_t n_inst, const rpim_ins
                                                   rpim_pattern **out, int64_t *nnz_blocks)
 {
     return create(n_inst, inst, xyz, cell_lo, cell_hi, alpha_c, q, gauss_order, stream, out, nnz_blocks);
+}
+
+extern "C" rpim_status rpim_pattern_set_buckets(rpim_pattern *p, int32_t n_bounds, const int32_t *bounds,
+                                                rpim_stream_t stream)
+{
+    if (!p || n_bounds < 1 || n_bounds > 31 || !bounds) return fail(RPIM_E_ARG, "bad bucket bounds");
+    for (int i = 0; i < n_bounds; i++)
+        if (bounds[i] < 1 || (i > 0 && bounds[i] <= bounds[i - 1])) return fail(RPIM_E_ARG, "bucket bounds must increase");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    return make_buckets(p, std::vector<int32_t>(bounds, bounds + n_bounds), s);
+}
+
+extern "C" rpim_status rpim_pattern_get_buckets(const rpim_pattern *p, int32_t *n_buckets, int32_t *bounds,
+                                                int32_t *max_support, int64_t *counts, int32_t capacity)
+{
+    if (!p || !n_buckets) return fail(RPIM_E_ARG, "null argument");
+    const int nb = (int)p->bucket_count.size();
+    *n_buckets = nb;
+    for (int b = 0; b < nb && b < capacity; b++) {
+        if (bounds) bounds[b] = p->bucket_bounds.empty() ? 0 : p->bucket_bounds[b];
+        if (max_support) max_support[b] = p->bucket_nc[b];
+        if (counts) counts[b] = p->bucket_count[b];
+    }
+    return RPIM_OK;
 }

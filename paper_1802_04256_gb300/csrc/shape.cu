@@ -32,7 +32,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -124,15 +126,15 @@ struct PointSmem {
     double *M;      // [16] P_p^{-T}, row-major
     double *App;    // [16]
     double *red;    // [4 * 16] per-warp partial sums of the pivot values
-    float *redv;    // [4 passes][4 warps] argmax values
-    int *redj;      // [4 passes][4 warps] argmax indices
+    float *redv;    // [4 passes][16 warps] argmax values
+    int *redj;      // [4 passes][16 warps] argmax indices
     int *r2o;       // [NC] rest index -> original index
     double *piv;    // [2] reciprocal of the next LDL' pivot (0 when not positive)
 };
 
 __host__ __device__ inline int64_t point_smem_doubles(int NC)
 {
-    return 3 * NC + (3 * NC + 1) / 2 + 4 * NC + 4 * NC + 4 * NC + (int64_t)NC * (NC + 1) / 2 + 32 + 64 + 8 + 8 +
+    return 3 * NC + (3 * NC + 1) / 2 + 4 * NC + 4 * NC + 4 * NC + (int64_t)NC * (NC + 1) / 2 + 32 + 64 + 32 + 32 +
            (NC + 1) / 2 + 2 + 2;
 }
 
@@ -149,8 +151,8 @@ __device__ __forceinline__ PointSmem carve(double *base, int NC)
     w.M = p; p += 16;
     w.App = p; p += 16;
     w.red = p; p += 64;
-    w.redv = (float *)p; p += 8;
-    w.redj = (int *)p; p += 8;
+    w.redv = (float *)p; p += 32;
+    w.redj = (int *)p; p += 32;
     w.r2o = (int *)p; p += (NC + 1) / 2;
     w.piv = p;
     return w;
@@ -194,6 +196,357 @@ __device__ __forceinline__ void tri_decode(int u, int &i, int &j)
     j = u - r * (r + 1) / 2;
 }
 
+// Thread roles inside one point group of G warps.
+struct Group {
+    int GT, gt, lane, wig, G, bar;
+};
+
+// Shape functions of point p by one group (all G*32 threads of the group
+// call it; the phases are separated by the group's named barrier).
+__device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries &ks, const PointSmem &W, const int NC,
+                                            const Group &gr, const double *__restrict__ pts,
+                                            const int32_t *__restrict__ inst_of, int shift,
+                                            const InstGrid *__restrict__ ig, const int64_t *__restrict__ soff,
+                                            const int32_t *__restrict__ sidx, const double *__restrict__ xyz,
+                                            double *__restrict__ phi, DevError *err)
+{
+    const int GT = gr.GT, gt = gr.gt, lane = gr.lane, wig = gr.wig, G = gr.G, bar = gr.bar;
+    const double c2 = ks.c2;
+    const double inv_h = ig[instance_of(inst_of, shift, p)].inv_h;
+    const int64_t base = soff[p];
+    const int n = (int)(soff[p + 1] - base);
+    if (n < 4 || n > NC) {
+        if (gt == 0) dev_fail(err, RPIM_E_SUPPORT, p);
+        return;
+    }
+    const int m = n - 4;
+    const double gx = pts[3 * p], gy = pts[3 * p + 1], gz = pts[3 * p + 2];
+
+    // 1. local coordinates (FP64) and a single-precision copy
+    for (int j = gt; j < n; j += GT) {
+        const int64_t J = sidx[base + j];
+        const double a = (xyz[3 * J] - gx) * inv_h, b = (xyz[3 * J + 1] - gy) * inv_h,
+                     c = (xyz[3 * J + 2] - gz) * inv_h;
+        W.xi[j] = a;
+        W.xi[NC + j] = b;
+        W.xi[2 * NC + j] = c;
+        W.xf[j] = f32_from_f64(a);
+        W.xf[NC + j] = f32_from_f64(b);
+        W.xf[2 * NC + j] = f32_from_f64(c);
+    }
+    group_sync(bar, GT);
+
+    // 2. greedy pivot tetrahedron (single precision is enough to choose);
+    //    each pass: warp argmax, then the group combines the G warps in
+    //    order
+    const float *X = W.xf, *Yc = W.xf + NC, *Z = W.xf + 2 * NC;
+    auto group_argmax = [&](float bv, int bj, int pass) {
+        warp_argmax(bv, bj);
+        if (lane == 0) {
+            W.redv[16 * pass + wig] = bv;
+            W.redj[16 * pass + wig] = bj;
+        }
+        group_sync(bar, GT);
+        float v = W.redv[16 * pass];
+        int j = W.redj[16 * pass];
+        for (int w = 1; w < G; w++) {
+            const float ov = W.redv[16 * pass + w];
+            const int oj = W.redj[16 * pass + w];
+            if (ov > v || (ov == v && oj < j)) { v = ov; j = oj; }
+        }
+        return ArgMax{v, j};
+    };
+    int p0, p1, p2, p3;
+    {
+        float bv = -INFINITY;
+        int bj = 0x7fffffff;
+        for (int j = gt; j < n; j += GT)
+            if (-X[j] > bv) { bv = -X[j]; bj = j; }
+        p0 = group_argmax(bv, bj, 0).j;
+    }
+    const float ax = X[p0], ay = Yc[p0], az = Z[p0];
+    {
+        float bv = -1.0f;
+        int bj = 0x7fffffff;
+        for (int j = gt; j < n; j += GT) {
+            float dx = X[j] - ax, dy = Yc[j] - ay, dz = Z[j] - az;
+            float d = dx * dx + dy * dy + dz * dz;
+            if (d > bv) { bv = d; bj = j; }
+        }
+        p1 = group_argmax(bv, bj, 1).j;
+    }
+    const float ux = X[p1] - ax, uy = Yc[p1] - ay, uz = Z[p1] - az;
+    {
+        float bv = -1.0f;
+        int bj = 0x7fffffff;
+        for (int j = gt; j < n; j += GT) {
+            float dx = X[j] - ax, dy = Yc[j] - ay, dz = Z[j] - az;
+            float cx = dy * uz - dz * uy, cy = dz * ux - dx * uz, cz = dx * uy - dy * ux;
+            float d = cx * cx + cy * cy + cz * cz;
+            if (d > bv) { bv = d; bj = j; }
+        }
+        p2 = group_argmax(bv, bj, 2).j;
+    }
+    {
+        const float vx = X[p2] - ax, vy = Yc[p2] - ay, vz = Z[p2] - az;
+        const float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+        float bv = -1.0f;
+        int bj = 0x7fffffff;
+        for (int j = gt; j < n; j += GT) {
+            float d = fabsf((X[j] - ax) * nx + (Yc[j] - ay) * ny + (Z[j] - az) * nz);
+            if (d > bv) { bv = d; bj = j; }
+        }
+        auto r = group_argmax(bv, bj, 3);
+        p3 = r.j;
+        const float ulen2 = ux * ux + uy * uy + uz * uz;
+        if (!(r.v > 1e-5f * ulen2 * sqrtf(ulen2))) {
+            if (gt == 0) dev_fail(err, RPIM_E_SINGULAR, p);
+            group_sync(bar, GT);
+            return;
+        }
+    }
+    // rest ordering: original order without the pivots
+    for (int j = gt; j < n; j += GT) {
+        int less = (p0 < j) + (p1 < j) + (p2 < j) + (p3 < j);
+        bool isp = j == p0 || j == p1 || j == p2 || j == p3;
+        if (!isp) W.r2o[j - less] = j;
+    }
+    auto pivot = [&](int k) { return k == 0 ? p0 : k == 1 ? p1 : k == 2 ? p2 : p3; };
+
+    // 3. M = P_p^{-T} = cofactor matrix / det, one cofactor per lane 0..15
+    //    of the group's first warp
+    if (wig == 0) {
+        const int ri = (lane >> 2) & 3, cj = lane & 3;
+        double e[3][3];
+        int rr = 0;
+        for (int r = 0; r < 4; r++) {
+            if (r == ri) continue;
+            const int pr = pivot(r);
+            const double row[4] = {1.0, W.xi[pr], W.xi[NC + pr], W.xi[2 * NC + pr]};
+            int cc = 0;
+            for (int c = 0; c < 4; c++)
+                if (c != cj) e[rr][cc++] = row[c];
+            rr++;
+        }
+        double cof = det3(e[0][0], e[0][1], e[0][2], e[1][0], e[1][1], e[1][2], e[2][0], e[2][1], e[2][2]);
+        if ((ri + cj) & 1) cof = -cof;
+        const double prow = cj == 0 ? 1.0 : W.xi[(cj - 1) * NC + p0];
+        double part = lane < 4 ? prow * cof : 0.0;
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        const double det = __shfl_sync(0xffffffffu, part, 0);
+        const double idet = recip_nr(det);
+        if (lane < 16) W.M[lane] = cof * idet;
+    }
+    group_sync(bar, GT);
+
+    // 4. A_pp, C and A_rp
+    if (gt < 16) {
+        const int a = gt >> 2, b = gt & 3;
+        const int ia = pivot(a), ib = pivot(b);
+        double val = ks.diag;
+        if (a != b) {
+            double dx = W.xi[ia] - W.xi[ib], dy = W.xi[NC + ia] - W.xi[NC + ib], dz = W.xi[2 * NC + ia] - W.xi[2 * NC + ib];
+            val = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
+        }
+        W.App[gt] = val;
+    }
+    for (int t = gt; t < 4 * m; t += GT) {
+        const int r = t >> 2, k = t & 3;
+        const int j = W.r2o[r];
+        const double x0 = W.xi[j], x1 = W.xi[NC + j], x2 = W.xi[2 * NC + j];
+        W.C[k * NC + r] = fma(W.M[4 * k + 3], x2, fma(W.M[4 * k + 2], x1, fma(W.M[4 * k + 1], x0, W.M[4 * k])));
+        const int ik = pivot(k);
+        double dx = x0 - W.xi[ik], dy = x1 - W.xi[NC + ik], dz = x2 - W.xi[2 * NC + ik];
+        W.Y[k * NC + r] = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
+    }
+    group_sync(bar, GT);
+
+    // 5. right-hand sides v = r - A_:p d  (d = columns of M), all nodes
+    for (int j = gt; j < n; j += GT) {
+        const double x0 = W.xi[j], x1 = W.xi[NC + j], x2 = W.xi[2 * NC + j];
+        double Aj, dAj;
+        series_A_dA(ks, fma(x2, x2, fma(x1, x1, fma(x0, x0, c2))), Aj, dAj);
+        const double m2 = -2.0 * dAj;
+        const double rr[4] = {Aj, m2 * x0, m2 * x1, m2 * x2};
+        double Ajp[4];
+        int kp = -1;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (pivot(k) == j) kp = k;
+        if (kp >= 0) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) Ajp[k] = W.App[4 * kp + k];
+        } else {
+            const int r = j - (p0 < j) - (p1 < j) - (p2 < j) - (p3 < j);
+#pragma unroll
+            for (int k = 0; k < 4; k++) Ajp[k] = W.Y[k * NC + r];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            double acc = rr[q];
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc = fma(-Ajp[k], W.M[4 * k + q], acc);
+            W.v[q * NC + j] = acc;
+        }
+    }
+    group_sync(bar, GT);
+    // Y = A_rp - C' A_pp / 2
+    for (int t = gt; t < 4 * m; t += GT) {
+        const int r = t >> 2, k = t & 3;
+        double acc = 0.0;
+#pragma unroll
+        for (int s2 = 0; s2 < 4; s2++) acc = fma(W.C[s2 * NC + r], W.App[4 * s2 + k], acc);
+        W.Y[k * NC + r] = fma(-0.5, acc, W.Y[k * NC + r]);  // each thread owns its element
+    }
+    group_sync(bar, GT);
+
+    // 6. S = A_rr - Y C - C' Y' (packed lower triangle, rows 0..m-1),
+    //    then the reduced right-hand sides as rows m..m+3 (entries
+    //    j < m), so that the elimination below also performs the
+    //    forward substitution
+    {
+        const int T = m * (m + 1) / 2;
+        for (int u = gt; u < T; u += GT) {
+            int i, j;
+            tri_decode(u, i, j);
+            const int oi = W.r2o[i], oj = W.r2o[j];
+            double a;
+            if (i == j) {
+                a = ks.diag;
+            } else {
+                double dx = W.xi[oi] - W.xi[oj], dy = W.xi[NC + oi] - W.xi[NC + oj], dz = W.xi[2 * NC + oi] - W.xi[2 * NC + oj];
+                a = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                a = fma(-W.Y[k * NC + i], W.C[k * NC + j], a);
+                a = fma(-W.C[k * NC + i], W.Y[k * NC + j], a);
+            }
+            W.S[u] = a;
+            if (u == 0) W.piv[0] = positive_normal(a) ? recip_nr(a) : 0.0;  // first pivot
+        }
+    }
+    for (int t = gt; t < 4 * (m + 4); t += GT) {
+        const int q = t / (m + 4), r = t - q * (m + 4);
+        double acc = 0.0;
+        if (r < m) {
+            const int j = W.r2o[r];
+            acc = W.v[q * NC + j];
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc = fma(-W.C[k * NC + r], W.v[q * NC + pivot(k)], acc);
+        }
+        if (r <= m + q) W.S[(m + q) * (m + q + 1) / 2 + r] = acc;
+    }
+    group_sync(bar, GT);
+
+    // 7. S = L D L' (right-looking, packed, in place) on the order-(m+4)
+    //    triangle; W.v holds the unscaled column of the current step.
+    //    After step m-1 the rhs rows hold z = D^-1 L^-1 rhs.
+    const int M2 = m + 4;
+    double *col = W.v;
+    bool ok = true;
+    //    The reciprocal of each pivot is computed once, by the thread
+    //    that finishes the pivot (u == 0 of the previous update), and read
+    //    from shared memory by the group: replicated in every warp it
+    //    would cost each warp a full FP64 issue slot per instruction.
+    for (int k = 0; k < m; k++) {
+        const double iv = W.piv[0];
+        if (!(iv > 0.0)) { ok = false; break; }
+        for (int i = k + 1 + gt; i < M2; i += GT) {
+            const int ik = i * (i + 1) / 2 + k;
+            const double a = W.S[ik];
+            col[i] = a;
+            W.S[ik] = a * iv;
+        }
+        group_sync(bar, GT);
+        const int tk = M2 - k - 1;
+        const int T = tk * (tk + 1) / 2;
+        for (int u = gt; u < T; u += GT) {
+            int ri, rj;
+            tri_decode(u, ri, rj);
+            const int i = k + 1 + ri, j = k + 1 + rj;
+            const int ib = i * (i + 1) / 2;
+            const double nv = fma(-W.S[ib + k], col[j], W.S[ib + j]);
+            W.S[ib + j] = nv;
+            if (u == 0 && k + 1 < m) W.piv[0] = positive_normal(nv) ? recip_nr(nv) : 0.0;
+        }
+        group_sync(bar, GT);
+    }
+    if (!ok) {
+        if (gt == 0) dev_fail(err, RPIM_E_SINGULAR, p);
+        group_sync(bar, GT);
+        return;
+    }
+
+    // 8. L' a = z, column by column; threads over (row, rhs) pairs
+    double *Z0 = W.S + (size_t)m * (m + 1) / 2;  // rhs row q starts at Z0 + q*m + q*(q+1)/2
+    for (int k = m - 1; k > 0; k--) {
+        const int kb = k * (k + 1) / 2;
+        for (int t = gt; t < 4 * k; t += GT) {
+            const int q = t & 3, i = t >> 2;
+            double *zq = Z0 + q * m + q * (q + 1) / 2;
+            zq[i] = fma(-W.S[kb + i], zq[k], zq[i]);
+        }
+        group_sync(bar, GT);
+    }
+
+    // 9. pivot values a_p = d - C a_r: 16 sums over the rest rows, by the
+    //    group's first warp alone (lane-strided partial sums, then
+    //    reduce-scattered so that lane l ends with sum l >> 1). The
+    //    summation order is therefore the same for every group width G,
+    //    and the other warps issue no FP64 work here.
+    if (wig == 0) {
+        double v[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) v[k] = 0.0;
+        for (int r = lane; r < m; r += 32) {
+            double ar[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) ar[q] = Z0[q * m + q * (q + 1) / 2 + r];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const double c = W.C[k * NC + r];
+#pragma unroll
+                for (int q = 0; q < 4; q++) v[4 * k + q] = fma(c, ar[q], v[4 * k + q]);
+            }
+        }
+#pragma unroll
+        for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
+            const bool up = (lane & bit) != 0;
+#pragma unroll
+            for (int i = 0; i < half; i++) {
+                const double mine = up ? v[i + half] : v[i];
+                const double theirs = up ? v[i] : v[i + half];
+                v[i] = mine + __shfl_xor_sync(0xffffffffu, theirs, bit);
+            }
+        }
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+        if ((lane & 1) == 0) W.red[lane >> 1] = v[0];
+    }
+
+    double *out = phi + 4 * base;
+    bool finite = true;
+    for (int r = gt; r < m; r += GT) {
+        const int j = W.r2o[r];
+        double2 lo2 = make_double2(Z0[r], Z0[m + 1 + r] * inv_h);
+        double2 hi2 = make_double2(Z0[2 * m + 3 + r] * inv_h, Z0[3 * m + 6 + r] * inv_h);
+        finite &= isfinite(lo2.x) && isfinite(lo2.y) && isfinite(hi2.x) && isfinite(hi2.y);
+        *(double2 *)(out + 4 * j) = lo2;
+        *(double2 *)(out + 4 * j + 2) = hi2;
+    }
+    group_sync(bar, GT);
+    if (gt < 16) {
+        const int k = gt >> 2, q = gt & 3;
+        double val = W.M[4 * k + q] - W.red[gt];
+        if (q) val *= inv_h;
+        finite &= isfinite(val);
+        out[4 * pivot(k) + q] = val;
+    }
+    if (!__all_sync(0xffffffffu, finite) && lane == 0) dev_fail(err, RPIM_E_NONFINITE, p);
+    group_sync(bar, GT);
+}
+
 // One group of G warps per point. Every loop below is a flattened parallel
 // loop over the group's G*32 threads; the phases are separated by a named
 // barrier of the group. Groups of one block are independent.
@@ -222,344 +575,79 @@ __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double
     const int ppb = blockDim.x / GT;
     const int bar = 1 + grp;
     PointSmem W = carve(dsm + (size_t)grp * point_smem_doubles(NC), NC);
-    const double c2 = ks.c2;
     const int64_t stride = (int64_t)gridDim.x * ppb;
 
+    const Group gr{GT, gt, lane, wig, G, bar};
     for (int64_t pk = (int64_t)blockIdx.x * ppb + grp; pk < n_pts; pk += stride) {
         const int64_t p = order ? (int64_t)order[pk] : pk;
-        const double inv_h = ig[instance_of(inst_of, shift, p)].inv_h;
-        const int64_t base = soff[p];
-        const int n = (int)(soff[p + 1] - base);
-        if (n < 4 || n > NC) {
-            if (gt == 0) dev_fail(err, RPIM_E_SUPPORT, p);
-            continue;
-        }
-        const int m = n - 4;
-        const double gx = pts[3 * p], gy = pts[3 * p + 1], gz = pts[3 * p + 2];
+        shape_point(p, ks, W, NC, gr, pts, inst_of, shift, ig, soff, sidx, xyz, phi, err);
+    }
+}
 
-        // 1. local coordinates (FP64) and a single-precision copy
-        for (int j = gt; j < n; j += GT) {
-            const int64_t J = sidx[base + j];
-            const double a = (xyz[3 * J] - gx) * inv_h, b = (xyz[3 * J + 1] - gy) * inv_h,
-                         c = (xyz[3 * J + 2] - gz) * inv_h;
-            W.xi[j] = a;
-            W.xi[NC + j] = b;
-            W.xi[2 * NC + j] = c;
-            W.xf[j] = f32_from_f64(a);
-            W.xf[NC + j] = f32_from_f64(b);
-            W.xf[2 * NC + j] = f32_from_f64(c);
-        }
-        group_sync(bar, GT);
+// Work plan of the persistent shape kernel: the support-size buckets, largest
+// supports first, each with its launch shape (ppb groups of G warps per block,
+// NC-sized point buffers) and its slice [start, start + count) of the point
+// order.
+constexpr int kMaxTileBuckets = 32;
+struct BucketPlan {
+    int nb;
+    int pad;
+    long long total;                       // points of all buckets
+    int NC[kMaxTileBuckets], G[kMaxTileBuckets], ppb[kMaxTileBuckets];
+    long long start[kMaxTileBuckets];      // first position of the bucket in the order list
+    long long count[kMaxTileBuckets];      // points of the bucket
+};
 
-        // 2. greedy pivot tetrahedron (single precision is enough to choose);
-        //    each pass: warp argmax, then the group combines the G warps in
-        //    order
-        const float *X = W.xf, *Yc = W.xf + NC, *Z = W.xf + 2 * NC;
-        auto group_argmax = [&](float bv, int bj, int pass) {
-            warp_argmax(bv, bj);
-            if (lane == 0) {
-                W.redv[4 * pass + wig] = bv;
-                W.redj[4 * pass + wig] = bj;
-            }
-            group_sync(bar, GT);
-            float v = W.redv[4 * pass];
-            int j = W.redj[4 * pass];
-            for (int w = 1; w < G; w++) {
-                const float ov = W.redv[4 * pass + w];
-                const int oj = W.redj[4 * pass + w];
-                if (ov > v || (ov == v && oj < j)) { v = ov; j = oj; }
-            }
-            return ArgMax{v, j};
-        };
-        int p0, p1, p2, p3;
-        {
-            float bv = -INFINITY;
-            int bj = 0x7fffffff;
-            for (int j = gt; j < n; j += GT)
-                if (-X[j] > bv) { bv = -X[j]; bj = j; }
-            p0 = group_argmax(bv, bj, 0).j;
-        }
-        const float ax = X[p0], ay = Yc[p0], az = Z[p0];
-        {
-            float bv = -1.0f;
-            int bj = 0x7fffffff;
-            for (int j = gt; j < n; j += GT) {
-                float dx = X[j] - ax, dy = Yc[j] - ay, dz = Z[j] - az;
-                float d = dx * dx + dy * dy + dz * dz;
-                if (d > bv) { bv = d; bj = j; }
-            }
-            p1 = group_argmax(bv, bj, 1).j;
-        }
-        const float ux = X[p1] - ax, uy = Yc[p1] - ay, uz = Z[p1] - az;
-        {
-            float bv = -1.0f;
-            int bj = 0x7fffffff;
-            for (int j = gt; j < n; j += GT) {
-                float dx = X[j] - ax, dy = Yc[j] - ay, dz = Z[j] - az;
-                float cx = dy * uz - dz * uy, cy = dz * ux - dx * uz, cz = dx * uy - dy * ux;
-                float d = cx * cx + cy * cy + cz * cz;
-                if (d > bv) { bv = d; bj = j; }
-            }
-            p2 = group_argmax(bv, bj, 2).j;
-        }
-        {
-            const float vx = X[p2] - ax, vy = Yc[p2] - ay, vz = Z[p2] - az;
-            const float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
-            float bv = -1.0f;
-            int bj = 0x7fffffff;
-            for (int j = gt; j < n; j += GT) {
-                float d = fabsf((X[j] - ax) * nx + (Yc[j] - ay) * ny + (Z[j] - az) * nz);
-                if (d > bv) { bv = d; bj = j; }
-            }
-            auto r = group_argmax(bv, bj, 3);
-            p3 = r.j;
-            const float ulen2 = ux * ux + uy * uy + uz * uz;
-            if (!(r.v > 1e-5f * ulen2 * sqrtf(ulen2))) {
-                if (gt == 0) dev_fail(err, RPIM_E_SINGULAR, p);
-                group_sync(bar, GT);
-                continue;
+// Persistent shape kernel: one launch over a (bucket, point) work list. The
+// blocks walk the buckets in the plan's order; for each bucket a block lays
+// its shared memory out for that bucket's launch shape, and each of its
+// point groups takes the bucket's next point from a device counter until the
+// bucket is exhausted, independently of the other groups (no block-wide
+// wait per point). A block-wide barrier separates buckets, since group roles
+// and buffers change between them. Every value is computed by the same
+// thread-level formula as in shape_kernel, whatever the launch shape, so the
+// results are bitwise those of the per-bucket launches.
+__global__ void __launch_bounds__(1024) shape_tiles_kernel(const BucketPlan plan, unsigned long long *counters,
+                                                           const double *__restrict__ pts,
+                                                           const int32_t *__restrict__ inst_of, int shift,
+                                                           const InstGrid *__restrict__ ig,
+                                                           const int32_t *__restrict__ order,
+                                                           const int64_t *__restrict__ soff,
+                                                           const int32_t *__restrict__ sidx,
+                                                           const double *__restrict__ xyz,
+                                                           const KernelSeries *__restrict__ ks_g,
+                                                           double *__restrict__ phi, DevError *err)
+{
+    extern __shared__ double dsm[];
+    __shared__ KernelSeries ks;
+    __shared__ long long s_next[32];
+    {
+        const int nw = sizeof(KernelSeries) / sizeof(int);
+        const int *src = (const int *)ks_g;
+        int *dst = (int *)&ks;
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int b = 0; b < plan.nb; b++) {
+        const int G = plan.G[b], ppb = plan.ppb[b], NC = plan.NC[b];
+        const int GT = G * 32;
+        const int grp = threadIdx.x / GT;
+        if (grp < ppb) {
+            const int gt = threadIdx.x - grp * GT;
+            const Group gr{GT, gt, lane, gt >> 5, G, 1 + grp};
+            const PointSmem W = carve(dsm + (size_t)grp * point_smem_doubles(NC), NC);
+            for (;;) {
+                if (gt == 0) s_next[grp] = (long long)atomicAdd(&counters[b], 1ull);
+                group_sync(1 + grp, GT);
+                const long long pk = s_next[grp];
+                group_sync(1 + grp, GT);   // every thread holds pk before the next fetch
+                if (pk >= plan.count[b]) break;
+                const int64_t p = (int64_t)order[plan.start[b] + pk];
+                shape_point(p, ks, W, NC, gr, pts, inst_of, shift, ig, soff, sidx, xyz, phi, err);
             }
         }
-        // rest ordering: original order without the pivots
-        for (int j = gt; j < n; j += GT) {
-            int less = (p0 < j) + (p1 < j) + (p2 < j) + (p3 < j);
-            bool isp = j == p0 || j == p1 || j == p2 || j == p3;
-            if (!isp) W.r2o[j - less] = j;
-        }
-        auto pivot = [&](int k) { return k == 0 ? p0 : k == 1 ? p1 : k == 2 ? p2 : p3; };
-
-        // 3. M = P_p^{-T} = cofactor matrix / det, one cofactor per lane 0..15
-        //    of the group's first warp
-        if (wig == 0) {
-            const int ri = (lane >> 2) & 3, cj = lane & 3;
-            double e[3][3];
-            int rr = 0;
-            for (int r = 0; r < 4; r++) {
-                if (r == ri) continue;
-                const int pr = pivot(r);
-                const double row[4] = {1.0, W.xi[pr], W.xi[NC + pr], W.xi[2 * NC + pr]};
-                int cc = 0;
-                for (int c = 0; c < 4; c++)
-                    if (c != cj) e[rr][cc++] = row[c];
-                rr++;
-            }
-            double cof = det3(e[0][0], e[0][1], e[0][2], e[1][0], e[1][1], e[1][2], e[2][0], e[2][1], e[2][2]);
-            if ((ri + cj) & 1) cof = -cof;
-            const double prow = cj == 0 ? 1.0 : W.xi[(cj - 1) * NC + p0];
-            double part = lane < 4 ? prow * cof : 0.0;
-            part += __shfl_xor_sync(0xffffffffu, part, 1);
-            part += __shfl_xor_sync(0xffffffffu, part, 2);
-            const double det = __shfl_sync(0xffffffffu, part, 0);
-            const double idet = recip_nr(det);
-            if (lane < 16) W.M[lane] = cof * idet;
-        }
-        group_sync(bar, GT);
-
-        // 4. A_pp, C and A_rp
-        if (gt < 16) {
-            const int a = gt >> 2, b = gt & 3;
-            const int ia = pivot(a), ib = pivot(b);
-            double val = ks.diag;
-            if (a != b) {
-                double dx = W.xi[ia] - W.xi[ib], dy = W.xi[NC + ia] - W.xi[NC + ib], dz = W.xi[2 * NC + ia] - W.xi[2 * NC + ib];
-                val = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
-            }
-            W.App[gt] = val;
-        }
-        for (int t = gt; t < 4 * m; t += GT) {
-            const int r = t >> 2, k = t & 3;
-            const int j = W.r2o[r];
-            const double x0 = W.xi[j], x1 = W.xi[NC + j], x2 = W.xi[2 * NC + j];
-            W.C[k * NC + r] = fma(W.M[4 * k + 3], x2, fma(W.M[4 * k + 2], x1, fma(W.M[4 * k + 1], x0, W.M[4 * k])));
-            const int ik = pivot(k);
-            double dx = x0 - W.xi[ik], dy = x1 - W.xi[NC + ik], dz = x2 - W.xi[2 * NC + ik];
-            W.Y[k * NC + r] = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
-        }
-        group_sync(bar, GT);
-
-        // 5. right-hand sides v = r - A_:p d  (d = columns of M), all nodes
-        for (int j = gt; j < n; j += GT) {
-            const double x0 = W.xi[j], x1 = W.xi[NC + j], x2 = W.xi[2 * NC + j];
-            double Aj, dAj;
-            series_A_dA(ks, fma(x2, x2, fma(x1, x1, fma(x0, x0, c2))), Aj, dAj);
-            const double m2 = -2.0 * dAj;
-            const double rr[4] = {Aj, m2 * x0, m2 * x1, m2 * x2};
-            double Ajp[4];
-            int kp = -1;
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (pivot(k) == j) kp = k;
-            if (kp >= 0) {
-#pragma unroll
-                for (int k = 0; k < 4; k++) Ajp[k] = W.App[4 * kp + k];
-            } else {
-                const int r = j - (p0 < j) - (p1 < j) - (p2 < j) - (p3 < j);
-#pragma unroll
-                for (int k = 0; k < 4; k++) Ajp[k] = W.Y[k * NC + r];
-            }
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                double acc = rr[q];
-#pragma unroll
-                for (int k = 0; k < 4; k++) acc = fma(-Ajp[k], W.M[4 * k + q], acc);
-                W.v[q * NC + j] = acc;
-            }
-        }
-        group_sync(bar, GT);
-        // Y = A_rp - C' A_pp / 2
-        for (int t = gt; t < 4 * m; t += GT) {
-            const int r = t >> 2, k = t & 3;
-            double acc = 0.0;
-#pragma unroll
-            for (int s2 = 0; s2 < 4; s2++) acc = fma(W.C[s2 * NC + r], W.App[4 * s2 + k], acc);
-            W.Y[k * NC + r] = fma(-0.5, acc, W.Y[k * NC + r]);  // each thread owns its element
-        }
-        group_sync(bar, GT);
-
-        // 6. S = A_rr - Y C - C' Y' (packed lower triangle, rows 0..m-1),
-        //    then the reduced right-hand sides as rows m..m+3 (entries
-        //    j < m), so that the elimination below also performs the
-        //    forward substitution
-        {
-            const int T = m * (m + 1) / 2;
-            for (int u = gt; u < T; u += GT) {
-                int i, j;
-                tri_decode(u, i, j);
-                const int oi = W.r2o[i], oj = W.r2o[j];
-                double a;
-                if (i == j) {
-                    a = ks.diag;
-                } else {
-                    double dx = W.xi[oi] - W.xi[oj], dy = W.xi[NC + oi] - W.xi[NC + oj], dz = W.xi[2 * NC + oi] - W.xi[2 * NC + oj];
-                    a = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
-                }
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    a = fma(-W.Y[k * NC + i], W.C[k * NC + j], a);
-                    a = fma(-W.C[k * NC + i], W.Y[k * NC + j], a);
-                }
-                W.S[u] = a;
-                if (u == 0) W.piv[0] = positive_normal(a) ? recip_nr(a) : 0.0;  // first pivot
-            }
-        }
-        for (int t = gt; t < 4 * (m + 4); t += GT) {
-            const int q = t / (m + 4), r = t - q * (m + 4);
-            double acc = 0.0;
-            if (r < m) {
-                const int j = W.r2o[r];
-                acc = W.v[q * NC + j];
-#pragma unroll
-                for (int k = 0; k < 4; k++) acc = fma(-W.C[k * NC + r], W.v[q * NC + pivot(k)], acc);
-            }
-            if (r <= m + q) W.S[(m + q) * (m + q + 1) / 2 + r] = acc;
-        }
-        group_sync(bar, GT);
-
-        // 7. S = L D L' (right-looking, packed, in place) on the order-(m+4)
-        //    triangle; W.v holds the unscaled column of the current step.
-        //    After step m-1 the rhs rows hold z = D^-1 L^-1 rhs.
-        const int M2 = m + 4;
-        double *col = W.v;
-        bool ok = true;
-        //    The reciprocal of each pivot is computed once, by the thread
-        //    that finishes the pivot (u == 0 of the previous update), and read
-        //    from shared memory by the group: replicated in every warp it
-        //    would cost each warp a full FP64 issue slot per instruction.
-        for (int k = 0; k < m; k++) {
-            const double iv = W.piv[0];
-            if (!(iv > 0.0)) { ok = false; break; }
-            for (int i = k + 1 + gt; i < M2; i += GT) {
-                const int ik = i * (i + 1) / 2 + k;
-                const double a = W.S[ik];
-                col[i] = a;
-                W.S[ik] = a * iv;
-            }
-            group_sync(bar, GT);
-            const int tk = M2 - k - 1;
-            const int T = tk * (tk + 1) / 2;
-            for (int u = gt; u < T; u += GT) {
-                int ri, rj;
-                tri_decode(u, ri, rj);
-                const int i = k + 1 + ri, j = k + 1 + rj;
-                const int ib = i * (i + 1) / 2;
-                const double nv = fma(-W.S[ib + k], col[j], W.S[ib + j]);
-                W.S[ib + j] = nv;
-                if (u == 0 && k + 1 < m) W.piv[0] = positive_normal(nv) ? recip_nr(nv) : 0.0;
-            }
-            group_sync(bar, GT);
-        }
-        if (!ok) {
-            if (gt == 0) dev_fail(err, RPIM_E_SINGULAR, p);
-            group_sync(bar, GT);
-            continue;
-        }
-
-        // 8. L' a = z, column by column; threads over (row, rhs) pairs
-        double *Z0 = W.S + (size_t)m * (m + 1) / 2;  // rhs row q starts at Z0 + q*m + q*(q+1)/2
-        for (int k = m - 1; k > 0; k--) {
-            const int kb = k * (k + 1) / 2;
-            for (int t = gt; t < 4 * k; t += GT) {
-                const int q = t & 3, i = t >> 2;
-                double *zq = Z0 + q * m + q * (q + 1) / 2;
-                zq[i] = fma(-W.S[kb + i], zq[k], zq[i]);
-            }
-            group_sync(bar, GT);
-        }
-
-        // 9. pivot values a_p = d - C a_r: 16 sums over the rest rows, by the
-        //    group's first warp alone (lane-strided partial sums, then
-        //    reduce-scattered so that lane l ends with sum l >> 1). The
-        //    summation order is therefore the same for every group width G,
-        //    and the other warps issue no FP64 work here.
-        if (wig == 0) {
-            double v[16];
-#pragma unroll
-            for (int k = 0; k < 16; k++) v[k] = 0.0;
-            for (int r = lane; r < m; r += 32) {
-                double ar[4];
-#pragma unroll
-                for (int q = 0; q < 4; q++) ar[q] = Z0[q * m + q * (q + 1) / 2 + r];
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const double c = W.C[k * NC + r];
-#pragma unroll
-                    for (int q = 0; q < 4; q++) v[4 * k + q] = fma(c, ar[q], v[4 * k + q]);
-                }
-            }
-#pragma unroll
-            for (int half = 8, bit = 16; half >= 1; half >>= 1, bit >>= 1) {
-                const bool up = (lane & bit) != 0;
-#pragma unroll
-                for (int i = 0; i < half; i++) {
-                    const double mine = up ? v[i + half] : v[i];
-                    const double theirs = up ? v[i] : v[i + half];
-                    v[i] = mine + __shfl_xor_sync(0xffffffffu, theirs, bit);
-                }
-            }
-            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-            if ((lane & 1) == 0) W.red[lane >> 1] = v[0];
-        }
-
-        double *out = phi + 4 * base;
-        bool finite = true;
-        for (int r = gt; r < m; r += GT) {
-            const int j = W.r2o[r];
-            double2 lo2 = make_double2(Z0[r], Z0[m + 1 + r] * inv_h);
-            double2 hi2 = make_double2(Z0[2 * m + 3 + r] * inv_h, Z0[3 * m + 6 + r] * inv_h);
-            finite &= isfinite(lo2.x) && isfinite(lo2.y) && isfinite(hi2.x) && isfinite(hi2.y);
-            *(double2 *)(out + 4 * j) = lo2;
-            *(double2 *)(out + 4 * j + 2) = hi2;
-        }
-        group_sync(bar, GT);
-        if (gt < 16) {
-            const int k = gt >> 2, q = gt & 3;
-            double val = W.M[4 * k + q] - W.red[gt];
-            if (q) val *= inv_h;
-            finite &= isfinite(val);
-            out[4 * pivot(k) + q] = val;
-        }
-        if (!__all_sync(0xffffffffu, finite) && lane == 0) dev_fail(err, RPIM_E_NONFINITE, p);
-        group_sync(bar, GT);
+        __syncthreads();
     }
 }
 
@@ -578,10 +666,11 @@ static ShapeCfg g_tuned[RPIM_MAX_SUPPORT + 1];
 static size_t point_bytes(int NC) { return (size_t)point_smem_doubles(NC) * sizeof(double); }
 
 constexpr size_t kShapeSmemBudget = 216 * 1024;
+constexpr int kMaxGroupWarps = 16;   // warps per point group (argmax buffers hold 16)
 
 static bool cfg_valid(int NC, ShapeCfg c)
 {
-    return c.G >= 1 && c.G <= 4 && c.ppb >= 1 && c.ppb <= 15 && c.ppb * c.G * 32 <= 1024 &&
+    return c.G >= 1 && c.G <= kMaxGroupWarps && c.ppb >= 1 && c.ppb <= 15 && c.ppb * c.G * 32 <= 1024 &&
            (size_t)c.ppb * point_bytes(NC) <= kShapeSmemBudget;
 }
 
@@ -589,7 +678,7 @@ static ShapeCfg default_cfg(int NC)
 {
     ShapeCfg c;
     c.ppb = (int)std::min<size_t>(15, kShapeSmemBudget / point_bytes(NC));  // points (groups) per block
-    c.G = std::max(1, std::min(4, 32 / std::max(1, c.ppb)));               // warps per point
+    c.G = std::max(1, std::min(c.ppb <= 2 ? 8 : 4, 32 / std::max(1, c.ppb)));   // warps per point
     return c;
 }
 
@@ -621,12 +710,16 @@ rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, c
 {
     if (n_pts == 0) return RPIM_OK;
     if (max_n > RPIM_MAX_SUPPORT) return fail(RPIM_E_SUPPORT, "support larger than RPIM_MAX_SUPPORT");
+    if (p->shape_kind != RPIM_SHAPE_RPIM)   // MLS or Shepard
+        return mls_shape_functions(p, n_pts, pts, inst_of, shift, order, soff, sidx, phi, s, tag);
     const int NC = std::max(8, (int)max_n);
     if (point_bytes(NC) > kShapeSmemBudget) return fail(RPIM_E_SUPPORT, "support too large for shared memory");
     return launch_shape(p, n_pts, pts, inst_of, shift, order, soff, sidx, NC, shape_cfg(NC), phi, s, tag);
 }
 
-rpim_status shape_functions_all(rpim_pattern *p, double *phi, cudaStream_t s)
+static std::atomic<int> g_persistent{1};
+
+static rpim_status shape_functions_buckets(rpim_pattern *p, double *phi, cudaStream_t s)
 {
     int64_t start = 0;
     for (size_t b = 0; b < p->bucket_count.size(); b++) {
@@ -639,6 +732,117 @@ rpim_status shape_functions_all(rpim_pattern *p, double *phi, cudaStream_t s)
     return RPIM_OK;
 }
 
+// Plan of the persistent launch over the pattern's buckets (a sample of
+// `frac` of every bucket when tuning). Returns the shared memory and threads
+// per block and the largest number of blocks with work.
+static rpim_status bucket_plan(const rpim_pattern *p, double frac, BucketPlan *plan, size_t *smem_out,
+                               int *threads_out, int64_t *blocks_out)
+{
+    *plan = BucketPlan{};
+    struct B { int NC; ShapeCfg c; int64_t start, count; };
+    std::vector<B> bs;
+    int64_t start = 0;
+    for (size_t b = 0; b < p->bucket_count.size(); b++) {
+        const int64_t full = p->bucket_count[b];
+        const int64_t cnt = frac >= 1.0 ? full : std::min<int64_t>(full, (int64_t)(full * frac) + 1);
+        if (cnt > 0) {
+            if (p->bucket_nc[b] > RPIM_MAX_SUPPORT) return fail(RPIM_E_SUPPORT, "support larger than RPIM_MAX_SUPPORT");
+            const int NC = std::max(8, (int)p->bucket_nc[b]);
+            if (point_bytes(NC) > kShapeSmemBudget) return fail(RPIM_E_SUPPORT, "support too large for shared memory");
+            bs.push_back(B{NC, shape_cfg(NC), start, cnt});
+        }
+        start += full;
+    }
+    if ((int)bs.size() > kMaxTileBuckets) return fail(RPIM_E_ARG, "too many support-size buckets");
+    std::stable_sort(bs.begin(), bs.end(), [](const B &a, const B &b) { return a.NC > b.NC; });
+    size_t smem = 0;
+    int threads = 32;
+    int64_t blocks = 1;
+    plan->nb = (int)bs.size();
+    for (int b = 0; b < plan->nb; b++) {
+        plan->NC[b] = bs[b].NC;
+        plan->G[b] = bs[b].c.G;
+        plan->ppb[b] = bs[b].c.ppb;
+        plan->start[b] = bs[b].start;
+        plan->count[b] = bs[b].count;
+        plan->total += bs[b].count;
+        smem = std::max(smem, (size_t)bs[b].c.ppb * point_bytes(bs[b].NC));
+        threads = std::max(threads, bs[b].c.ppb * bs[b].c.G * 32);
+        blocks = std::max<int64_t>(blocks, (bs[b].count + bs[b].c.ppb - 1) / bs[b].c.ppb);
+    }
+    *smem_out = smem;
+    *threads_out = threads;
+    *blocks_out = blocks;
+    return RPIM_OK;
+}
+
+static rpim_status shape_functions_tiles(rpim_pattern *p, double *phi, cudaStream_t s, double frac = 1.0)
+{
+    BucketPlan plan;
+    size_t smem = 0;
+    int threads = 0;
+    int64_t need = 0;
+    RPIM_CHECK(bucket_plan(p, frac, &plan, &smem, &threads, &need));
+    if (plan.total == 0) return RPIM_OK;
+    if (!p->tile_counter) RPIM_CHECK(dalloc(&p->tile_counter, kMaxTileBuckets, s));
+    RPIM_CUDA(cudaMemsetAsync(p->tile_counter, 0, kMaxTileBuckets * sizeof(unsigned long long), s));
+    RPIM_CUDA(cudaFuncSetAttribute(shape_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    RPIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shape_tiles_kernel, threads, smem));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)p->sm_count * std::max(1, per_sm), need));
+    launch("shape", shape_tiles_kernel, (unsigned)blocks, threads, smem, s, plan, p->tile_counter,
+           (const double *)p->pts, (const int32_t *)p->node_inst, 3, (const InstGrid *)p->ig,
+           (const int32_t *)p->bucket_order, (const int64_t *)p->soff, (const int32_t *)p->sidx,
+           (const double *)p->xyz, (const KernelSeries *)p->series, phi, p->err);
+    RPIM_CUDA(cudaGetLastError());
+    return RPIM_OK;
+}
+
+// Everything that decides what shape_functions_all launches for a pattern
+// (kind, schedule, the tile plan with its tuned launch shapes): a captured
+// assembly graph stays valid while this key is unchanged.
+rpim_status shape_launch_key(const rpim_pattern *p, std::vector<unsigned char> *key)
+{
+    key->clear();
+    auto put = [&](const void *a, size_t n) {
+        const unsigned char *c = (const unsigned char *)a;
+        key->insert(key->end(), c, c + n);
+    };
+    const int kind = p->shape_kind, sched = g_persistent.load();
+    put(&kind, sizeof kind);
+    put(&sched, sizeof sched);
+    if (kind == RPIM_SHAPE_RPIM) {
+        if (sched) {
+            BucketPlan plan;
+            size_t smem = 0;
+            int threads = 0;
+            int64_t blocks = 0;
+            RPIM_CHECK(bucket_plan(p, 1.0, &plan, &smem, &threads, &blocks));
+            put(&plan, sizeof plan);
+        } else {
+            for (size_t b = 0; b < p->bucket_count.size(); b++) {
+                const int NC = std::max(8, (int)p->bucket_nc[b]);
+                const ShapeCfg c = shape_cfg(NC);
+                put(&p->bucket_count[b], sizeof(int64_t));
+                put(&NC, sizeof NC);
+                put(&c, sizeof c);
+            }
+        }
+    }
+    return RPIM_OK;
+}
+
+rpim_status shape_functions_all(rpim_pattern *p, double *phi, cudaStream_t s)
+{
+    // MLS and Shepard: one launch over all points in their natural order (the
+    // eight points of a cell, which share most of their support, run side by
+    // side)
+    if (p->shape_kind != RPIM_SHAPE_RPIM)
+        return mls_shape_functions(p, p->n_points, p->pts, p->node_inst, 3, nullptr, p->soff, p->sidx, phi, s,
+                                   p->shape_kind == RPIM_SHAPE_MLS ? "mls_shape" : "shepard_shape");
+    return g_persistent.load() ? shape_functions_tiles(p, phi, s) : shape_functions_buckets(p, phi, s);
+}
+
 } // namespace rpim
 
 using namespace rpim;
@@ -647,6 +851,10 @@ extern "C" rpim_status rpim_autotune_shape(rpim_pattern *p, int64_t max_points, 
                                            rpim_stream_t stream)
 {
     if (!p || max_points < 1) return fail(RPIM_E_ARG, "bad argument");
+    if (p->shape_kind != RPIM_SHAPE_RPIM) {   // only the RPIM kernel has launch shapes to tune
+        if (n_table) *n_table = 0;
+        return RPIM_OK;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;
     if (!p->phi) RPIM_CHECK(dalloc(&p->phi, 4 * p->n_entries, s));
@@ -664,7 +872,7 @@ extern "C" rpim_status rpim_autotune_shape(rpim_pattern *p, int64_t max_points, 
         if (cnt == 0 || point_bytes(NC) > kShapeSmemBudget) continue;
         ShapeCfg best = default_cfg(NC);
         float best_ms = 1e30f;
-        for (int G = 1; G <= 4 && st == RPIM_OK; G++)
+        for (int G : {1, 2, 3, 4, 6, 8, 12, 16})
             for (int ppb = 1; ppb <= 15 && st == RPIM_OK; ppb++) {
                 const ShapeCfg c{ppb, G};
                 if (!cfg_valid(NC, c)) continue;
@@ -717,7 +925,75 @@ extern "C" rpim_status rpim_autotune_set(int32_t max_support, int32_t warps_per_
 
 extern "C" rpim_status rpim_autotune_reset(void)
 {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    for (auto &c : g_tuned) c = ShapeCfg{};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto &c : g_tuned) c = ShapeCfg{};
+    }
+    set_default_buckets({});
     return RPIM_OK;
+}
+
+extern "C" rpim_status rpim_set_shape_schedule(int32_t persistent)
+{
+    if (persistent != 0 && persistent != 1) return fail(RPIM_E_ARG, "schedule must be 0 or 1");
+    g_persistent.store(persistent);
+    return RPIM_OK;
+}
+
+// Bucket bounds autotuner: candidate bound sets (the built-in one and
+// uniform widths of 4-32 support sizes between the smallest and largest
+// support) are each applied to the pattern and the persistent shape pass is
+// timed on a sample of every bucket (CUDA events); the fastest set stays.
+extern "C" rpim_status rpim_autotune_buckets(rpim_pattern *p, int64_t max_points, int32_t *bounds_out,
+                                             int32_t *n_bounds_out, rpim_stream_t stream)
+{
+    if (!p || max_points < 1) return fail(RPIM_E_ARG, "bad argument");
+    if (p->shape_kind != RPIM_SHAPE_RPIM) {
+        if (n_bounds_out) *n_bounds_out = 0;
+        return RPIM_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    if (!p->phi) RPIM_CHECK(dalloc(&p->phi, 4 * p->n_entries, s));
+    std::vector<std::vector<int32_t>> cands;
+    cands.push_back({40, 56, 72, 96, 128, 160});
+    for (int w : {4, 8, 12, 16, 24, 32}) {
+        std::vector<int32_t> b;
+        for (int v = std::max(8, (int)p->min_support + w - 1); v < (int)p->max_support; v += w) b.push_back(v);
+        if (b.empty()) b.push_back((int32_t)p->max_support);
+        if ((int)b.size() <= 31) cands.push_back(b);
+    }
+    const double frac = std::min(1.0, (double)max_points / (double)std::max<int64_t>(1, p->n_points));
+    cudaEvent_t e0, e1;
+    RPIM_CUDA(cudaEventCreate(&e0));
+    RPIM_CUDA(cudaEventCreate(&e1));
+    rpim_status st = RPIM_OK;
+    float best_ms = 1e30f;
+    size_t best = 0;
+    for (size_t c = 0; c < cands.size() && st == RPIM_OK; c++) {
+        st = rpim_pattern_set_buckets(p, (int32_t)cands[c].size(), cands[c].data(), stream);
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3 && st == RPIM_OK; rep++) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) { st = fail(RPIM_E_CUDA, "tune: event"); break; }
+            st = shape_functions_tiles(p, p->phi, s, frac);
+            if (st != RPIM_OK) break;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                st = fail(RPIM_E_CUDA, "tune: event");
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms = std::min(ms, t);
+        }
+        if (st == RPIM_OK && ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == RPIM_OK) st = rpim_pattern_set_buckets(p, (int32_t)cands[best].size(), cands[best].data(), stream);
+    RPIM_CHECK(st);
+    set_default_buckets(cands[best]);
+    if (n_bounds_out) *n_bounds_out = (int32_t)cands[best].size();
+    if (bounds_out)
+        for (size_t i = 0; i < cands[best].size(); i++) bounds_out[i] = cands[best][i];
+    return check_device_error(p, "autotune buckets");
 }

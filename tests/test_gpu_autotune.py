@@ -40,7 +40,7 @@ def test_forced_launch_shapes_give_identical_results(batch):
     tried = 0
     # force the shape for every support size where it is admissible (the
     # others keep the built-in rule), so each pass mixes launch shapes
-    for G, ppb in [(1, 4), (2, 3), (3, 2), (4, 1), (1, 8), (2, 5)]:
+    for G, ppb in [(1, 4), (2, 3), (3, 2), (4, 1), (1, 8), (2, 5), (8, 1), (16, 2), (12, 1)]:
         R.rpim_autotune_reset()
         n_set = 0
         for nc in range(8, nmax + 1):
@@ -56,7 +56,7 @@ def test_forced_launch_shapes_give_identical_results(batch):
         assert torch.equal(phi, phi0), (G, ppb)
         assert torch.equal(K, K0), (G, ppb)
         tried += 1
-    assert tried >= 4
+    assert tried >= 6
     R.rpim_autotune_reset()
 
 
@@ -68,7 +68,7 @@ def test_autotuner_picks_admissible_shapes_and_keeps_K(batch):
     print("tuned (largest support, warps per point, points per block):", table)
     assert len(table) >= 2
     for nc, G, ppb in table:
-        assert 1 <= G <= 4 and 1 <= ppb <= 15 and G * ppb * 32 <= 1024
+        assert 1 <= G <= 16 and 1 <= ppb <= 15 and G * ppb * 32 <= 1024
     K, f = pat.assemble(E, nu)
     assert torch.equal(K, K0)
     assert torch.equal(f, f0)
@@ -78,5 +78,7 @@ def test_autotuner_picks_admissible_shapes_and_keeps_K(batch):
 def test_inadmissible_shape_rejected():
     with pytest.raises(R.RpimError):
         R.rpim_autotune_set(200, 4, 15)   # 1920 threads
+    with pytest.raises(R.RpimError):
+        R.rpim_autotune_set(100, 17, 1)   # more warps than the argmax buffers hold
     with pytest.raises(R.RpimError):
         R.rpim_autotune_set(216, 1, 15)   # shared memory of 15 large points

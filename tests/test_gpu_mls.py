@@ -1,0 +1,209 @@
+"""Parity of the MLS and Shepard shape-function variants (Sec. 4 lists moving
+least squares and Shepard functions as planned alternatives to RPIM) on the
+CUDA path with the oracle's.
+
+Tolerances, from the arithmetic: in local coordinates the 4x4 MLS moment
+matrix is well conditioned (cond ~ 1e1-1e3) and Shepard has no system at
+all, so two FP64 evaluations of the same definition agree to a few ulps
+times the support size. The pins (test_oracle_mls.py,
+test_oracle_shepard.py) show the f64 oracle within ~1e-13 of the extended
+one.
+The GPU values must agree with the extended oracle to TOL_PHI (shape
+functions, gradients scaled by h) and TOL_K (K entrywise, relative to
+max|K|): both about 100x the observed FP64 spread, far below any modelling
+effect. Pattern, supports and points are shared with the RPIM path and are
+compared bitwise there.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+from gpu_util import bsr_matvec, t
+
+import paper_1802_04256_gb300 as R
+
+pytestmark = pytest.mark.gpu
+
+TOL_PHI = 1e-12
+TOL_K = 1e-12
+
+PROBLEMS = {
+    "cube6_jitter": lambda: gen.cube_config(jitter=0.2, seed=7),
+    "ragged": lambda: gen.cantilever_config(shape=(9, 7, 7), length=1.0, jitter=0.15, seed=9),
+    "column": lambda: gen.gravity_column(),
+}
+
+
+KINDS = ["mls", "shepard"]
+ORACLE_SHAPE = {"mls": oracle.shape_mls, "shepard": oracle.shape_shepard}
+
+
+class MlsRun:
+    def __init__(self, p, kind="mls"):
+        self.p = p
+        self.kind = kind
+        self.pat = R.Pattern.from_problem(p, shape=kind)
+        self.E, self.nu = t(p.E), t(p.nu)
+        self.body = t(p.body) if np.any(p.body) else None
+        self.K, self.f = self.pat.assemble(self.E, self.nu, self.body)
+        if len(p.load_xyz):
+            self.pat.add_point_loads(t(p.load_xyz), t(p.load_force), self.f)
+        torch.cuda.synchronize()
+
+
+@pytest.fixture(scope="module", params=[(k, n) for k in KINDS for n in sorted(PROBLEMS)],
+                ids=lambda kn: "%s-%s" % kn)
+def case(request):
+    kind, name = request.param
+    p = PROBLEMS[name]()
+    g = MlsRun(p, kind)
+    with oracle.shape_kind(kind):
+        m = oracle.assemble_problem(p, "f64")
+    return p, g, m
+
+
+def test_kind_is_recorded(case):
+    p, g, m = case
+    assert g.pat.shape == g.kind
+
+
+def test_shape_functions_vs_oracle(case):
+    p, g, m = case
+    phi = g.pat.shape_functions().cpu().numpy()
+    xyz, wj, soff, sidx = [a.cpu().numpy() for a in g.pat.points()]
+    scale = np.array([1.0, p.h, p.h, p.h])
+    worst = e64 = 0.0
+    for k in range(0, p.n_points, max(1, p.n_points // 150)):
+        s = sidx[soff[k]:soff[k + 1]]
+        mine = phi[soff[k]:soff[k + 1]].T * scale[:, None]
+        a = ORACLE_SHAPE[g.kind](p.xyz, s, xyz[k], p.h, p.alpha_s, "f64") * scale[:, None]
+        b = ORACLE_SHAPE[g.kind](p.xyz, s, xyz[k], p.h, p.alpha_s, "ld") * scale[:, None]
+        worst = max(worst, np.abs(mine - b).max())
+        e64 = max(e64, np.abs(a - b).max())
+    print("%s phi: |gpu - ld| %.3e, |f64 - ld| %.3e" % (g.kind, worst, e64))
+    assert worst < TOL_PHI
+
+
+def test_K_and_f_vs_oracle(case):
+    p, g, m = case
+    K = g.K.cpu().numpy()
+    rowptr, cols = [a.cpu().numpy() for a in g.pat.csr()]
+    assert np.array_equal(rowptr, m.rowptr) and np.array_equal(cols, m.cols)
+    kmax = np.abs(m.vals).max()
+    d64 = np.abs(K - m.vals).max() / kmax
+    if p.n_nodes <= 250:
+        with oracle.shape_kind(g.kind):
+            ml = oracle.assemble_problem(p, "ld")
+        dld = np.abs(K - ml.vals).max() / kmax
+    else:
+        dld = d64
+    print("%s K: |gpu - ld| %.3e, |gpu - f64| %.3e" % (g.kind, dld, d64))
+    assert dld < TOL_K and d64 < TOL_K
+    fd = np.abs(g.f.cpu().numpy() - m.f).max() / max(np.abs(m.f).max(), 1e-300)
+    print("%s f: rel %.3e" % (g.kind, fd))
+    assert fd < 1e-12
+
+
+def test_K_symmetric_and_rigid_modes(case):
+    p, g, m = case
+    rowptr, cols = [a.cpu().numpy() for a in g.pat.csr()]
+    K = g.K.cpu().numpy()
+    rows = np.repeat(np.arange(p.n_nodes), np.diff(rowptr))
+    key = rows.astype(np.int64) * p.n_nodes + cols
+    tkey = cols.astype(np.int64) * p.n_nodes + rows
+    order = np.argsort(key)
+    pos = order[np.searchsorted(key[order], tkey)]
+    Kb = K.reshape(-1, 3, 3)
+    assert np.array_equal(Kb, np.transpose(Kb[pos], (0, 2, 1)))
+    X = p.xyz - p.xyz.mean(0)
+    kn = np.abs(K).max() * np.sqrt(3 * p.n_nodes)
+    # MLS reproduces linear fields (six rigid modes); Shepard only constants
+    for mode in range(6 if g.kind == "mls" else 3):
+        u = np.zeros((p.n_nodes, 3))
+        if mode < 3:
+            u[:, mode] = 1.0
+        else:
+            a, b = [(1, 2), (2, 0), (0, 1)][mode - 3]
+            u[:, a] = -X[:, b]
+            u[:, b] = X[:, a]
+        r = bsr_matvec(rowptr, cols, K.ravel(), u.ravel())
+        assert np.linalg.norm(r) / (kn * np.linalg.norm(u)) < 1e-12
+
+
+def test_solution_and_stress_vs_oracle(case):
+    p, g, m = case
+    K, f = g.K.clone(), g.f.clone()
+    g.pat.apply_penalty(K, f, t(p.fixed_dofs, torch.int64), t(p.fixed_vals))
+    u, it, rr = g.pat.solve_pcg(K, f, rtol=1e-12)
+    with oracle.shape_kind(g.kind):
+        mo, uo, ito, rro, ao = oracle.solve_problem(p, "f64", rtol=1e-12)
+        d = np.linalg.norm(u.cpu().numpy() - uo) / np.linalg.norm(uo)
+        print("%s u: rel %.3e (%d / %d iterations)" % (g.kind, d, it, ito))
+        assert d < 1e-7
+        pts = m.pts[:: max(1, len(m.pts) // 64)]
+        E = np.full(len(pts), p.E[0])
+        nu = np.full(len(pts), p.nu[0])
+        sg = g.pat.stress(u, t(pts), t(E), t(nu)).cpu().numpy()
+        so = oracle.stress(p.xyz, u.cpu().numpy(), pts, E, nu, p.alpha_s, p.alpha_c, p.q, p.h, "f64")
+    ds = np.abs(sg - so).max() / np.abs(so).max()
+    print("%s stress: rel %.3e" % (g.kind, ds))
+    assert ds < 1e-11
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_material_gradient_vs_oracle(kind):
+    p = gen.cube_config(n=5, jitter=0.2, seed=11)
+    g = MlsRun(p, kind)
+    rng = np.random.default_rng(0)
+    u = t(rng.standard_normal(3 * p.n_nodes))
+    lam = t(rng.standard_normal(3 * p.n_nodes))
+    dE = torch.empty_like(g.E)
+    dnu = torch.empty_like(g.nu)
+    R.rpim_grad_material(g.pat.handle, u, lam, g.E, g.nu, dE, dnu)
+    xyz, wj, soff, sidx = [a.cpu().numpy() for a in g.pat.points()]
+    with oracle.shape_kind(kind):
+        oE, onu = oracle.grad_material(p.xyz, xyz, wj, p.E, p.nu, u.cpu().numpy(), lam.cpu().numpy(),
+                                       p.alpha_s, p.alpha_c, p.q, p.h)
+    assert np.abs(dE.cpu().numpy() - oE).max() < 1e-11 * np.abs(oE).max()
+    assert np.abs(dnu.cpu().numpy() - onu).max() < 1e-11 * np.abs(onu).max()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_batched_equals_per_instance(kind):
+    probs = [gen.cube_config(n=5, jitter=0.2, seed=31),
+             gen.cantilever_config(shape=(9, 4, 4), length=2.0, jitter=0.1, seed=32)]
+    pat, offs = R.Pattern.batched(probs)
+    pat.set_shape(kind)
+    E = t(np.concatenate([p.E for p in probs]))
+    nu = t(np.concatenate([p.nu for p in probs]))
+    K, f = pat.assemble(E, nu)
+    rowptr = pat.csr()[0].cpu().numpy()
+    Kh = K.cpu().numpy()
+    for k, p in enumerate(probs):
+        one = R.Pattern.from_problem(p, shape=kind)
+        K1, f1 = one.assemble(t(p.E), t(p.nu))
+        sl = slice(rowptr[offs[k]], rowptr[offs[k + 1]])
+        d = np.abs(Kh[sl] - K1.cpu().numpy()).max() / np.abs(K1.cpu().numpy()).max()
+        assert d == 0.0, d   # no kernel series is involved: bit for bit
+        one.free()
+
+
+def test_switching_kind_back_restores_rpim():
+    p = gen.cube_config(n=5)
+    pat = R.Pattern.from_problem(p)
+    E, nu = t(p.E), t(p.nu)
+    K0, _ = pat.assemble(E, nu)
+    pat.set_shape("mls")
+    K1, _ = pat.assemble(E, nu)
+    assert not torch.equal(K0, K1)
+    pat.set_shape("shepard")
+    K3, _ = pat.assemble(E, nu)
+    assert not torch.equal(K1, K3)
+    pat.set_shape("rpim")
+    K2, _ = pat.assemble(E, nu)
+    assert torch.equal(K0, K2)
+    with pytest.raises(R.RpimError) as e:
+        R.rpim_pattern_set_shape(pat.handle, 7)
+    assert e.value.status == 1
