@@ -504,7 +504,21 @@ def _batched(n_sel, dev, stream, reps=1, warm=1):
         lrs += (R.rpim_kernel_launches() - l0) / 2
         pt.free()
         del K1, f1
+    # the same per-instance re-assembly with the unbucketed kernel: one shape
+    # launch per instance sized for that instance's largest support (every
+    # point gets the largest point's shared-memory buffers and launch shape)
+    ru = 0.0
+    R.rpim_set_shape_schedule(False)
+    for p, d in zip(sel, single):
+        pt = R.Pattern(d["x"], d["lo"], d["hi"], p.alpha_s, p.alpha_c, p.q, p.h)
+        R.rpim_pattern_set_buckets(pt.handle, [1 << 29])
+        K1, f1 = pt.assemble(d["E"], d["nu"])
+        ru += min(timed(lambda: pt.assemble(d["E"], d["nu"], K=K1, f=f1))[0] for _ in range(2))
+        pt.free()
+        del K1, f1
+    R.rpim_set_shape_schedule(True)
     reasm = {"batched_graph_ms": min(rb), "per_instance_ms": rs, "speedup": rs / min(rb),
+             "per_instance_unbucketed_ms": ru, "speedup_vs_unbucketed": ru / min(rb),
              "batched_pts_per_s": npts / (min(rb) / 1e3), "per_instance_pts_per_s": npts / (rs / 1e3),
              "kernel_launches": {"batched": lrb, "per_instance": lrs},
              "kernel_ms": {k: round(v[1] / v[0], 3) for k, v in sorted(kprof.items(), key=lambda kv: -kv[1][1])},
@@ -513,7 +527,8 @@ def _batched(n_sel, dev, stream, reps=1, warm=1):
              "shape_tflops": fl_shape / (kprof["shape"][1] / 1e3) / 1e12 if "shape" in kprof else None,
              "support_sizes": {"min": int(nsup.min()), "max": int(nsup.max()), "mean": float(nsup.mean())},
              "step": "rpim_assemble_graphed on the batched pattern vs rpim_assemble per instance "
-                     "(patterns built beforehand, not timed)"}
+                     "(patterns built beforehand, not timed); unbucketed: one support-size bucket and one "
+                     "shape launch per instance"}
     return {"instances": len(sel), "of": len(allp), "selection": "every %d-th block of the 512-block workload"
             % max(1, len(allp) // n_sel), "n_nodes": int(offs[-1]), "n_points": npts,
             "node_range": [int(min(p.n_nodes for p in sel)), int(max(p.n_nodes for p in sel))],

@@ -83,6 +83,8 @@ struct InstGrid {
     double rs2;          // support radius squared
     double inv_h;        // 1 / nodal spacing
     int n[3];            // cells per axis
+    float q_cell;        // rs2 in squared cell edges (single precision)
+    float margin;        // bound on the single-precision error of a squared distance in cell units
     int pad;
     int64_t cell_off;    // first global cell of the instance
     int64_t node_begin, node_end;
@@ -167,6 +169,7 @@ struct rpim_pattern {
     // nodes
     double *xyz = nullptr;          // [n_nodes*3] copy of the coordinates
     double *sorted_xyz = nullptr;   // [n_nodes*4] coordinates in cell order (x,y,z,pad)
+    float *sorted_loc = nullptr;    // [n_nodes*4] the same in cell edges from the grid origin, FP32
     int32_t *sorted_ids = nullptr;  // [n_nodes] node ids in cell order
     int32_t *cell_start = nullptr;  // [cells+1]
     int32_t *node_cell = nullptr;   // [n_nodes] linear cell index of each node

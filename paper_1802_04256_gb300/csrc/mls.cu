@@ -26,9 +26,10 @@
 namespace rpim {
 
 // LU factorisation with partial pivoting (largest magnitude, lowest row on
-// ties) of a 4x4 matrix in place; piv[k] = row swapped into position k.
-// Returns false when a pivot is below 1e-13 times the largest entry.
-__device__ __forceinline__ bool lu4(double M[4][4], int piv[4])
+// ties) of a 4x4 matrix in place; piv[k] = row swapped into position k,
+// rinv[k] = 1 / U_kk. Returns false when a pivot is below 1e-13 times the
+// largest entry.
+__device__ __forceinline__ bool lu4(double M[4][4], int piv[4], double rinv[4])
 {
     double amax = 0.0;
 #pragma unroll
@@ -54,9 +55,10 @@ __device__ __forceinline__ bool lu4(double M[4][4], int piv[4])
                     M[i][j] = t;
                 }
             }
+        rinv[k] = 1.0 / M[k][k];
 #pragma unroll
         for (int i = k + 1; i < 4; i++) {
-            const double l = M[i][k] / M[k][k];
+            const double l = M[i][k] * rinv[k];
             M[i][k] = l;
 #pragma unroll
             for (int j = k + 1; j < 4; j++) M[i][j] = fma(-l, M[k][j], M[i][j]);
@@ -67,7 +69,7 @@ __device__ __forceinline__ bool lu4(double M[4][4], int piv[4])
 
 // solves (the factorised) M y = r in place, same row exchanges and
 // multipliers as the factorisation
-__device__ __forceinline__ void lu4_solve(const double M[4][4], const int piv[4], double r[4])
+__device__ __forceinline__ void lu4_solve(const double M[4][4], const int piv[4], const double rinv[4], double r[4])
 {
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -84,7 +86,7 @@ __device__ __forceinline__ void lu4_solve(const double M[4][4], const int piv[4]
         double s = r[k];
 #pragma unroll
         for (int i = k + 1; i < 4; i++) s = fma(-M[k][i], r[i], s);
-        r[k] = s / M[k][k];
+        r[k] = s * rinv[k];
     }
 }
 
@@ -142,12 +144,13 @@ __global__ void __launch_bounds__(128) mls_shape_kernel(int64_t n_pts, const dou
             const int64_t J = sidx[q];
             const double x0 = (xyz[3 * J] - gx) * inv_h, x1 = (xyz[3 * J + 1] - gy) * inv_h,
                          x2 = (xyz[3 * J + 2] - gz) * inv_h;
-            const double d = sqrt(fma(x2, x2, fma(x1, x1, x0 * x0)));
-            const double sb = d * inv_as;
+            const double d2 = fma(x2, x2, fma(x1, x1, x0 * x0));
+            const double rd = d2 > 0.0 ? rsqrt(d2) : 0.0;   // 1 / |xi| (0 for a node at the point)
+            const double sb = d2 * rd * inv_as;
             double w, dws;
             spline_weight(sb, w, dws);
             // dw/dx_k = w'(sb) d sb/dx_k = -w'(sb) xi_k / (alpha_s h |xi|)
-            const double c = d > 0.0 ? -dws * inv_as * inv_h / d : 0.0;
+            const double c = -dws * inv_as * inv_h * rd;
             const double w0 = c * x0, w1 = c * x1, w2 = c * x2;
             *(double2 *)(phi + 4 * q) = make_double2(w, w0);
             *(double2 *)(phi + 4 * q + 2) = make_double2(w1, w2);
@@ -160,15 +163,15 @@ __global__ void __launch_bounds__(128) mls_shape_kernel(int64_t n_pts, const dou
                 dA[2][t] = fma(w2, pp[t], dA[2][t]);
             }
         }
-        double M[4][4];
+        double M[4][4], rinv[4];
         int piv[4];
         sym4(A, M);
-        if (!lu4(M, piv)) {
+        if (!lu4(M, piv, rinv)) {
             dev_fail(err, RPIM_E_SINGULAR, p);
             continue;
         }
         double gam[4] = {1.0, 0.0, 0.0, 0.0};
-        lu4_solve(M, piv, gam);
+        lu4_solve(M, piv, rinv, gam);
         double dg[3][4];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(128) mls_shape_kernel(int64_t n_pts, const dou
                 for (int c2 = 0; c2 < 4; c2++) s = fma(-D[a][c2], gam[c2], s);
                 dg[k][a] = s;
             }
-            lu4_solve(M, piv, dg[k]);
+            lu4_solve(M, piv, rinv, dg[k]);
         }
         // pass 2: phi_i = w_i p_i.gamma, dphi_i/dx_k = dw_i/dx_k p_i.gamma + w_i p_i.dgamma_k
         bool finite = true;
@@ -239,11 +242,12 @@ __global__ void __launch_bounds__(128) shepard_shape_kernel(int64_t n_pts, const
             const int64_t J = sidx[q];
             const double x0 = (xyz[3 * J] - gx) * inv_h, x1 = (xyz[3 * J + 1] - gy) * inv_h,
                          x2 = (xyz[3 * J + 2] - gz) * inv_h;
-            const double d = sqrt(fma(x2, x2, fma(x1, x1, x0 * x0)));
-            const double sb = d * inv_as;
+            const double d2 = fma(x2, x2, fma(x1, x1, x0 * x0));
+            const double rd = d2 > 0.0 ? rsqrt(d2) : 0.0;
+            const double sb = d2 * rd * inv_as;
             double w, dws;
             spline_weight(sb, w, dws);
-            const double c = d > 0.0 ? -dws * inv_as * inv_h / d : 0.0;
+            const double c = -dws * inv_as * inv_h * rd;
             *(double2 *)(phi + 4 * q) = make_double2(w, c * x0);
             *(double2 *)(phi + 4 * q + 2) = make_double2(c * x1, c * x2);
             W += w;

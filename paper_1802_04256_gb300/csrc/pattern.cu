@@ -134,7 +134,8 @@ __global__ void fill_cells(int64_t n, const int32_t *node_cell, const int32_t *c
 // one thread per cell: insertion sort of the (few) ids, then coordinates
 // in cell order and each node's rank in that order
 __global__ void finish_cells(int64_t cells, const int32_t *cell_start, int32_t *sorted_ids,
-                             const double *xyz, double *sorted_xyz, int32_t *node_rank, int *max_cell)
+                             const double *xyz, const InstGrid *ig, const int32_t *node_inst, double *sorted_xyz,
+                             float *sorted_loc, int32_t *node_rank, int *max_cell)
 {
     int mc = 0;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
@@ -154,6 +155,11 @@ __global__ void finish_cells(int64_t cells, const int32_t *cell_start, int32_t *
             sorted_xyz[4 * (int64_t)i + 1] = xyz[3 * (int64_t)id + 1];
             sorted_xyz[4 * (int64_t)i + 2] = xyz[3 * (int64_t)id + 2];
             sorted_xyz[4 * (int64_t)i + 3] = 0.0;
+            const InstGrid &g = ig[node_inst[id]];
+            sorted_loc[4 * (int64_t)i + 0] = (float)((xyz[3 * (int64_t)id + 0] - g.lo[0]) * g.inv_edge);
+            sorted_loc[4 * (int64_t)i + 1] = (float)((xyz[3 * (int64_t)id + 1] - g.lo[1]) * g.inv_edge);
+            sorted_loc[4 * (int64_t)i + 2] = (float)((xyz[3 * (int64_t)id + 2] - g.lo[2]) * g.inv_edge);
+            sorted_loc[4 * (int64_t)i + 3] = 0.0f;
         }
     }
     for (int o = 16; o > 0; o >>= 1) mc = max(mc, __shfl_down_sync(0xffffffffu, mc, o));
@@ -177,7 +183,7 @@ __device__ __forceinline__ double dist2(double4 n, double x, double y, double z)
 template <int PASS>
 __global__ void __launch_bounds__(256) search_kernel(int64_t n_pts, const double *pts, const int32_t *inst_of,
                                                      int shift, const InstGrid *ig, const int32_t *cell_start,
-                                                     const double4 *sorted_xyz,
+                                                     const double4 *sorted_xyz, const float4 *sorted_loc,
                                                      const int32_t *sorted_ids,
                                                      int64_t *cnt_or_off, int32_t *sidx,
                                                      int *minmax, DevError *err)
@@ -198,6 +204,10 @@ __global__ void __launch_bounds__(256) search_kernel(int64_t n_pts, const double
             f = fmin(fmax(f, -2.0), (double)g.n[k] + 1.0);
             c[k] = (int)f;
         }
+        // the point in cell edges (FP32) for the prefilter
+        const float ux = (float)((x - g.lo[0]) * g.inv_edge), uy = (float)((y - g.lo[1]) * g.inv_edge),
+                    uz = (float)((z - g.lo[2]) * g.inv_edge);
+        const float q_in = g.q_cell - g.margin, q_out = g.q_cell + g.margin;
         int count = 0;
         for (int dz = -1; dz <= 1; dz++) {
             int cz = c[2] + dz;
@@ -212,7 +222,12 @@ __global__ void __launch_bounds__(256) search_kernel(int64_t n_pts, const double
                 for (int k0 = b; k0 < e; k0 += 32) {
                     int k = k0 + lane;
                     bool in = false;
-                    if (k < e) in = dist2(sorted_xyz[k], x, y, z) <= rs2;
+                    if (k < e) {
+                        const float4 l = sorted_loc[k];
+                        const float ex = l.x - ux, ey = l.y - uy, ez = l.z - uz;
+                        const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                        in = d2 < q_in || (d2 <= q_out && dist2(sorted_xyz[k], x, y, z) <= rs2);
+                    }
                     unsigned m = __ballot_sync(0xffffffffu, in);
                     if (PASS == 1 && in) {
                         int pos = count + __popc(m & ((1u << lane) - 1));
@@ -280,7 +295,7 @@ rpim_status search_supports(rpim_pattern *p, int64_t n_pts, const double *pts, c
     RPIM_CUDA(cudaMemcpyAsync(mm, init, sizeof init, cudaMemcpyHostToDevice, s));
     int grid = grid_size(p->sm_count, 8, n_pts * 32, 256);
     launch(tag, search_kernel<0>, grid, 256, 0, s, n_pts, pts, inst_of, shift, (const InstGrid *)p->ig,
-           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const int32_t *)p->sorted_ids, soff,
+           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const float4 *)p->sorted_loc, (const int32_t *)p->sorted_ids, soff,
            (int32_t *)nullptr, mm, p->err);
     RPIM_CUDA(cudaGetLastError());
     RPIM_CHECK(exclusive_scan(soff, n_pts, tmp, s));
@@ -299,7 +314,7 @@ rpim_status search_supports(rpim_pattern *p, int64_t n_pts, const double *pts, c
     }
     RPIM_CHECK(dalloc(&sidx, ne, s));
     launch(tag, search_kernel<1>, grid, 256, 0, s, n_pts, pts, inst_of, shift, (const InstGrid *)p->ig,
-           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const int32_t *)p->sorted_ids, soff, sidx,
+           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const float4 *)p->sorted_loc, (const int32_t *)p->sorted_ids, soff, sidx,
            (int *)nullptr, p->err);
     RPIM_CUDA(cudaGetLastError());
     *soff_out = soff;
@@ -322,7 +337,7 @@ rpim_status search_supports_into(rpim_pattern *p, int64_t n_pts, const double *p
     RPIM_CUDA(cudaMemcpyAsync(minmax, init, sizeof init, cudaMemcpyHostToDevice, s));
     const int grid = grid_size(p->sm_count, 8, n_pts * 32, 256);
     launch(tag, search_kernel<0>, grid, 256, 0, s, n_pts, pts, (const int32_t *)nullptr, 0, (const InstGrid *)p->ig,
-           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const int32_t *)p->sorted_ids, soff,
+           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const float4 *)p->sorted_loc, (const int32_t *)p->sorted_ids, soff,
            (int32_t *)nullptr, minmax, p->err);
     RPIM_CUDA(cudaGetLastError());
     RPIM_CHECK(exclusive_scan(soff, n_pts, tmp, s));
@@ -343,7 +358,7 @@ rpim_status search_supports_into(rpim_pattern *p, int64_t n_pts, const double *p
         return fail(RPIM_E_ARG, buf);
     }
     launch(tag, search_kernel<1>, grid, 256, 0, s, n_pts, pts, (const int32_t *)nullptr, 0, (const InstGrid *)p->ig,
-           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const int32_t *)p->sorted_ids, soff, sidx,
+           (const int32_t *)p->cell_start, (const double4 *)p->sorted_xyz, (const float4 *)p->sorted_loc, (const int32_t *)p->sorted_ids, soff, sidx,
            (int *)nullptr, p->err);
     RPIM_CUDA(cudaGetLastError());
     *n_entries = ne;
@@ -539,7 +554,7 @@ using namespace rpim;
 static void pattern_release(rpim_pattern *p)
 {
     cudaStream_t s = p->stream;
-    dfree(p->xyz, s); dfree(p->sorted_xyz, s); dfree(p->sorted_ids, s); dfree(p->cell_start, s);
+    dfree(p->xyz, s); dfree(p->sorted_xyz, s); dfree(p->sorted_loc, s); dfree(p->sorted_ids, s); dfree(p->cell_start, s);
     dfree(p->node_cell, s); dfree(p->node_cpk, s); dfree(p->node_rank, s); dfree(p->pts, s); dfree(p->wj, s);
     dfree(p->soff, s); dfree(p->sidx, s); dfree(p->entry_pt, s); dfree(p->toff, s);
     dfree(p->tent, s); dfree(p->rowptr, s); dfree(p->cols, s); dfree(p->diag, s);
@@ -804,6 +819,21 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
         }
         for (int k = 0; k < 3; k++) g.lo[k] = bmin[k];
         g.inv_edge = 1.0 / edge;
+        // Single-precision prefilter of the support test. In cell edges the
+        // test reads |u_n - u_p|^2 <= q, q = rs2 / edge^2, u = (x - lo) / edge.
+        // Nodes and points are rounded to FP32 (|u| <= U = largest extent + 2),
+        // every tested node lies within 2 cells of the point per axis, and the
+        // squared distance is summed in FP32; the bound below covers these
+        // roundings with a 1.5x reserve. Outside [q - margin, q + margin] the
+        // FP32 decision equals the exact one; inside it the FP64 test decides.
+        {
+            const double q = g.rs2 * g.inv_edge * g.inv_edge;
+            const double U = (double)std::max(g.n[0], std::max(g.n[1], g.n[2])) + 2.0;
+            const double e24 = std::ldexp(1.0, -24), W = 2.0002 * U + 2.01;
+            const double m = 3.0 * e24 * (q + 12.2) + 6.0 * 2.01 * e24 * W + 3.0 * e24 * e24 * W * W + 1e-12;
+            g.q_cell = (float)q;
+            g.margin = (float)(1.5 * m);
+        }
         g.cell_off = cell_off;
         cell_off += cells;
     }
@@ -824,6 +854,7 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     RPIM_CHECK(dalloc(&tmp, scan_tmp_size(cells), s));
     RPIM_CHECK(dalloc(&p->sorted_ids, n, s));
     RPIM_CHECK(dalloc(&p->sorted_xyz, 4 * n, s));
+    RPIM_CHECK(dalloc(&p->sorted_loc, 4 * n, s));
     RPIM_CHECK(dalloc(&dmax, 1, s));
     RPIM_CUDA(cudaMemsetAsync(p->cell_start, 0, (cells + 1) * sizeof(int32_t), s));
     RPIM_CUDA(cudaMemsetAsync(cursor, 0, (cells + 1) * sizeof(int32_t), s));
@@ -833,7 +864,7 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     RPIM_CHECK(exclusive_scan32(p->cell_start, cells, tmp, s));
     launch("fill_cells", fill_cells, grid_size(p->sm_count, 4, n, 256), 256, 0, s, n, p->node_cell, p->cell_start, cursor, p->sorted_ids);
     launch("finish_cells", finish_cells, grid_size(p->sm_count, 4, cells, 128), 128, 0, s, cells, p->cell_start, p->sorted_ids, xyz,
-                                                                        p->sorted_xyz, p->node_rank, dmax);
+           (const InstGrid *)p->ig, (const int32_t *)p->node_inst, p->sorted_xyz, p->sorted_loc, p->node_rank, dmax);
     RPIM_CUDA(cudaGetLastError());
     RPIM_CUDA(cudaMemcpyAsync(&p->max_cell, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
     dfree(cursor, s);
