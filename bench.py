@@ -649,6 +649,11 @@ def run_ours(args, rank, world, local_rank):
                 dict(xyz=p.xyz, lo=p.cell_lo, hi=p.cell_hi, E=p.E, nu=p.nu, lx=p.load_xyz, lf=p.load_force).items()}
         h2d = sum(v.numel() * v.element_size() for v in host.values())
         Kh = None
+        # the device->host copy of a step's K and f runs on its own stream,
+        # overlapped with the next step's assembly (pipelined as a caller
+        # would run a stream of problems); record_stream keeps the caching
+        # allocator from reusing K and f before their copy has finished
+        copy_stream = torch.cuda.Stream(device=dev)
 
         def e2e_step():
             nonlocal Kh
@@ -659,8 +664,14 @@ def run_ours(args, rank, world, local_rank):
             if Kh is None:
                 Kh = (torch.empty(K.shape, dtype=K.dtype, pin_memory=True),
                       torch.empty(f.shape, dtype=f.dtype, pin_memory=True))
-            Kh[0].copy_(K, non_blocking=True)
-            Kh[1].copy_(f, non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(stream)
+            copy_stream.wait_event(done)
+            with torch.cuda.stream(copy_stream):
+                Kh[0].copy_(K, non_blocking=True)
+                Kh[1].copy_(f, non_blocking=True)
+            K.record_stream(copy_stream)
+            f.record_stream(copy_stream)
             pat.free()
             return K.numel() * 8 + f.numel() * 8
 

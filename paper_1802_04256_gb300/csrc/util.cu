@@ -385,8 +385,8 @@ rpim_status build_incidence(int64_t n_nodes, int64_t ne, const int32_t *sidx, in
 static rpim_status build_kernel_series_uncached(double alpha_c, double alpha_s, double q, KernelSeries *ks);
 
 // The series depends on (alpha_c, alpha_s, q) only; it is built (and
-// checked, which takes tens of milliseconds where long double is emulated in
-// software) once per parameter set and process.
+// checked against the closed form in long double, a few milliseconds where
+// long double is emulated in software) once per parameter set and process.
 rpim_status build_kernel_series(double alpha_c, double alpha_s, double q, KernelSeries *ks)
 {
     static std::mutex mu;
@@ -490,17 +490,27 @@ static rpim_status build_kernel_series_uncached(double alpha_c, double alpha_s, 
         dv = 0;
         for (int j = D - 1; j >= 0; j--) dv = dv * (L)t + (L)ks->dcoef[k][j];
     };
+    // Sample points: 129 per piece, evenly spaced in t over [-1.02, 1.02]
+    // (a truncated series errs most at the ends of its piece, and the
+    // single-precision piece choice may move a point just across a piece
+    // boundary), clipped to the range of s the device evaluates. Long double
+    // is emulated in software on some hosts, so the sample is kept to a few
+    // thousand closed-form evaluations.
     L worst = 0, worst_d = 0;
-    const int NS = 20000;
-    for (int i = 0; i <= NS; i++) {
-        // sample at doubles: the device only ever sees double arguments
-        const double sd = (double)(c2 + (s_hi - c2) * ((L)i / NS));
-        L s = (L)sd, v, dv;
-        eval(s, v, dv);
-        L want = powl(s, ql) - alpha0 - beta * s;
-        L dwant = ql * powl(s, ql - 1) - beta;
-        worst = fmaxl(worst, fabsl(v - want));
-        worst_d = fmaxl(worst_d, fabsl(dv - dwant));
+    const int NT = 128;
+    for (int k = 0; k < P; k++) {
+        const L m = (L)ks->centre[k], w = 1 / (L)ks->inv_w[k];
+        for (int i = 0; i <= NT; i++) {
+            L sl = m + w * (-1.02L + 2.04L * (L)i / NT);
+            sl = sl < c2 ? c2 : (sl > s_hi ? s_hi : sl);
+            // sample at doubles: the device only ever sees double arguments
+            L s = (L)(double)sl, v, dv;
+            eval(s, v, dv);
+            L want = powl(s, ql) - alpha0 - beta * s;
+            L dwant = ql * powl(s, ql - 1) - beta;
+            worst = fmaxl(worst, fabsl(v - want));
+            worst_d = fmaxl(worst_d, fabsl(dv - dwant));
+        }
     }
     ks->check_err = (double)fmaxl(worst, worst_d);
     if (worst > 5e-17L || worst_d > 5e-17L) {
