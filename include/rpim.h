@@ -140,8 +140,9 @@ rpim_status rpim_build_pattern_batched(int32_t n_inst, const rpim_instance *inst
  * MLS and Shepard shape functions do not interpolate (phi_i(x_j) !=
  * delta_ij), so penalty values act on nodal parameters.
  * The kind is stored in the pattern; set it before the stage that should use
- * it. rpim_autotune_shape tunes the RPIM kernel only (MLS has no launch
- * shape to tune) and leaves an MLS pattern untouched.
+ * it. rpim_autotune_shape and rpim_autotune_buckets tune the RPIM kernel
+ * only (the MLS and Shepard kernels have no launch shape to tune) and leave
+ * such a pattern untouched.
  * Errors: RPIM_E_ARG (null pattern, unknown kind). MLS assembly reports
  * RPIM_E_SINGULAR when the 4x4 moment matrix has a pivot below
  * 1e-13 max|A| (fewer than four non-coplanar weighted nodes); Shepard when
@@ -259,16 +260,17 @@ rpim_status rpim_pattern_get_buckets(const rpim_pattern *pattern, int32_t *n_buc
  * this pattern and as the bounds every pattern built later in the process
  * starts with (like the launch shapes of rpim_autotune_shape).
  *   bounds host int32 [31], optional; n_bounds host, optional.
- * Synchronises. An MLS pattern is left as it is (n_bounds = 0).
+ * Synchronises. An MLS or Shepard pattern is left as it is (n_bounds = 0).
  */
 rpim_status rpim_autotune_buckets(rpim_pattern *pattern, int64_t max_points, int32_t *bounds,
                                   int32_t *n_bounds, rpim_stream_t stream);
 
 /*
  * Schedule of the RPIM shape kernel over the buckets, process-wide:
- * 1 (default) one persistent launch in which blocks take tiles of a bucket
- * (largest supports first) from a device counter; 0 one launch per bucket.
- * The shape functions are bitwise the same either way. Errors: RPIM_E_ARG.
+ * 1 (default) one persistent launch: the blocks walk the buckets, largest
+ * supports first, and each point group takes the bucket's next point from a
+ * device counter; 0 one launch per bucket. The shape functions are bitwise
+ * the same either way. Errors: RPIM_E_ARG.
  */
 rpim_status rpim_set_shape_schedule(int32_t persistent);
 
