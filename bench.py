@@ -173,9 +173,17 @@ def whole_job_rate(units_per_rank, world, ms):
 
 
 # --------------------------------------------------------------------------- CPU baseline
+def _spread(n, m):
+    """Every k-th of n items, m of them (a sample spread evenly over the
+    workload, interior and boundary points in their proportions)."""
+    k = max(1, n // max(1, m))
+    return slice(0, k * min(m, n), k), k
+
+
 def cpu_baseline(p, budget_s=15.0):
-    """The oracle (FP64, OpenMP over points on all host cores) on the first M
-    Gauss points of the workload, M sized to about `budget_s` seconds."""
+    """The oracle (FP64, OpenMP over points on all host cores) on M Gauss
+    points spread evenly over the workload, M sized to about `budget_s`
+    seconds; and the same oracle on one thread on a smaller spread sample."""
     import oracle
     oracle.build()
     cores = _cores()
@@ -183,17 +191,23 @@ def cpu_baseline(p, budget_s=15.0):
     pts, wj = oracle.gauss_points(p.cell_lo, p.cell_hi)
 
     def run(m):
+        sel, k = _spread(len(pts), m)
         t0 = time.perf_counter()
-        oracle.assemble(p.xyz, pts[:m], wj[:m], p.E[:m], p.nu[:m], p.alpha_s, p.alpha_c, p.q, p.h)
-        return time.perf_counter() - t0
+        oracle.assemble(p.xyz, pts[sel], wj[sel], p.E[sel], p.nu[sel], p.alpha_s, p.alpha_c, p.q, p.h)
+        return time.perf_counter() - t0, len(pts[sel]), k
 
     m0 = 1024
-    t0 = run(m0)
+    t0, _, _ = run(m0)
     m = int(min(len(pts), max(m0, m0 * budget_s / max(t0, 1e-3))))
-    dt = run(m)
+    dt, m, k = run(m)
+    oracle.set_threads(1)
+    dt1, m1, k1 = run(max(256, m // (2 * cores)))
+    oracle.set_threads(cores)
     return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first %d of %d Gauss points of the workload (%.1f%%), f64 oracle, OpenMP %d threads, %.1f s"
-                      % (m, len(pts), 100.0 * m / len(pts), cores, dt)}
+            "sample": "every %d-th of the %d Gauss points of the workload (%d, %.1f%%), f64 oracle, OpenMP %d "
+                      "threads, %.1f s" % (k, len(pts), m, 100.0 * m / len(pts), cores, dt),
+            "single_thread": {"value": m1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": "every %d-th Gauss point (%d), f64 oracle, 1 thread, %.1f s" % (k1, m1, dt1)}}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -208,8 +222,9 @@ def run_reference(args, rank):
     pts, wj = oracle.gauss_points(p.cell_lo, p.cell_hi)
 
     def step(m):
+        sel, _ = _spread(len(pts), m)
         t0 = time.perf_counter()
-        oracle.assemble(p.xyz, pts[:m], wj[:m], p.E[:m], p.nu[:m], p.alpha_s, p.alpha_c, p.q, p.h)
+        oracle.assemble(p.xyz, pts[sel], wj[sel], p.E[sel], p.nu[sel], p.alpha_s, p.alpha_c, p.q, p.h)
         return time.perf_counter() - t0
 
     # size each step to about 4 s of host work
@@ -220,7 +235,8 @@ def run_reference(args, rank):
     times = [step(m) for _ in range(args.steps)]
     ms = 1e3 * sum(times) / len(times)
     value = m / (ms / 1e3)
-    sample = "first %d of %d Gauss points of the workload per step, f64 oracle, OpenMP %d threads" % (m, len(pts), cores)
+    sample = ("%d of the %d Gauss points of the workload per step, spread evenly (every %d-th), f64 oracle, "
+              "OpenMP %d threads" % (len(pts[_spread(len(pts), m)[0]]), len(pts), _spread(len(pts), m)[1], cores))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
