@@ -45,8 +45,14 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t 
 }
 
 // Row kernel. One warp owns row I and accumulates the upper blocks (J >= I)
-// of its row in place in K (L2-resident read-modify-write; every block is
-// touched by one lane at a time, in ascending point order). The warps of a
+// of its row (every block is touched by one lane at a time, in ascending
+// point order). The running sums live in K (L2-resident read-modify-write)
+// or, while a run of consecutive points keeps touching them, in a per-warp
+// shared-memory cache of C blocks: a block enters the cache with its running
+// sum from K and is written back when the cache fills or the row ends.
+// Moving a sum between K and the cache is exact, so every block is the same
+// fused multiply-add sequence as without the cache (bitwise), with fewer
+// L2 round trips between consecutive points. The warps of a
 // wave keep their rows' upper blocks (about 19 KB a row on the cantilever)
 // in L2, so the number of resident warps is a trade: 16 per SM (2 blocks,
 // 100 registers) measured 27 ms on the cantilever; 8 (shared-memory
@@ -65,29 +71,38 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t 
 //   K = kappa V + V^T + tr(V) I.
 // Other rows accumulate K_ab directly (lambda and mu terms, 24 FP64
 // operations per pair).
-__global__ void __launch_bounds__(256) row_kernel(int64_t n_nodes, const int64_t *__restrict__ toff,
-                                                  const int64_t *__restrict__ tent,
-                                                  const int32_t *__restrict__ entry_pt,
-                                                  const int64_t *__restrict__ soff,
-                                                  const int32_t *__restrict__ sidx,
-                                                  const double *__restrict__ phi,
-                                                  const double *__restrict__ lamw,
-                                                  const double *__restrict__ wj,
-                                                  const double *__restrict__ nu,
-                                                  const double *__restrict__ body,
-                                                  const int64_t *__restrict__ rowptr,
-                                                  const int32_t *__restrict__ cols,
-                                                  const int64_t *__restrict__ diag, const InstGrid *__restrict__ ig,
-                                                  const int32_t *__restrict__ node_inst,
-                                                  const int32_t *__restrict__ cell_start,
-                                                  const uint32_t *__restrict__ node_cpk,
-                                                  const int32_t *__restrict__ node_rank, int nbits, double *K,
-                                                  double *__restrict__ f, DevError *err)
+__global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int64_t *__restrict__ toff,
+                                                     const int64_t *__restrict__ tent,
+                                                     const int32_t *__restrict__ entry_pt,
+                                                     const int64_t *__restrict__ soff,
+                                                     const int32_t *__restrict__ sidx,
+                                                     const double *__restrict__ phi,
+                                                     const double *__restrict__ lamw,
+                                                     const double *__restrict__ wj,
+                                                     const double *__restrict__ nu,
+                                                     const double *__restrict__ body,
+                                                     const int64_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ cols,
+                                                     const int64_t *__restrict__ diag, const InstGrid *__restrict__ ig,
+                                                     const int32_t *__restrict__ node_inst,
+                                                     const int32_t *__restrict__ cell_start,
+                                                     const uint32_t *__restrict__ node_cpk,
+                                                     const int32_t *__restrict__ node_rank, int nbits, int max_upper,
+                                                     int C, double *K, double *__restrict__ f, DevError *err)
 {
-    extern __shared__ int16_t slot_tab[];
+    extern __shared__ __align__(16) unsigned char row_smem[];
     __shared__ int run_start[8][25], run_pre[8][26];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    int16_t *tab = slot_tab + (size_t)wi * nbits;
+    // per-warp shared memory: slot table | slot -> cache index | cache index
+    // -> slot | block cache [C][9]
+    const size_t tab_b = ((size_t)nbits * 2 + 15) & ~(size_t)15, map_b = ((size_t)max_upper + 15) & ~(size_t)15,
+                 cs_b = ((size_t)C * 2 + 15) & ~(size_t)15;
+    unsigned char *wbase = row_smem + (size_t)wi * (tab_b + map_b + cs_b + (size_t)C * 72);
+    int16_t *tab = (int16_t *)wbase;
+    int8_t *lmap = (int8_t *)(wbase + tab_b);
+    int16_t *cslot = (int16_t *)(wbase + tab_b + map_b);
+    double *cache = (double *)(wbase + tab_b + map_b + cs_b);
+    const unsigned lt = (1u << lane) - 1u;
     double b0 = 0.0, b1 = 0.0, b2 = 0.0;
     if (body) { b0 = body[0]; b1 = body[1]; b2 = body[2]; }
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -100,11 +115,12 @@ __global__ void __launch_bounds__(256) row_kernel(int64_t n_nodes, const int64_t
         const uint32_t ci = node_cpk[I];
         const int cx = (int)(ci & 0x7FF), cy = (int)((ci >> 11) & 0x7FF), cz = (int)(ci >> 22);
         const int total = cell_runs(ig[node_inst[I]], cell_start, cx, cy, cz, lane, run_start[wi], run_pre[wi]);
-        if (total > nbits) {
+        if (total > nbits || U > max_upper) {
             if (lane == 0) dev_fail(err, RPIM_E_ARG, I);
             continue;
         }
         for (int i = lane; i < total; i += 32) tab[i] = -1;
+        for (int i = lane; i < U; i += 32) lmap[i] = -1;
         __syncwarp();
         for (int s = lane; s < U; s += 32) {
             const int bi = run_bit(node_cpk, node_rank, ucols[s], cx, cy, cz, run_start[wi], run_pre[wi]);
@@ -118,6 +134,21 @@ __global__ void __launch_bounds__(256) row_kernel(int64_t n_nodes, const int64_t
         for (int64_t t = t0 + lane; t < t1; t += 32) uni &= nu[entry_pt[tent[t]]] == nu0;
         uni = __all_sync(0xffffffffu, uni);
         __syncwarp();
+        int nloc = 0;   // cached blocks (warp-uniform)
+        // writes the cached blocks back to K (every block keeps its running
+        // sum whether it lives in the cache or in K)
+        auto flush = [&]() {
+            for (int li = lane; li < nloc; li += 32) {
+                const int s = cslot[li];
+                const double *c = cache + 9 * li;
+                double *o = Ku + 9 * s;
+#pragma unroll
+                for (int i = 0; i < 9; i++) o[i] = c[i];
+                lmap[s] = -1;
+            }
+            nloc = 0;
+            __syncwarp();
+        };
         double f0 = 0.0, f1 = 0.0, f2 = 0.0;
         for (int64_t tb = t0; tb < t1; tb += 32) {
             // prefetch: lane l loads the scalars of point tb + l
@@ -140,49 +171,82 @@ __global__ void __launch_bounds__(256) row_kernel(int64_t n_nodes, const int64_t
                 const int64_t end = __shfl_sync(0xffffffffu, pend, k);
                 const double M0 = __shfl_sync(0xffffffffu, pM0, k), M1 = __shfl_sync(0xffffffffu, pM1, k),
                              M2 = __shfl_sync(0xffffffffu, pM2, k);
-                const double w = __shfl_sync(0xffffffffu, pw, k);
-                f0 = fma(w, b0, f0);
-                f1 = fma(w, b1, f1);
-                f2 = fma(w, b2, f2);
-                if (uni) {
-                    for (int64_t q = e + lane; q < end; q += 32) {
-                        const int bi = run_bit(node_cpk, node_rank, sidx[q], cx, cy, cz, run_start[wi], run_pre[wi]);
-                        const int slot = bi >= 0 && bi < total ? tab[bi] : -1;
-                        if (slot < 0) { dev_fail(err, RPIM_E_ARG, I); continue; }
-                        const double2 qa = *(const double2 *)(phi + 4 * q);
-                        const double2 qb = *(const double2 *)(phi + 4 * q + 2);
-                        const double d0 = qa.y, d1 = qb.x, d2 = qb.y;
-                        double *o = Ku + 9 * slot;
-                        o[0] = fma(M0, d0, o[0]); o[1] = fma(M0, d1, o[1]); o[2] = fma(M0, d2, o[2]);
-                        o[3] = fma(M1, d0, o[3]); o[4] = fma(M1, d1, o[4]); o[5] = fma(M1, d2, o[5]);
-                        o[6] = fma(M2, d0, o[6]); o[7] = fma(M2, d1, o[7]); o[8] = fma(M2, d2, o[8]);
-                    }
-                } else {
-                    const double A0 = __shfl_sync(0xffffffffu, pA0, k), A1 = __shfl_sync(0xffffffffu, pA1, k),
-                                 A2 = __shfl_sync(0xffffffffu, pA2, k);
-                    for (int64_t q = e + lane; q < end; q += 32) {
-                        const int bi = run_bit(node_cpk, node_rank, sidx[q], cx, cy, cz, run_start[wi], run_pre[wi]);
-                        const int slot = bi >= 0 && bi < total ? tab[bi] : -1;
-                        if (slot < 0) { dev_fail(err, RPIM_E_ARG, I); continue; }
-                        const double2 qa = *(const double2 *)(phi + 4 * q);
-                        const double2 qb = *(const double2 *)(phi + 4 * q + 2);
-                        const double d0 = qa.y, d1 = qb.x, d2 = qb.y;
-                        const double md = fma(M2, d2, fma(M1, d1, M0 * d0));
-                        double *o = Ku + 9 * slot;
-                        o[0] = fma(M0, d0, fma(A0, d0, o[0] + md));
-                        o[1] = fma(M1, d0, fma(A0, d1, o[1]));
-                        o[2] = fma(M2, d0, fma(A0, d2, o[2]));
-                        o[3] = fma(M0, d1, fma(A1, d0, o[3]));
-                        o[4] = fma(M1, d1, fma(A1, d1, o[4] + md));
-                        o[5] = fma(M2, d1, fma(A1, d2, o[5]));
-                        o[6] = fma(M0, d2, fma(A2, d0, o[6]));
-                        o[7] = fma(M1, d2, fma(A2, d1, o[7]));
-                        o[8] = fma(M2, d2, fma(A2, d2, o[8] + md));
-                    }
+                double A0 = 0.0, A1 = 0.0, A2 = 0.0;
+                if (!uni) {
+                    A0 = __shfl_sync(0xffffffffu, pA0, k);
+                    A1 = __shfl_sync(0xffffffffu, pA1, k);
+                    A2 = __shfl_sync(0xffffffffu, pA2, k);
                 }
-                __syncwarp();
+                const double w = __shfl_sync(0xffffffffu, pw, k);
+                if (body) {
+                    f0 = fma(w, b0, f0);
+                    f1 = fma(w, b1, f1);
+                    f2 = fma(w, b2, f2);
+                }
+                for (int64_t qb = e; qb < end; qb += 32) {
+                    const int64_t q = qb + lane;
+                    int slot = -1;
+                    double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+                    if (q < end) {
+                        const int bi = run_bit(node_cpk, node_rank, sidx[q], cx, cy, cz, run_start[wi], run_pre[wi]);
+                        slot = bi >= 0 && bi < total ? tab[bi] : -1;
+                        if (slot < 0) dev_fail(err, RPIM_E_ARG, I);
+                        const double2 qa = *(const double2 *)(phi + 4 * q);
+                        const double2 qb2 = *(const double2 *)(phi + 4 * q + 2);
+                        d0 = qa.y; d1 = qb2.x; d2 = qb2.y;
+                    }
+                    // the block's place: in the cache (li >= 0), or to be
+                    // brought in; blocks stay in K when the cache is full
+                    int li = slot >= 0 ? (int)lmap[slot] : -1;
+                    unsigned need = __ballot_sync(0xffffffffu, slot >= 0 && li < 0);
+                    if (need && nloc + __popc(need) > C) {
+                        flush();
+                        li = slot >= 0 ? (int)lmap[slot] : -1;
+                        need = __ballot_sync(0xffffffffu, slot >= 0 && li < 0);
+                    }
+                    bool fresh = false;
+                    if (slot >= 0 && li < 0) {
+                        const int n = nloc + __popc(need & lt);
+                        if (n < C) {
+                            li = n;
+                            lmap[slot] = (int8_t)n;
+                            cslot[n] = (int16_t)slot;
+                            fresh = true;
+                        }
+                    }
+                    nloc = min(C, nloc + __popc(need));
+                    if (slot >= 0) {
+                        // running sum of the block: from K when it enters the
+                        // cache or stays out of it, else from the cache
+                        const double *src = (li >= 0 && !fresh) ? cache + 9 * li : Ku + 9 * slot;
+                        double o[9];
+#pragma unroll
+                        for (int i = 0; i < 9; i++) o[i] = src[i];
+                        if (uni) {
+                            o[0] = fma(M0, d0, o[0]); o[1] = fma(M0, d1, o[1]); o[2] = fma(M0, d2, o[2]);
+                            o[3] = fma(M1, d0, o[3]); o[4] = fma(M1, d1, o[4]); o[5] = fma(M1, d2, o[5]);
+                            o[6] = fma(M2, d0, o[6]); o[7] = fma(M2, d1, o[7]); o[8] = fma(M2, d2, o[8]);
+                        } else {
+                            const double md = fma(M2, d2, fma(M1, d1, M0 * d0));
+                            o[0] = fma(M0, d0, fma(A0, d0, o[0] + md));
+                            o[1] = fma(M1, d0, fma(A0, d1, o[1]));
+                            o[2] = fma(M2, d0, fma(A0, d2, o[2]));
+                            o[3] = fma(M0, d1, fma(A1, d0, o[3]));
+                            o[4] = fma(M1, d1, fma(A1, d1, o[4] + md));
+                            o[5] = fma(M2, d1, fma(A1, d2, o[5]));
+                            o[6] = fma(M0, d2, fma(A2, d0, o[6]));
+                            o[7] = fma(M1, d2, fma(A2, d1, o[7]));
+                            o[8] = fma(M2, d2, fma(A2, d2, o[8] + md));
+                        }
+                        double *dst = li >= 0 ? cache + 9 * li : Ku + 9 * slot;
+#pragma unroll
+                        for (int i = 0; i < 9; i++) dst[i] = o[i];
+                    }
+                    __syncwarp();   // cache map and entries visible to the next round's lanes
+                }
             }
         }
+        flush();
         // finish the upper blocks
         const double kappa = 2.0 * nu0 / (1.0 - 2.0 * nu0);
         for (int s = lane; s < U; s += 32) {
@@ -394,15 +458,24 @@ static rpim_status assemble_issue(rpim_pattern *p, const double *E, const double
 {
     launch("lame", lame_kernel, grid_size(p->sm_count, 4, p->n_points, 256), 256, 0, s, p->n_points, E, nu, p->wj, p->lamw, p->err);
     RPIM_CHECK(shape_functions_all(p, p->phi, s));
-    // per warp: the slot table (int16 per bitmap position)
+    // per warp: the slot table (int16 per bitmap position), the block cache's
+    // map (int8 per upper block of the row) and the cache of C blocks; C is
+    // the largest of 64, 32, 0 that keeps two blocks of 8 warps per SM
     const int nbits = 32 * p->bit_words;
-    const size_t smem = (size_t)8 * nbits * sizeof(int16_t);
+    const int max_upper = std::max(1, p->max_row);
+    auto per_warp = [&](int c) {
+        return (((size_t)nbits * 2 + 15) & ~(size_t)15) + (((size_t)max_upper + 15) & ~(size_t)15) +
+               (((size_t)c * 2 + 15) & ~(size_t)15) + (size_t)c * 72;
+    };
+    int C = 64;
+    while (C > 0 && 8 * per_warp(C) > 108 * 1024) C -= 32;
+    const size_t smem = 8 * per_warp(C);
     if (nbits > 32767 || smem > 216 * 1024) return fail(RPIM_E_SUPPORT, "row slot table too large (too many nodes per cell)");
     RPIM_CUDA(cudaFuncSetAttribute(row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     launch("row", row_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, smem, s, p->n_nodes, p->toff,
            p->tent, p->entry_pt, p->soff, p->sidx, p->phi, p->lamw, p->wj, nu, body, p->rowptr, p->cols, p->diag,
            (const InstGrid *)p->ig, (const int32_t *)p->node_inst, (const int32_t *)p->cell_start,
-           (const uint32_t *)p->node_cpk, (const int32_t *)p->node_rank, nbits, K, f, p->err);
+           (const uint32_t *)p->node_cpk, (const int32_t *)p->node_rank, nbits, max_upper, C, K, f, p->err);
     RPIM_CUDA(cudaGetLastError());
     launch("mirror", mirror_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, 0, s, p->n_nodes, p->rowptr, p->cols, K);
     RPIM_CUDA(cudaGetLastError());
