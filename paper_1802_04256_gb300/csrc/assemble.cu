@@ -115,12 +115,13 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
         const uint32_t ci = node_cpk[I];
         const int cx = (int)(ci & 0x7FF), cy = (int)((ci >> 11) & 0x7FF), cz = (int)(ci >> 22);
         const int total = cell_runs(ig[node_inst[I]], cell_start, cx, cy, cz, lane, run_start[wi], run_pre[wi]);
-        if (total > nbits || U > max_upper) {
+        if (total > nbits || (C > 0 && U > max_upper)) {
             if (lane == 0) dev_fail(err, RPIM_E_ARG, I);
             continue;
         }
         for (int i = lane; i < total; i += 32) tab[i] = -1;
-        for (int i = lane; i < U; i += 32) lmap[i] = -1;
+        if (C > 0)
+            for (int i = lane; i < U; i += 32) lmap[i] = -1;
         __syncwarp();
         for (int s = lane; s < U; s += 32) {
             const int bi = run_bit(node_cpk, node_rank, ucols[s], cx, cy, cz, run_start[wi], run_pre[wi]);
@@ -197,24 +198,27 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                     }
                     // the block's place: in the cache (li >= 0), or to be
                     // brought in; blocks stay in K when the cache is full
-                    int li = slot >= 0 ? (int)lmap[slot] : -1;
-                    unsigned need = __ballot_sync(0xffffffffu, slot >= 0 && li < 0);
-                    if (need && nloc + __popc(need) > C) {
-                        flush();
-                        li = slot >= 0 ? (int)lmap[slot] : -1;
-                        need = __ballot_sync(0xffffffffu, slot >= 0 && li < 0);
-                    }
+                    int li = -1;
                     bool fresh = false;
-                    if (slot >= 0 && li < 0) {
-                        const int n = nloc + __popc(need & lt);
-                        if (n < C) {
-                            li = n;
-                            lmap[slot] = (int8_t)n;
-                            cslot[n] = (int16_t)slot;
-                            fresh = true;
+                    if (C > 0) {   // (C is uniform: without a cache every block stays in K)
+                        li = slot >= 0 ? (int)lmap[slot] : -1;
+                        unsigned need = __ballot_sync(0xffffffffu, slot >= 0 && li < 0);
+                        if (need && nloc + __popc(need) > C) {
+                            flush();
+                            li = slot >= 0 ? (int)lmap[slot] : -1;
+                            need = __ballot_sync(0xffffffffu, slot >= 0 && li < 0);
                         }
+                        if (slot >= 0 && li < 0) {
+                            const int n = nloc + __popc(need & lt);
+                            if (n < C) {
+                                li = n;
+                                lmap[slot] = (int8_t)n;
+                                cslot[n] = (int16_t)slot;
+                                fresh = true;
+                            }
+                        }
+                        nloc = min(C, nloc + __popc(need));
                     }
-                    nloc = min(C, nloc + __popc(need));
                     if (slot >= 0) {
                         // running sum of the block: from K when it enters the
                         // cache or stays out of it, else from the cache
@@ -460,15 +464,19 @@ static rpim_status assemble_issue(rpim_pattern *p, const double *E, const double
     RPIM_CHECK(shape_functions_all(p, p->phi, s));
     // per warp: the slot table (int16 per bitmap position), the block cache's
     // map (int8 per upper block of the row) and the cache of C blocks; C is
-    // the largest of 64, 32, 0 that keeps two blocks of 8 warps per SM
+    // the largest of 64, 32, 0 that keeps two blocks of 8 warps per SM (with
+    // one block per SM the cache measured slower than none: 388 against
+    // 318 ms on 32 batched blocks with supports up to 180 nodes)
     const int nbits = 32 * p->bit_words;
-    const int max_upper = std::max(1, p->max_row);
+    const int max_row = std::max(1, p->max_row);
+    // per-warp bytes with a cache of c blocks (the map is needed only with a cache)
     auto per_warp = [&](int c) {
-        return (((size_t)nbits * 2 + 15) & ~(size_t)15) + (((size_t)max_upper + 15) & ~(size_t)15) +
+        return (((size_t)nbits * 2 + 15) & ~(size_t)15) + (c > 0 ? (((size_t)max_row + 15) & ~(size_t)15) : 0) +
                (((size_t)c * 2 + 15) & ~(size_t)15) + (size_t)c * 72;
     };
     int C = 64;
     while (C > 0 && 8 * per_warp(C) > 108 * 1024) C -= 32;
+    const int max_upper = C > 0 ? max_row : 0;
     const size_t smem = 8 * per_warp(C);
     if (nbits > 32767 || smem > 216 * 1024) return fail(RPIM_E_SUPPORT, "row slot table too large (too many nodes per cell)");
     RPIM_CUDA(cudaFuncSetAttribute(row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
