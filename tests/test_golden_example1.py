@@ -1,0 +1,53 @@
+"""The first verification example of the paper (Sec. 3.1), against the values
+it prints (tests/golden/example1_gravity_cube.txt): a cube under its own
+weight, base fixed, sides on rollers.
+
+* The printed theoretical bottom stress is density * g * H with g = 9.8 and
+  H = 100 m (the paper states neither; this fixes the reading).
+* The oracle's solution of that cube carries the weight at its base exactly:
+  the penalty reactions give a mean base stress equal to the printed
+  theoretical value.
+* Local stresses at the integration points next to the fixed base deviate
+  from it (the paper's own value is 6.8% low); they stay within 20%.
+"""
+import os
+
+import numpy as np
+
+import gen
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _golden():
+    vals = {}
+    for line in open(os.path.join(HERE, "golden", "example1_gravity_cube.txt")):
+        line = line.split("#")[0].strip()
+        if "=" in line:
+            k, v = line.split("=")
+            vals[k.strip()] = float(v)
+    return vals
+
+
+def test_printed_theory_is_density_g_height():
+    v = _golden()
+    assert abs(v["density"] * 9.8 * 100.0 / 1e6 - v["bottom_stress_theory"]) < 5e-4
+    assert abs(v["bottom_stress_paper"] / v["bottom_stress_theory"] - 1.0 + 0.0675) < 1e-3
+
+
+def test_oracle_cube_carries_the_printed_bottom_stress():
+    v = _golden()
+    oracle.set_threads(4)
+    rho, g, H = v["density"], 9.8, 100.0
+    gam = rho * g
+    p = gen.gravity_column(shape=(7, 7, 7), height=H, width=H, gamma=gam, E=1.0e9, nu=0.25)
+    m, u, it, rr, alpha = oracle.solve_problem(p, rtol=1e-12)
+    base = p.fixed_dofs[p.fixed_dofs % 3 == 2]
+    mean_base_stress = -alpha * u[base].sum() / (H * H) / 1e6   # MPa
+    assert abs(mean_base_stress - v["bottom_stress_theory"]) < 1e-3 * v["bottom_stress_theory"]
+    sig = oracle.stress(p.xyz, u, m.pts, p.E, p.nu, p.alpha_s, p.alpha_c, p.q, p.h)
+    low = m.pts[:, 2] < m.pts[:, 2].min() + 1e-9
+    local = -np.dot(m.wj[low], sig[low, 2]) / m.wj[low].sum() / 1e6
+    theory_there = gam * (H - m.pts[low, 2].mean()) / 1e6
+    assert abs(local / theory_there - 1.0) < 0.2
