@@ -10,8 +10,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = "".join(open(os.path.join(ROOT, "include", h)).read()
-                  for h in sorted(os.listdir(os.path.join(ROOT, "include"))) if h.endswith(".h"))
+    src = ""
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            with open(os.path.join(ROOT, "include", h)) as fh:
+                src += fh.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(rpim_\w+)\s*\(", src)))
 

@@ -22,11 +22,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 def _golden():
     vals = {}
-    for line in open(os.path.join(HERE, "golden", "example1_gravity_cube.txt")):
-        line = line.split("#")[0].strip()
-        if "=" in line:
-            k, v = line.split("=")
-            vals[k.strip()] = float(v)
+    with open(os.path.join(HERE, "golden", "example1_gravity_cube.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if "=" in line:
+                k, v = line.split("=")
+                vals[k.strip()] = float(v)
     return vals
 
 

@@ -165,11 +165,13 @@ MUTANTS = {
 def mutant(request, tmp_path_factory):
     name = request.param
     a, b = MUTANTS[name]
-    src = open(oracle.SRC).read()
+    with open(oracle.SRC) as fh:
+        src = fh.read()
     assert src.count(a) == 1, name
     d = tmp_path_factory.mktemp(name)
     c = os.path.join(d, "m.c")
-    open(c, "w").write(src.replace(a, b))
+    with open(c, "w") as fh:
+        fh.write(src.replace(a, b))
     so = os.path.join(d, "m.so")
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", c, "-o", so, "-lm"],
                    check=True)
