@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "Problem", "splitmix64", "uniform", "normal", "lattice_problem", "cube_config",
     "cantilever_config", "gravity_column", "slope_config", "batched_configs",
-    "backanalysis_config", "config",
+    "backanalysis_config", "config", "concat_faces",
 ]
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -65,8 +65,14 @@ class Problem:
     Volume integration points are numbered ``8*i + l`` (``l = a + 2b + 4c`` for the
     2x2x2 rule of cell ``i``); ``E`` and ``nu`` are given per integration point in
     that numbering. ``fixed_dofs`` (DOF ``3*node + axis``) are held at
-    ``fixed_vals`` by the penalty method; ``load_xyz``/``load_force`` are surface
-    loads lumped at the face quadrature points (force = traction x weight).
+    ``fixed_vals`` by the penalty method. Surface tractions act on the
+    rectangles ``[face_lo[k], face_hi[k]]`` (planar: ``face_lo == face_hi``
+    along the normal axis ``face_axis[k]``); component ``c`` of the traction
+    on face ``k`` is the polynomial
+    ``sum_j face_coef[k, c, j] * m_j(u, v)``, ``m = (1, u, v, u^2, u v, v^2)``,
+    in the global coordinates ``u < v`` of the face's two tangent axes (in
+    ascending axis order). How a face is integrated is left to the library
+    and to the oracle.
     """
     name: str
     xyz: np.ndarray
@@ -81,8 +87,10 @@ class Problem:
     body: np.ndarray = field(default_factory=lambda: np.zeros(3))
     fixed_dofs: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     fixed_vals: np.ndarray = field(default_factory=lambda: np.zeros(0))
-    load_xyz: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
-    load_force: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    face_lo: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    face_hi: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    face_axis: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int8))
+    face_coef: np.ndarray = field(default_factory=lambda: np.zeros((0, 3, 6)))
     extent: tuple = (1.0, 1.0, 1.0)
     shape: tuple = (0, 0, 0)
     nominal: np.ndarray | None = None
@@ -95,6 +103,10 @@ class Problem:
     @property
     def n_points(self) -> int:
         return 8 * self.n_nodes
+
+    @property
+    def n_faces(self) -> int:
+        return int(self.face_lo.shape[0])
 
     @property
     def volume(self) -> float:
@@ -132,36 +144,28 @@ def lattice_problem(name, shape, extent, jitter=0.0, seed=0, keep=None):
     return ijk, nom, xyz, lo, hi, spacing
 
 
-def _face_loads(nom, spacing, extent, ijk, shape, axis, side, traction_fn):
-    """2x2 Gauss points on the face cells of the nodes on one box face.
-
-    ``traction_fn(points) -> (m, 3)`` gives the traction at each face point;
-    the returned force is traction times the Gauss weight (product of the
-    half-extents of the face rectangle, unit Gauss weights).
-    """
+def _faces(nom, spacing, extent, ijk, shape, axis, side, coef):
+    """The face rectangles of the node cells on one box face: the cell of each
+    node on the face, clipped to the domain, flattened onto the face plane.
+    ``coef`` (3 x 6) is the traction polynomial of every one of them (see
+    :class:`Problem`)."""
     n_ax = shape[axis]
     on = ijk[:, axis] == (n_ax - 1 if side else 0)
-    if not np.any(on):
-        return np.zeros((0, 3)), np.zeros((0, 3))
     c = nom[on]
-    ta = [a for a in range(3) if a != axis]
     lo = np.maximum(c - 0.5 * spacing, 0.0)
     hi = np.minimum(c + 0.5 * spacing, np.array(extent))
-    mid = 0.5 * (lo + hi)
-    half = 0.5 * (hi - lo)
-    g = 1.0 / np.sqrt(3.0)
-    pts, wts = [], []
-    for sa in (-g, g):
-        for sb in (-g, g):
-            p = mid.copy()
-            p[:, axis] = extent[axis] if side else 0.0
-            p[:, ta[0]] = mid[:, ta[0]] + half[:, ta[0]] * sa
-            p[:, ta[1]] = mid[:, ta[1]] + half[:, ta[1]] * sb
-            pts.append(p)
-            wts.append(half[:, ta[0]] * half[:, ta[1]])
-    pts = np.concatenate(pts)
-    wts = np.concatenate(wts)
-    return pts, traction_fn(pts) * wts[:, None]
+    lo[:, axis] = hi[:, axis] = extent[axis] if side else 0.0
+    m = len(c)
+    return (lo, hi, np.full(m, axis, np.int8),
+            np.broadcast_to(np.asarray(coef, np.float64), (m, 3, 6)).copy())
+
+
+def _pressure(p):
+    """Traction polynomial of a uniform pressure p on a top face (inward
+    normal: -z)."""
+    c = np.zeros((3, 6))
+    c[2, 0] = -p
+    return c
 
 
 def _fix_face(ijk, shape, axis, side, comps=(0, 1, 2)):
@@ -186,10 +190,9 @@ def cube_config(n=6, seed=0, jitter=0.0, pressure=10.0, E=1.0e4, nu=0.3):
     ijk, nom, xyz, lo, hi, sp = lattice_problem("cube", shape, ext, jitter, seed)
     Ev, nuv = _material(len(xyz), E, nu)
     fixed = _fix_face(ijk, shape, 2, 0)
-    lx, lf = _face_loads(nom, sp, ext, ijk, shape, 2, 1,
-                         lambda p: np.tile([0.0, 0.0, -pressure], (len(p), 1)))
+    fl, fh, fa, fc = _faces(nom, sp, ext, ijk, shape, 2, 1, _pressure(pressure))
     return Problem("cube%d" % n, xyz, lo, hi, 2.5, 4.0, 1.03, float(sp.max()), Ev, nuv,
-                   np.zeros(3), fixed, np.zeros(len(fixed)), lx, lf, ext, shape, nom,
+                   np.zeros(3), fixed, np.zeros(len(fixed)), fl, fh, fa, fc, ext, shape, nom,
                    {"pressure": pressure, "E": E, "nu": nu})
 
 
@@ -205,15 +208,14 @@ def cantilever_config(shape=(129, 17, 17), length=8.0, seed=1, jitter=0.2, P=1.0
     ijk, nom, xyz, lo, hi, sp = lattice_problem("cantilever", shape, ext, jitter, seed)
     Ev, nuv = _material(len(xyz), E, nu)
     fixed = _fix_face(ijk, shape, 0, 0)
-
-    def shear(p):
-        t = np.zeros((len(p), 3))
-        t[:, 2] = -(1.5 * P) * (1.0 - 4.0 * (p[:, 2] - 0.5) ** 2)
-        return t
-
-    lx, lf = _face_loads(nom, sp, ext, ijk, shape, 0, 1, shear)
+    # t_z = -(3P/2)(1 - 4(z - 1/2)^2) = -6P z + 6P z^2 on the face x = L,
+    # whose tangent coordinates are (u, v) = (y, z)
+    shear = np.zeros((3, 6))
+    shear[2, 2] = -6.0 * P
+    shear[2, 5] = 6.0 * P
+    fl, fh, fa, fc = _faces(nom, sp, ext, ijk, shape, 0, 1, shear)
     return Problem("cantilever", xyz, lo, hi, 2.5, 4.0, 1.03, float(sp.max()), Ev, nuv,
-                   np.zeros(3), fixed, np.zeros(len(fixed)), lx, lf, ext, shape, nom,
+                   np.zeros(3), fixed, np.zeros(len(fixed)), fl, fh, fa, fc, ext, shape, nom,
                    {"P": P, "E": E, "nu": nu, "L": length, "D": 1.0})
 
 
@@ -236,8 +238,8 @@ def gravity_column(shape=(5, 5, 9), height=2.0, width=1.0, gamma=20.0, E=1.0e4, 
     fixed = np.unique(fixed)
     return Problem("column", xyz, lo, hi, 2.5, 4.0, 1.03, float(sp.max()), Ev, nuv,
                    np.array([0.0, 0.0, -gamma]), fixed, np.zeros(len(fixed)),
-                   np.zeros((0, 3)), np.zeros((0, 3)), ext, shape, nom,
-                   {"gamma": gamma, "H": height, "E": E, "nu": nu})
+                   extent=ext, shape=shape, nominal=nom,
+                   meta={"gamma": gamma, "H": height, "E": E, "nu": nu})
 
 
 def slope_config(n=100, seed=2, jitter=0.2, gamma=20.0):
@@ -265,7 +267,7 @@ def slope_config(n=100, seed=2, jitter=0.2, gamma=20.0):
     ]))
     return Problem("slope", xyz, lo, hi, 3.0, 4.0, 1.03, float(sp.max()), Ev, nuv,
                    np.array([0.0, 0.0, -gamma]), fixed, np.zeros(len(fixed)),
-                   np.zeros((0, 3)), np.zeros((0, 3)), ext, shape, nom, {"gamma": gamma})
+                   extent=ext, shape=shape, nominal=nom, meta={"gamma": gamma})
 
 
 def batched_configs(count=512, seed=3, lo_nodes=500, hi_nodes=20000):
@@ -291,10 +293,9 @@ def batched_configs(count=512, seed=3, lo_nodes=500, hi_nodes=20000):
         Ev, nuv = _material(len(xyz), Es[k], nus[k])
         fixed = _fix_face(ijk, shape, 2, 0)
         p = prs[k]
-        lx, lf = _face_loads(nom, sp, ext, ijk, shape, 2, 1,
-                             lambda q_, p=p: np.tile([0.0, 0.0, -p], (len(q_), 1)))
+        fl, fh, fa, fc = _faces(nom, sp, ext, ijk, shape, 2, 1, _pressure(p))
         out.append(Problem("block%d" % k, xyz, lo, hi, float(als[k]), 4.0, 1.03, float(sp.max()),
-                           Ev, nuv, np.zeros(3), fixed, np.zeros(len(fixed)), lx, lf, ext, shape,
+                           Ev, nuv, np.zeros(3), fixed, np.zeros(len(fixed)), fl, fh, fa, fc, ext, shape,
                            nom, {"E": Es[k], "nu": nus[k], "pressure": p}))
     return out
 
@@ -347,12 +348,11 @@ def backanalysis_config(shape=(64, 32, 32), seed=4, hidden_seed=1004, n_obs=500)
     Ev, nuv = fields(seed)
     Eh, nuh = fields(hidden_seed)
     fixed = _fix_face(ijk, shape, 2, 0)
-    lx, lf = _face_loads(nom, sp, ext, ijk, shape, 2, 1,
-                         lambda p: np.tile([0.0, 0.0, -10.0], (len(p), 1)))
+    fl, fh, fa, fc = _faces(nom, sp, ext, ijk, shape, 2, 1, _pressure(10.0))
     obs = np.sort((splitmix64(seed, 42, n_obs) % np.uint64(len(xyz))).astype(np.int64))
     obs = np.unique(obs)
     return Problem("backanalysis", xyz, lo, hi, 2.5, 4.0, 1.03, float(sp.max()), Ev, nuv,
-                   np.zeros(3), fixed, np.zeros(len(fixed)), lx, lf, ext, shape, nom,
+                   np.zeros(3), fixed, np.zeros(len(fixed)), fl, fh, fa, fc, ext, shape, nom,
                    {"E_hidden": Eh, "nu_hidden": nuh, "obs_nodes": obs})
 
 
@@ -361,3 +361,11 @@ def config(i: int, **kw):
     2 layered slope, 3 batched blocks, 4 back-analysis block)."""
     return [cube_config, cantilever_config, slope_config, batched_configs,
             backanalysis_config][i](**kw)
+
+
+def concat_faces(problems):
+    """Faces of several problems concatenated (lo, hi, axis, coef, instance
+    of every face), for a batched pattern of those problems in that order."""
+    cat = lambda name: np.concatenate([getattr(p, name) for p in problems])
+    inst = np.concatenate([np.full(p.n_faces, k, np.int32) for k, p in enumerate(problems)])
+    return cat("face_lo"), cat("face_hi"), cat("face_axis").astype(np.int8), cat("face_coef"), inst

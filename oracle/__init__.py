@@ -71,7 +71,7 @@ def lib(kind: str = "f64"):
     L.orc_shape_shepard.restype = i32
     L.orc_set_shape.argtypes = [i32]
     L.orc_get_shape.restype = i32
-    L.orc_assemble.argtypes = [i64, _D, i64, _D, _D, _D, _D, vp, dbl, dbl, dbl, dbl, i32]
+    L.orc_assemble.argtypes = [i64, _D, i64, _D, _D, _D, _D, vp, dbl, dbl, dbl, dbl, i32, vp]
     L.orc_assemble.restype = vp
     L.orc_free.argtypes = [vp]
     for fn in ("orc_status",):
@@ -84,9 +84,12 @@ def lib(kind: str = "f64"):
     L.orc_copy_support.argtypes = [vp, _I64, _I32]
     L.orc_point_loads.argtypes = [i64, _D, i64, _D, _D, dbl, dbl, dbl, dbl, i32, _D]
     L.orc_point_loads.restype = i32
+    L.orc_traction.argtypes = [i64, _D, i64, _D, _D, _P(dtype=np.int8, flags="C_CONTIGUOUS"), _D, dbl, dbl,
+                               dbl, dbl, i32, _D]
+    L.orc_traction.restype = i32
     L.orc_penalty.argtypes = [i64, _I64, _I32, _D, _D, i64, _I64, _D, dbl, C.POINTER(dbl)]
     L.orc_penalty.restype = i32
-    L.orc_pcg.argtypes = [i64, _I64, _I32, _D, _D, _D, dbl, i32, C.POINTER(i32), C.POINTER(dbl)]
+    L.orc_pcg.argtypes = [i64, _I64, _I32, _D, _D, _D, dbl, i32, C.POINTER(i32), C.POINTER(dbl), i32]
     L.orc_pcg.restype = i32
     L.orc_stress.argtypes = [i64, _D, _D, i64, _D, _D, _D, dbl, dbl, dbl, dbl, i32, _D]
     L.orc_stress.restype = i32
@@ -215,8 +218,10 @@ def shape_shepard(xyz, supp, x, h, alpha_s, kind="f64"):
     return out.reshape(4, len(s))
 
 def assemble(xyz, pts, wj, E, nu, alpha_s, alpha_c, q, h, body=None, kind="f64",
-             max_support=MAX_SUPPORT):
-    """Assemble K and f over the given integration points (ascending order)."""
+             max_support=MAX_SUPPORT, rows=None):
+    """Assemble K and f over the given integration points (ascending order);
+    with `rows` (node ids), only those rows of K and entries of f are formed
+    (the others are zero)."""
     L = lib(kind)
     xyz = _c(xyz)
     pts = _c(pts)
@@ -224,8 +229,13 @@ def assemble(xyz, pts, wj, E, nu, alpha_s, alpha_c, q, h, body=None, kind="f64",
     if body is not None:
         bb = _c(body)
         bodyp = bb.ctypes.data_as(C.c_void_p)
+    maskp = None
+    if rows is not None:
+        mask = np.zeros(xyz.shape[0], np.uint8)
+        mask[np.asarray(rows, np.int64)] = 1
+        maskp = mask.ctypes.data_as(C.c_void_p)
     h_ = L.orc_assemble(xyz.shape[0], xyz, pts.shape[0], pts, _c(wj), _c(E), _c(nu), bodyp,
-                        alpha_s, alpha_c, q, h, max_support)
+                        alpha_s, alpha_c, q, h, max_support, maskp)
     if not h_:
         raise OracleError(3, "allocation")
     try:
@@ -249,14 +259,26 @@ def assemble(xyz, pts, wj, E, nu, alpha_s, alpha_c, q, h, body=None, kind="f64",
 
 
 def assemble_problem(p, kind="f64", with_loads=True):
-    """Gauss points, K, f (body force + surface loads) for a gen.Problem."""
+    """Gauss points, K, f (body force + surface tractions) for a gen.Problem."""
     pts, wj = gauss_points(p.cell_lo, p.cell_hi, kind)
     m = assemble(p.xyz, pts, wj, p.E, p.nu, p.alpha_s, p.alpha_c, p.q, p.h,
                  body=p.body if np.any(p.body) else None, kind=kind)
-    if with_loads and len(p.load_xyz):
-        point_loads(p.xyz, p.load_xyz, p.load_force, p.alpha_s, p.alpha_c, p.q, p.h, m.f, kind)
+    if with_loads and p.n_faces:
+        traction(p.xyz, p.face_lo, p.face_hi, p.face_axis, p.face_coef, p.alpha_s, p.alpha_c, p.q, p.h,
+                 m.f, kind)
     m.pts, m.wj = pts, wj
     return m
+
+
+def traction(xyz, face_lo, face_hi, face_axis, face_coef, alpha_s, alpha_c, q, h, f, kind="f64"):
+    """f += the tractions of the faces (2x2 Gauss-Legendre per face rectangle)."""
+    xyz = _c(xyz)
+    assert f.dtype == np.float64 and f.flags.c_contiguous
+    st = lib(kind).orc_traction(xyz.shape[0], xyz, len(face_lo), _c(face_lo), _c(face_hi),
+                                _c(face_axis, np.int8), _c(face_coef), alpha_s, alpha_c, q, h, MAX_SUPPORT, f)
+    if st:
+        raise OracleError(st, "traction")
+    return f
 
 
 def point_loads(xyz, pts, force, alpha_s, alpha_c, q, h, f, kind="f64"):
@@ -279,12 +301,14 @@ def penalty(n_nodes, rowptr, cols, vals, f, dofs, values, scale=1e8, kind="f64")
     return a.value
 
 
-def pcg(n_nodes, rowptr, cols, vals, f, u0=None, rtol=1e-10, max_iter=100000, kind="f64"):
+def pcg(n_nodes, rowptr, cols, vals, f, u0=None, rtol=1e-10, max_iter=100000, kind="f64", precond="jacobi"):
+    """PCG with the Jacobi or the 3x3 block-Jacobi ("block") preconditioner:
+    (u, iterations, relative residual, status)."""
     u = np.zeros(3 * n_nodes) if u0 is None else _c(u0).copy()
     it = C.c_int(0)
     rr = C.c_double(0)
     st = lib(kind).orc_pcg(n_nodes, _c(rowptr, np.int64), _c(cols, np.int32), _c(vals), _c(f), u,
-                           rtol, max_iter, C.byref(it), C.byref(rr))
+                           rtol, max_iter, C.byref(it), C.byref(rr), {"jacobi": 0, "block": 1}[precond])
     return u, it.value, rr.value, st
 
 

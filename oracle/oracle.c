@@ -41,7 +41,8 @@
  *    D(E, nu). Every block (I, J) is formed on its own (no mirroring), and
  *    blocks are summed in ascending point order.
  *  - Body force f_I += phi_I b w|J|; surface loads f_I += phi_I F at given
- *    points.
+ *    points, or tractions integrated over face rectangles (2x2 Gauss-Legendre
+ *    per face).
  *  - Penalty (Sec. 2, second stage): alpha = scale * max_i K_ii,
  *    K_dd += alpha, f_d += alpha * u_d for each constrained DOF d.
  *  - Solve (Sec. 2, third stage): Jacobi-preconditioned conjugate gradients.
@@ -513,7 +514,8 @@ void orc_free(orc_model *m)
 
 orc_model *orc_assemble(int64_t n_nodes, const double *xyz, int64_t n_pts, const double *pts,
                         const double *wj, const double *E, const double *nu, const double *body,
-                        double alpha_s, double alpha_c, double q, double h, int max_support)
+                        double alpha_s, double alpha_c, double q, double h, int max_support,
+                        const uint8_t *row_mask)
 {
     orc_model *m = (orc_model *)calloc(1, sizeof(orc_model));
     if (!m) return NULL;
@@ -586,12 +588,12 @@ orc_model *orc_assemble(int64_t n_nodes, const double *xyz, int64_t n_pts, const
             }
         }
     }
-    free(ioff); free(ipts); free(mark); free(cnt);
+    free(mark); free(cnt);
 
     /* shape functions of every point (independent per point; the paper's CPU
      * scheme runs these in parallel with OpenMP, Sec. 2) */
     real *phis = (real *)malloc((size_t)m->soff[n_pts] * 4 * sizeof(real) + 8);
-    if (!phis) { m->status = ORC_E_OOM; return m; }
+    if (!phis) { free(ioff); free(ipts); m->status = ORC_E_OOM; return m; }
     int64_t bad = -1;
     int bad_status = ORC_OK;
 #pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
@@ -604,17 +606,27 @@ orc_model *orc_assemble(int64_t n_nodes, const double *xyz, int64_t n_pts, const
             { if (bad < 0 || g < bad) { bad = g; bad_status = st; } }
         }
     }
-    if (bad >= 0) { free(phis); m->status = bad_status; m->bad_point = bad; return m; }
+    if (bad >= 0) { free(ioff); free(ipts); free(phis); m->status = bad_status; m->bad_point = bad; return m; }
 
-    /* accumulate w|J| B_I^T D B_J for every ordered pair, ascending point */
-    for (int64_t g = 0; g < n_pts; g++) {
-        const int n = (int)(m->soff[g + 1] - m->soff[g]);
-        const int32_t *s = m->sidx + m->soff[g];
-        const real *ph = phis + 4 * m->soff[g];
-        real D[6][6];
-        elastic_D((real)E[g], (real)nu[g], D);
-        const real w = (real)wj[g];
-        for (int a = 0; a < n; a++) {
+    /* accumulate w|J| B_I^T D B_J for every ordered pair (I, J) of every
+     * point's support, each block over the points in ascending order. Row I
+     * takes its points from the incidence list (ascending) and is formed by
+     * one thread, so rows can be formed in parallel and each block is the
+     * same sum in the same order as a point-by-point sweep. With row_mask,
+     * only the rows I with row_mask[I] != 0 are formed (the others stay 0). */
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
+    for (int64_t I = 0; I < n_nodes; I++) {
+        if (row_mask && !row_mask[I]) continue;
+        for (int64_t t = ioff[I]; t < ioff[I + 1]; t++) {
+            const int64_t g = ipts[t];
+            const int n = (int)(m->soff[g + 1] - m->soff[g]);
+            const int32_t *s = m->sidx + m->soff[g];
+            const real *ph = phis + 4 * m->soff[g];
+            real D[6][6];
+            elastic_D((real)E[g], (real)nu[g], D);
+            const real w = (real)wj[g];
+            int a = 0;
+            while (s[a] != (int32_t)I) a++;   /* I's place in the support of g */
             real ga[3] = {ph[n + a], ph[2 * n + a], ph[3 * n + a]};
             real Ba[6][3];
             strain_B(ga, Ba);
@@ -641,7 +653,7 @@ orc_model *orc_assemble(int64_t n_nodes, const double *xyz, int64_t n_pts, const
                 for (int k = 0; k < 3; k++) m->f[3 * (int64_t)s[a] + k] += ph[a] * (real)body[k] * w;
         }
     }
-    free(phis);
+    free(ioff); free(ipts); free(phis);
     return m;
 }
 
@@ -685,6 +697,65 @@ int orc_point_loads(int64_t n_nodes, const double *xyz, int64_t n, const double 
         if (st != ORC_OK) break;
         for (int64_t a = 0; a < c; a++)
             for (int k = 0; k < 3; k++) acc[3 * (int64_t)s[a] + k] += ph[a] * (real)force[3 * p + k];
+    }
+    if (st == ORC_OK)
+        for (int64_t i = 0; i < 3 * n_nodes; i++) f[i] += (double)acc[i];
+    free(s); free(ph); free(acc);
+    return st;
+}
+
+/* ---------------------------------------------------------------------------
+ * Surface tractions on axis-aligned face rectangles (the pressure and shear
+ * loads of the verification examples, Sec. 3): face k lies in the plane
+ * x_a = lo[a] (a = axis[k]) and spans [lo, hi] along the two other axes
+ * u < v. The traction component c is the polynomial
+ *     t_c(u, v) = C0 + C1 u + C2 v + C3 u^2 + C4 u v + C5 v^2
+ * (coef[18 k + 6 c + j]) in global coordinates. Each face is integrated with
+ * the 2x2 Gauss-Legendre rule: points mid +- half/sqrt(3) along u and v
+ * (point l = a + 2b, bit a for u, b for v, 0 -> minus), weight
+ * half_u * half_v, so f_I += sum over points of phi_I(x_p) t(x_p) w_p,
+ * faces in order, points in order. Exact for tractions of degree <= 3 in
+ * each tangent coordinate times polynomial shape functions.
+ * ------------------------------------------------------------------------- */
+int orc_traction(int64_t n_nodes, const double *xyz, int64_t n_faces, const double *lo,
+                 const double *hi, const int8_t *axis, const double *coef, double alpha_s,
+                 double alpha_c, double q, double h, int max_support, double *f)
+{
+    const double rs2 = orc_support_radius2(alpha_s, h);
+    int32_t *s = (int32_t *)malloc((size_t)max_support * sizeof(int32_t));
+    real *ph = (real *)malloc((size_t)max_support * 4 * sizeof(real));
+    real *acc = (real *)calloc((size_t)n_nodes * 3, sizeof(real));
+    if (!s || !ph || !acc) { free(s); free(ph); free(acc); return ORC_E_OOM; }
+    int st = ORC_OK;
+    for (int64_t k = 0; k < n_faces && st == ORC_OK; k++) {
+        const int a = axis[k];
+        if (a < 0 || a > 2) { st = ORC_E_ARG; break; }
+        const int ua = a == 0 ? 1 : 0, va = a == 2 ? 1 : 2;   /* tangent axes, ascending */
+        const double *l = lo + 3 * k, *u = hi + 3 * k;
+        if (l[a] != u[a] || !(l[ua] <= u[ua]) || !(l[va] <= u[va])) { st = ORC_E_ARG; break; }
+        const double mu = (l[ua] + u[ua]) * 0.5, hu = (u[ua] - l[ua]) * 0.5;
+        const double mv = (l[va] + u[va]) * 0.5, hv = (u[va] - l[va]) * 0.5;
+        const double w = hu * hv;
+        for (int pt = 0; pt < 4 && st == ORC_OK; pt++) {
+            double x[3];
+            x[a] = l[a];
+            x[ua] = mu + hu * ((pt & 1) ? GAUSS2 : -GAUSS2);
+            x[va] = mv + hv * ((pt & 2) ? GAUSS2 : -GAUSS2);
+            const double U = x[ua], V = x[va];
+            const double m[6] = {1.0, U, V, U * U, U * V, V * V};
+            real F[3];
+            for (int c = 0; c < 3; c++) {
+                real t = 0;
+                for (int j = 0; j < 6; j++) t += (real)coef[18 * k + 6 * c + j] * (real)m[j];
+                F[c] = t * (real)w;
+            }
+            int64_t cnt = orc_support(n_nodes, xyz, x, rs2, s, max_support);
+            if (cnt < 4 || cnt > max_support) { st = ORC_E_SUPPORT; break; }
+            st = shape_real(xyz, s, (int)cnt, x, h, alpha_s, alpha_c, q, ph);
+            if (st != ORC_OK) break;
+            for (int64_t i = 0; i < cnt; i++)
+                for (int c = 0; c < 3; c++) acc[3 * (int64_t)s[i] + c] += ph[i] * F[c];
+        }
     }
     if (st == ORC_OK)
         for (int64_t i = 0; i < 3 * n_nodes; i++) f[i] += (double)acc[i];
@@ -746,34 +817,86 @@ static real dot(int64_t n, const real *a, const real *b)
     return s;
 }
 
+/* inverse of a 3x3 matrix by Gauss-Jordan elimination with partial pivoting
+ * (row-major in and out); ORC_E_SINGULAR on a zero pivot */
+static int inverse3(const double *a, real *inv)
+{
+    real m[3][6];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 6; j++) m[i][j] = j < 3 ? (real)a[3 * i + j] : (real)(j - 3 == i);
+    for (int k = 0; k < 3; k++) {
+        int p = k;
+        for (int i = k + 1; i < 3; i++) if (RABS(m[i][k]) > RABS(m[p][k])) p = i;
+        if (m[p][k] == 0) return ORC_E_SINGULAR;
+        for (int j = 0; j < 6; j++) { real t = m[k][j]; m[k][j] = m[p][j]; m[p][j] = t; }
+        const real piv = m[k][k];
+        for (int j = 0; j < 6; j++) m[k][j] /= piv;
+        for (int i = 0; i < 3; i++) {
+            if (i == k) continue;
+            const real l = m[i][k];
+            for (int j = 0; j < 6; j++) m[i][j] -= l * m[k][j];
+        }
+    }
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) inv[3 * i + j] = m[i][3 + j];
+    return ORC_OK;
+}
+
+/* z = M^-1 r: Jacobi (dinv[i] = 1 / K_ii) or block Jacobi (dinv[9I..] the
+ * inverse of node I's 3x3 diagonal block) */
+static void precondition(int block, int64_t n_nodes, const real *dinv, const real *r, real *z)
+{
+    if (!block) {
+        for (int64_t i = 0; i < 3 * n_nodes; i++) z[i] = dinv[i] * r[i];
+        return;
+    }
+    for (int64_t I = 0; I < n_nodes; I++)
+        for (int a = 0; a < 3; a++) {
+            real s = 0;
+            for (int b = 0; b < 3; b++) s += dinv[9 * I + 3 * a + b] * r[3 * I + b];
+            z[3 * I + a] = s;
+        }
+}
+
 /* ---------------------------------------------------------------------------
- * Jacobi-preconditioned conjugate gradients (Sec. 2, third stage; the paper
- * calls a library solver, this is the textbook PCG): stops when
+ * Preconditioned conjugate gradients (Sec. 2, third stage; the paper calls a
+ * library solver, this is the textbook PCG) with the Jacobi (block = 0) or
+ * 3x3 block-Jacobi (block = 1) preconditioner: stops when
  * ||r|| <= rtol ||f|| or after max_iter iterations. u holds the initial guess
  * on entry and the solution on exit.
  * ------------------------------------------------------------------------- */
 int orc_pcg(int64_t n_nodes, const int64_t *rowptr, const int32_t *cols, const double *vals,
-            const double *f, double *u, double rtol, int max_iter, int *iters, double *relres)
+            const double *f, double *u, double rtol, int max_iter, int *iters, double *relres, int block)
 {
     const int64_t n = 3 * n_nodes;
     real *x = (real *)malloc((size_t)n * sizeof(real)), *r = (real *)malloc((size_t)n * sizeof(real));
     real *z = (real *)malloc((size_t)n * sizeof(real)), *p = (real *)malloc((size_t)n * sizeof(real));
-    real *qv = (real *)malloc((size_t)n * sizeof(real)), *dinv = (real *)malloc((size_t)n * sizeof(real));
+    real *qv = (real *)malloc((size_t)n * sizeof(real));
+    real *dinv = (real *)malloc((size_t)(block ? 3 : 1) * n * sizeof(real));
     if (!x || !r || !z || !p || !qv || !dinv) {
         free(x); free(r); free(z); free(p); free(qv); free(dinv);
         return ORC_E_OOM;
     }
     for (int64_t I = 0; I < n_nodes; I++)
         for (int64_t t = rowptr[I]; t < rowptr[I + 1]; t++)
-            if (cols[t] == I)
-                for (int a = 0; a < 3; a++) dinv[3 * I + a] = 1 / (real)vals[9 * t + 4 * a];
+            if (cols[t] == I) {
+                if (block) {
+                    if (inverse3(vals + 9 * t, dinv + 9 * I) != ORC_OK) {
+                        free(x); free(r); free(z); free(p); free(qv); free(dinv);
+                        return ORC_E_SINGULAR;
+                    }
+                } else {
+                    for (int a = 0; a < 3; a++) dinv[3 * I + a] = 1 / (real)vals[9 * t + 4 * a];
+                }
+            }
     for (int64_t i = 0; i < n; i++) x[i] = (real)u[i];
     spmv(n_nodes, rowptr, cols, vals, x, qv);
     real fn = 0;
     for (int64_t i = 0; i < n; i++) { r[i] = (real)f[i] - qv[i]; fn += (real)f[i] * (real)f[i]; }
     fn = RSQRT(fn);
     if (fn == 0) fn = 1;
-    for (int64_t i = 0; i < n; i++) { z[i] = dinv[i] * r[i]; p[i] = z[i]; }
+    precondition(block, n_nodes, dinv, r, z);
+    for (int64_t i = 0; i < n; i++) p[i] = z[i];
     real rz = dot(n, r, z);
     real rn = RSQRT(dot(n, r, r));
     int it = 0;
@@ -781,7 +904,7 @@ int orc_pcg(int64_t n_nodes, const int64_t *rowptr, const int32_t *cols, const d
         spmv(n_nodes, rowptr, cols, vals, p, qv);
         real alpha = rz / dot(n, p, qv);
         for (int64_t i = 0; i < n; i++) { x[i] += alpha * p[i]; r[i] -= alpha * qv[i]; }
-        for (int64_t i = 0; i < n; i++) z[i] = dinv[i] * r[i];
+        precondition(block, n_nodes, dinv, r, z);
         real rz_new = dot(n, r, z);
         real beta = rz_new / rz;
         rz = rz_new;

@@ -14,5 +14,10 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session", autouse=True)
 def _build_oracle():
+    """Builds the oracle and lets it use every host core (its results do not
+    depend on the thread count: every sum keeps its order)."""
     import oracle
     oracle.build()
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    for kind in ("f64", "ld"):
+        oracle.set_threads(n, kind)

@@ -50,6 +50,16 @@ def _check_jitter(p, amp):
     assert np.all(p.xyz[on_face] == p.nominal[on_face])
 
 
+def _check_faces_tile(p, axis, plane, area):
+    """Every face lies in the plane x_axis = plane, and the faces tile an area."""
+    assert np.all(p.face_axis == axis)
+    assert np.all(p.face_lo[:, axis] == plane) and np.all(p.face_hi[:, axis] == plane)
+    ext = p.face_hi - p.face_lo
+    ext[:, axis] = 1.0
+    assert np.all(ext > 0)
+    assert np.prod(ext, axis=1).sum() == pytest.approx(area, rel=1e-12)
+
+
 def test_cube_workload():
     p = gen.cube_config()
     assert p.n_nodes == 216 and p.n_points == 1728
@@ -57,7 +67,10 @@ def test_cube_workload():
     _check_cells_tile(p, 1.0)
     # base fixed in all three directions; the pressure's resultant is 10 x area
     assert len(p.fixed_dofs) == 3 * 36
-    assert p.load_force.sum(0) == pytest.approx([0.0, 0.0, -10.0], abs=1e-12)
+    # the pressure acts on the 36 top-face rectangles, which tile z = 1
+    _check_faces_tile(p, 2, 1.0, 1.0)
+    assert np.all(p.face_coef[:, 2, 0] == -10.0)
+    assert np.count_nonzero(p.face_coef) == p.n_faces
 
 
 def test_cantilever_workload():
@@ -66,12 +79,11 @@ def test_cantilever_workload():
     assert p.h == pytest.approx(1 / 16)
     _check_cells_tile(p, 8.0)
     _check_jitter(p, 0.2)
-    # the parabolic shear sums to the tip load P = 1 along -z, with no moment
-    # about the beam axis
-    F = p.load_force
-    assert F.sum(0) == pytest.approx([0.0, 0.0, -1.0], abs=1e-12)
-    assert np.all(p.load_xyz[:, 0] == 8.0)
-    assert (F[:, 2] * (p.load_xyz[:, 1] - 0.5)).sum() == pytest.approx(0.0, abs=1e-12)
+    # the parabolic shear t_z = -(3P/2)(1 - 4(z - 1/2)^2) = -6Pz + 6Pz^2 on
+    # the end face x = 8, in the face coordinates (u, v) = (y, z)
+    _check_faces_tile(p, 0, 8.0, 1.0)
+    assert np.all(p.face_coef[:, 2, 2] == -6.0) and np.all(p.face_coef[:, 2, 5] == 6.0)
+    assert np.count_nonzero(p.face_coef) == 2 * p.n_faces
     assert len(p.fixed_dofs) == 3 * 17 * 17
 
 
@@ -99,7 +111,8 @@ def test_batched_workload():
     for p in ps[::97]:
         _check_cells_tile(p, float(np.prod(p.extent)))
         _check_jitter(p, 0.2)
-        assert p.load_force.sum(0)[2] == pytest.approx(-p.meta["pressure"] * np.prod(p.extent[:2]), rel=1e-12)
+        _check_faces_tile(p, 2, 1.0, float(np.prod(p.extent[:2])))
+        assert np.all(p.face_coef[:, 2, 0] == -p.meta["pressure"])
 
 
 def test_backanalysis_workload():

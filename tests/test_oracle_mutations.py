@@ -31,6 +31,18 @@ MUTANTS = {
                      "real lam = E * nu / ((1 + nu) * (1 - nu));"),
     "dmu_dnu_sign": ("real dmu = -E / (2 * (1 + nu) * (1 + nu));", "real dmu = E / (2 * (1 + nu) * (1 + nu));"),
     "dlam_dnu_term": ("real dlam = E * (1 + 2 * nu * nu)", "real dlam = E * (1 + nu * nu)"),
+    "traction_full_extent_weight": ("const double w = hu * hv;", "const double w = 4 * hu * hv;"),
+    "traction_tangent_axes_swapped": ("const double U = x[ua], V = x[va];", "const double U = x[va], V = x[ua];"),
+    "traction_gauss_point_off": ("x[va] = mv + hv * ((pt & 2) ? GAUSS2 : -GAUSS2);",
+                                 "x[va] = mv + hv * ((pt & 2) ? 0.5 : -0.5);"),
+    "block_precond_diagonal_only": ("for (int b = 0; b < 3; b++) s += dinv[9 * I + 3 * a + b] * r[3 * I + b];",
+                                    "for (int b = 0; b < 3; b++) s += dinv[9 * I + 4 * a] * r[3 * I + a];"),
+    "block_inverse_wrong_row_op": ("for (int j = 0; j < 6; j++) m[i][j] -= l * m[k][j];",
+                                   "for (int j = 0; j < 3; j++) m[i][j] -= l * m[k][j];"),
+    "stress_voigt_slots_swapped": ("sigma[6 * p + r] = (double)acc;",
+                                   "sigma[6 * p + (r == 3 ? 5 : r == 5 ? 3 : r)] = (double)acc;"),
+    "stress_material_of_first_point": ("elastic_D((real)E[p], (real)nu[p], D);\n        for (int r = 0; r < 6; r++) {",
+                                       "elastic_D((real)E[0], (real)nu[0], D);\n        for (int r = 0; r < 6; r++) {"),
 }
 
 
@@ -64,6 +76,9 @@ def _pins(kind, cube):
     yield "penalty", lambda: _penalty(kind, cube)
     yield "grad", lambda: pins.check_grad_material(kind)
     yield "pcg", lambda: _pcg(kind, cube)
+    yield "stress", lambda: pins.test_stress_of_linear_fields_is_hookes_law(cube, kind)
+    yield "traction", lambda: pins.test_traction_resultant_and_moment_are_the_exact_integrals(cube, kind)
+    yield "block_pcg", lambda: pins.test_block_jacobi_pcg_is_exact_on_a_block_diagonal_matrix(cube, kind)
 
 
 def _quad(kind, cube):

@@ -237,6 +237,35 @@ def test_K_energy_of_linear_fields(cube_model, cube_j):
             assert abs(ua @ K @ ub - want) < 1e-9 * (lam + 2 * mu) * V
 
 
+@pytest.mark.parametrize("kind", KINDS)
+def test_stress_of_linear_fields_is_hookes_law(cube_j, kind):
+    """RPIM reproduces linear fields, so for u = A x the strain at every point
+    is the constant strain eps = (A + A^T)/2 and the stress is Hooke's law in
+    tensor form, sigma = lambda tr(eps) I + 2 mu eps, exactly (up to the
+    rounding of the reproduction). Checked for all six Voigt components
+    (xx, yy, zz, yz, xz, xy) of the six unit strains and of a rigid rotation
+    (zero stress), with E and nu drawn per point so that a stress computed
+    with another point's material, a swapped Voigt slot or a dropped shear
+    term fails."""
+    p = cube_j
+    pts = _points(p)[0][::29]
+    E = gen.uniform(7, 60, len(pts), 5e3, 2e4)
+    nu = gen.uniform(7, 61, len(pts), 0.2, 0.4)
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    W = np.array([[0.0, -0.3, 0.2], [0.3, 0.0, -0.7], [-0.2, 0.7, 0.0]])
+    cases = [A for _, A in _strain_fields(p.xyz)] + [W]
+    voigt = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    for A in cases:
+        u = (p.xyz @ A.T).ravel()
+        sig = oracle.stress(p.xyz, u, pts, E, nu, p.alpha_s, p.alpha_c, p.q, p.h, kind)
+        eps = 0.5 * (A + A.T)
+        want = np.zeros((len(pts), 6))
+        for c, (i, j) in enumerate(voigt):
+            want[:, c] = lam * np.trace(eps) * (i == j) + 2 * mu * eps[i, j]
+        assert np.abs(sig - want).max() <= 1e-12 * (lam + 2 * mu).max()
+
+
 def test_K_positive_diagonal(cube_model):
     K = cube_model.dense()
     assert np.all(np.diag(K) > 0)
@@ -263,14 +292,81 @@ def test_body_force_moments():
 
 
 def test_point_loads_force_and_moment(cube_j):
+    """f_I = sum_p phi_I(x_p) F_p: the nodal forces carry the applied
+    resultant (partition of unity) and moment (linear reproduction)."""
     p = cube_j
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0.05, 0.95, size=(30, 3))
+    F = rng.standard_normal((30, 3))
     f = np.zeros(3 * p.n_nodes)
-    oracle.point_loads(p.xyz, p.load_xyz, p.load_force, p.alpha_s, p.alpha_c, p.q, p.h, f)
-    F = f.reshape(-1, 3)
-    assert np.abs(F.sum(0) - p.load_force.sum(0)).max() < 1e-10
-    M = np.cross(p.xyz, F).sum(0)
-    Mp = np.cross(p.load_xyz, p.load_force).sum(0)
-    assert np.abs(M - Mp).max() < 1e-10
+    oracle.point_loads(p.xyz, x, F, p.alpha_s, p.alpha_c, p.q, p.h, f)
+    Fn = f.reshape(-1, 3)
+    assert np.abs(Fn.sum(0) - F.sum(0)).max() < 1e-10
+    assert np.abs(np.cross(p.xyz, Fn).sum(0) - np.cross(x, F).sum(0)).max() < 1e-10
+
+
+def _traction_faces():
+    """Faces normal to each axis, on the boundary of the unit cube, with
+    seeded quadratic traction polynomials (every coefficient set)."""
+    lo, hi, ax = [], [], []
+    for a, side in ((0, 1.0), (1, 0.0), (2, 1.0), (0, 0.0)):
+        for r in ((0.0, 0.6, 0.2, 0.9), (0.4, 1.0, 0.0, 0.5)):
+            l, h = np.zeros(3), np.zeros(3)
+            l[a] = h[a] = side
+            u, v = [b for b in range(3) if b != a]
+            l[u], h[u], l[v], h[v] = r
+            lo.append(l)
+            hi.append(h)
+            ax.append(a)
+    coef = gen.uniform(3, 77, 8 * 18, -4.0, 4.0).reshape(8, 3, 6)
+    return np.array(lo), np.array(hi), np.array(ax, np.int8), coef
+
+
+def _exact_face_loads(lo, hi, ax, coef):
+    """Resultant and moment about the origin of polynomial tractions over
+    face rectangles, from the closed-form integrals of monomials."""
+    R = np.zeros(3)
+    M = np.zeros(3)
+    for l, h, a, c in zip(lo, hi, ax, coef):
+        u, v = [b for b in range(3) if b != a]
+        I = lambda k, b: (h[b] ** (k + 1) - l[b] ** (k + 1)) / (k + 1)
+
+        def integral(du, dv):   # of u^du v^dv times each traction monomial
+            e = [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2)]
+            return np.array([I(du + i, u) * I(dv + j, v) for i, j in e])
+
+        R += c @ integral(0, 0)
+        # x = (plane, u, v) components; moment = integral of x cross t
+        xint = {a: l[a] * integral(0, 0), u: integral(1, 0), v: integral(0, 1)}
+        for i in range(3):
+            j, k = (i + 1) % 3, (i + 2) % 3
+            M[i] += c[k] @ xint[j] - c[j] @ xint[k]
+    return R, M
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_traction_resultant_and_moment_are_the_exact_integrals(cube_j, kind):
+    """The 2x2 Gauss rule integrates the (quadratic) traction times 1 and
+    times a coordinate exactly, and RPIM reproduces constants and linear
+    fields, so the nodal forces carry exactly the resultant and the moment of
+    the traction over the faces: pins the face points, weights, the tangent
+    axes and the polynomial of the oracle's face quadrature."""
+    p = cube_j
+    lo, hi, ax, coef = _traction_faces()
+    f = np.zeros(3 * p.n_nodes)
+    oracle.traction(p.xyz, lo, hi, ax, coef, p.alpha_s, p.alpha_c, p.q, p.h, f, kind)
+    Fn = f.reshape(-1, 3)
+    R, M = _exact_face_loads(lo, hi, ax, coef)
+    assert np.abs(Fn.sum(0) - R).max() < 1e-10 * np.abs(R).max()
+    assert np.abs(np.cross(p.xyz, Fn).sum(0) - M).max() < 1e-10 * np.abs(M).max()
+
+
+def test_cantilever_shear_sums_to_the_tip_load():
+    """The problem's parabolic end shear integrates to -P along z."""
+    p = gen.cantilever_config(shape=(17, 5, 5))
+    f = np.zeros(3 * p.n_nodes)
+    oracle.traction(p.xyz, p.face_lo, p.face_hi, p.face_axis, p.face_coef, p.alpha_s, p.alpha_c, p.q, p.h, f)
+    assert np.abs(f.reshape(-1, 3).sum(0) - [0.0, 0.0, -1.0]).max() < 1e-12
 
 
 # ---------------------------------------------------------------- penalty and solve
@@ -299,6 +395,40 @@ def test_pcg_matches_dense_solve(cube_j):
     oracle.penalty(cube_j.n_nodes, m.rowptr, m.cols, vals, f, cube_j.fixed_dofs,
                    cube_j.fixed_vals, 1e8)
     u, it, rr, st = oracle.pcg(cube_j.n_nodes, m.rowptr, m.cols, vals, f, rtol=1e-13)
+    assert st == 0 and rr <= 1e-13
+    K = oracle.Model(m.n_nodes, m.rowptr, m.cols, vals.reshape(-1, 9), f, None, None).dense()
+    ud = np.linalg.solve(K, f)
+    assert np.linalg.norm(u - ud) / np.linalg.norm(ud) < 1e-8
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_block_jacobi_pcg_is_exact_on_a_block_diagonal_matrix(cube_j, kind):
+    """With K reduced to its 3x3 diagonal blocks, the block-Jacobi
+    preconditioner is K^-1 itself: PCG converges in one iteration, to the
+    block-by-block solution (while scalar Jacobi needs more)."""
+    m = oracle.assemble_problem(cube_j)
+    vals = m.vals.ravel().copy()
+    f = m.f.copy()
+    oracle.penalty(cube_j.n_nodes, m.rowptr, m.cols, vals, f, cube_j.fixed_dofs, cube_j.fixed_vals, 1e8)
+    rows = np.repeat(np.arange(cube_j.n_nodes), np.diff(m.rowptr))
+    diag = np.nonzero(m.cols == rows)[0]
+    rowptr = np.arange(cube_j.n_nodes + 1, dtype=np.int64)
+    cols = np.arange(cube_j.n_nodes, dtype=np.int32)
+    bd = vals.reshape(-1, 9)[diag].ravel().copy()
+    u, it, rr, st = oracle.pcg(cube_j.n_nodes, rowptr, cols, bd, f, rtol=1e-12, kind=kind, precond="block")
+    assert st == 0 and it == 1
+    want = np.concatenate([np.linalg.solve(b.reshape(3, 3), f[3 * I:3 * I + 3]) for I, b in enumerate(bd.reshape(-1, 9))])
+    assert np.linalg.norm(u - want) <= 1e-12 * np.linalg.norm(want)
+    u2, it2, rr2, st2 = oracle.pcg(cube_j.n_nodes, rowptr, cols, bd, f, rtol=1e-12, kind=kind)
+    assert st2 == 0 and it2 > 1
+
+
+def test_block_jacobi_pcg_matches_dense_solve(cube_j):
+    m = oracle.assemble_problem(cube_j)
+    vals = m.vals.ravel().copy()
+    f = m.f.copy()
+    oracle.penalty(cube_j.n_nodes, m.rowptr, m.cols, vals, f, cube_j.fixed_dofs, cube_j.fixed_vals, 1e8)
+    u, it, rr, st = oracle.pcg(cube_j.n_nodes, m.rowptr, m.cols, vals, f, rtol=1e-13, precond="block")
     assert st == 0 and rr <= 1e-13
     K = oracle.Model(m.n_nodes, m.rowptr, m.cols, vals.reshape(-1, 9), f, None, None).dense()
     ud = np.linalg.solve(K, f)
@@ -382,7 +512,7 @@ def test_adjoint_gradient_matches_finite_differences_of_the_loss():
     E = gen.uniform(17, 1, p.n_points, 5e3, 2e4)
     nu = gen.uniform(17, 2, p.n_points, 0.2, 0.4)
     f_ext = np.zeros(3 * p.n_nodes)
-    oracle.point_loads(p.xyz, p.load_xyz, p.load_force, p.alpha_s, p.alpha_c, p.q, p.h, f_ext)
+    oracle.traction(p.xyz, p.face_lo, p.face_hi, p.face_axis, p.face_coef, p.alpha_s, p.alpha_c, p.q, p.h, f_ext)
     alpha = 1e8 * 4e3
     K, u = _dense_solve(p, pts, wj, E, nu, f_ext, alpha)
     u_obs = u * (1 + 0.1 * np.sin(np.arange(len(u))))
