@@ -1,15 +1,24 @@
 """Benchmark of the RPIM global stiffness assembly on GB300.
 
-Workload: the 129 x 17 x 17 cantilever (37,281 field nodes, 298,248 Gauss
-points, support radius 2.5h, multiquadric alpha_c = 4, q = 1.03), FP64,
+Headline workload: the layered slope at scale, 100 x 100 x 100 lattice in the
+unit cube clipped to a 45-degree face (590,500 field nodes, 4,724,000 Gauss
+points), interior jitter 0.2h, support radius 3.0h, multiquadric alpha_c = 4,
+q = 1.03, three horizontal layers of E and nu, gravity body force, FP64,
 seeded synthetic node cloud. One step is the whole assembly path of Sec. 2's
 first stage on device-resident inputs: rpim_build_pattern (Gauss points,
 cell list, supports, node incidence, BSR pattern) + rpim_assemble (shape
-functions, B^T D B, deterministic reduction) + rpim_add_point_loads. The
-penalty stage and the PCG solve are timed once after the timed steps and
-reported under "solve" (full solves/s). "batched" compares one batched
-pattern + assembly + batched PCG over blocks of the 512-block workload with
-the same blocks run one by one through the plain entry points.
+functions, B^T D B, deterministic reduction, body force) (+ rpim_add_traction
+on workloads with surface loads). The penalty stage and the PCG solve of the
+same system are timed separately afterwards ("solve": iterations and full
+solves/s, Jacobi and 3x3 block-Jacobi preconditioners).
+
+Extra keys: "configs" times the other workloads (the 6x6x6 cube, the
+129x17x17 cantilever, the 64x32x32 back-analysis block) the same way, each
+with its roofline fraction, solves/s and the oracle on the host cores;
+"batched" compares one batched pattern + assembly + batched PCG over blocks
+of the 512-block workload with the same blocks run one by one through the
+plain entry points; "backanalysis" times one material gradient; "mls" the
+cantilever step with MLS shape functions.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -38,8 +47,19 @@ import gen
 
 METRIC = "RPIM assembly Gauss-pts/s, % of FP64/HBM roofline; batched vs per-instance"
 UNIT = "Gauss-pts/s"
-WORKLOAD = ("cantilever 129x17x17 (37,281 nodes, 298,248 Gauss points), interior jitter 0.2h, "
-            "alpha_s 2.5, MQ alpha_c 4.0 q 1.03, E 1e4 nu 0.3, FP64")
+
+WORKLOADS = {
+    "slope": ("layered slope 100x100x100 clipped at 45 degrees (590,500 nodes, 4,724,000 Gauss points), "
+              "interior jitter 0.2h, alpha_s 3.0, MQ alpha_c 4.0 q 1.03, E 8e4/2e4/5e3 nu 0.25/0.30/0.35 "
+              "by layer, gravity 20, FP64", gen.slope_config),
+    "cantilever": ("cantilever 129x17x17 (37,281 nodes, 298,248 Gauss points), interior jitter 0.2h, "
+                   "alpha_s 2.5, MQ alpha_c 4.0 q 1.03, E 1e4 nu 0.3, parabolic end shear, FP64",
+                   gen.cantilever_config),
+    "cube": ("cube 6x6x6 (216 nodes, 1,728 Gauss points), alpha_s 2.5, MQ alpha_c 4.0 q 1.03, E 1e4 nu 0.3, "
+             "pressure 10 on top, FP64", gen.cube_config),
+    "backanalysis": ("back-analysis block 64x32x32 (65,536 nodes, 524,288 Gauss points), jitter 0.2h, "
+                     "alpha_s 2.5, log-normal E field, pressure 10 on top, FP64", gen.backanalysis_config),
+}
 
 
 def _hbm_peak():
@@ -52,6 +72,7 @@ def _hbm_peak():
 
 
 HBM_PEAK, HBM_SRC = _hbm_peak()
+SMS, DFMA_PER_CLK = 152, 2   # SMs of a GB300; FP64 FMA per clock per SM
 
 
 def _cores():
@@ -136,17 +157,17 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- traffic record
-def _traffic_for(kernel, source):
-    """DRAM bytes of `kernel` per step (all its launches in one step) from the
-    committed ncu summary, if the kernel's source is unchanged since the
-    counters were taken."""
+def _traffic_for(kernel, source, workload):
+    """DRAM bytes of `kernel` per step (all its launches in one step) of
+    `workload` from the committed ncu summary, if the kernel's source is
+    unchanged since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     sha = hashlib.sha256(open(source, "rb").read()).hexdigest()[:16]
     for line in open(path):
         kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
-        if kv.get("kernel") == kernel and kv.get("source_sha256") == sha:
+        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("source_sha256") == sha:
             try:
                 return float(kv["dram_bytes_per_step"])
             except (KeyError, ValueError):
@@ -180,7 +201,7 @@ def _spread(n, m):
     return slice(0, k * min(m, n), k), k
 
 
-def cpu_baseline(p, budget_s=15.0):
+def cpu_baseline(p, budget_s=15.0, single_s=None):
     """The oracle (FP64, OpenMP over points on all host cores) on M Gauss
     points spread evenly over the workload, M sized to about `budget_s`
     seconds; and the same oracle on one thread on a smaller spread sample."""
@@ -196,15 +217,17 @@ def cpu_baseline(p, budget_s=15.0):
         oracle.assemble(p.xyz, pts[sel], wj[sel], p.E[sel], p.nu[sel], p.alpha_s, p.alpha_c, p.q, p.h)
         return time.perf_counter() - t0, len(pts[sel]), k
 
-    m0 = 1024
+    m0 = 256
     t0, _, _ = run(m0)
     m = int(min(len(pts), max(m0, m0 * budget_s / max(t0, 1e-3))))
     dt, m, k = run(m)
     oracle.set_threads(1)
-    dt1, m1, k1 = run(max(256, m // (2 * cores)))
+    single_s = budget_s / 3 if single_s is None else single_s
+    m1 = int(min(len(pts), max(64, m * single_s / dt / cores)))
+    dt1, m1, k1 = run(m1)
     oracle.set_threads(cores)
     return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "every %d-th of the %d Gauss points of the workload (%d, %.1f%%), f64 oracle, OpenMP %d "
+            "sample": "every %d-th of the %d Gauss points of the workload (%d, %.2f%%), f64 oracle, OpenMP %d "
                       "threads, %.1f s" % (k, len(pts), m, 100.0 * m / len(pts), cores, dt),
             "single_thread": {"value": m1 / dt1, "unit": UNIT, "cores": 1,
                               "sample": "every %d-th Gauss point (%d), f64 oracle, 1 thread, %.1f s" % (k1, m1, dt1)}}
@@ -212,9 +235,12 @@ def cpu_baseline(p, budget_s=15.0):
 
 # --------------------------------------------------------------------------- reference arm
 def run_reference(args, rank):
+    """The oracle as it stands, on the host cores, on a bounded sample of the
+    headline workload per step (about 4 s of host work)."""
     if rank != 0:
         return
-    p = gen.cantilever_config()
+    desc, make = WORKLOADS[args.workload]
+    p = make()
     import oracle
     oracle.build()
     cores = _cores()
@@ -227,54 +253,138 @@ def run_reference(args, rank):
         oracle.assemble(p.xyz, pts[sel], wj[sel], p.E[sel], p.nu[sel], p.alpha_s, p.alpha_c, p.q, p.h)
         return time.perf_counter() - t0
 
-    # size each step to about 4 s of host work
-    t = step(1024)
-    m = int(min(len(pts), max(1024, 1024 * 4.0 / max(t, 1e-3))))
+    t = step(256)
+    m = int(min(len(pts), max(256, 256 * 4.0 / max(t, 1e-3))))
     for _ in range(args.warmup):
         step(m)
     times = [step(m) for _ in range(args.steps)]
     ms = 1e3 * sum(times) / len(times)
     value = m / (ms / 1e3)
+    sel, k = _spread(len(pts), m)
     sample = ("%d of the %d Gauss points of the workload per step, spread evenly (every %d-th), f64 oracle, "
-              "OpenMP %d threads" % (len(pts[_spread(len(pts), m)[0]]), len(pts), _spread(len(pts), m)[1], cores))
+              "OpenMP %d threads" % (len(pts[sel]), len(pts), k, cores))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "sample_points": m},
+           "config": {"workload": desc, "sample_points": m},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
-# --------------------------------------------------------------------------- stages 2 and 3
-def _solve(pat, p, E, nu, lxyz, lf, tt, stream, peak_gflops, fixed_iters=0):
-    """Penalty (alpha = 1e8 max diag K) and Jacobi-PCG to 1e-10, timed once
-    with CUDA events; the assembly that feeds it is not timed."""
+# --------------------------------------------------------------------------- device inputs
+class Inputs:
+    """Device tensors of one problem."""
+
+    def __init__(self, p, dev):
+        import torch
+        tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        self.p, self.dev = p, dev
+        self.xyz, self.lo, self.hi = tt(p.xyz), tt(p.cell_lo), tt(p.cell_hi)
+        self.E, self.nu = tt(p.E), tt(p.nu)
+        self.body = tt(p.body) if np.any(p.body) else None
+        self.faces = (tt(p.face_lo), tt(p.face_hi), tt(p.face_axis, torch.int8), tt(p.face_coef)) \
+            if p.n_faces else None
+        self.dofs, self.vals = tt(p.fixed_dofs, torch.int64), tt(p.fixed_vals)
+
+    def pattern(self, shape="rpim"):
+        import paper_1802_04256_gb300 as R
+        p = self.p
+        return R.Pattern(self.xyz, self.lo, self.hi, p.alpha_s, p.alpha_c, p.q, p.h, shape=shape)
+
+    def assemble(self, pat, K=None, f=None):
+        K, f = pat.assemble(self.E, self.nu, self.body, K=K, f=f)
+        if self.faces is not None:
+            pat.add_traction(*self.faces, f)
+        return K, f
+
+    def step(self, shape="rpim"):
+        """One assembly step: pattern + assembly (+ tractions)."""
+        pat = self.pattern(shape)
+        K, f = self.assemble(pat)
+        pat.free()
+        return K, f
+
+
+def _events(n):
     import torch
-    K, f = pat.assemble(E, nu)
-    pat.add_point_loads(lxyz, lf, f)
-    dofs, vals = tt(p.fixed_dofs, torch.int64), tt(p.fixed_vals)
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def _support_sizes(inp):
+    pat = inp.pattern()
+    nsup = np.diff(pat.points()[2].cpu().numpy())
+    nnzb = pat.nnz_blocks
+    pat.free()
+    return nsup, nnzb
+
+
+def _roofline(prof, steps, nsup, peak_gflops, workload):
+    """Roofline of the dominant kernel of an assembly step (largest device
+    time): its algorithmic flops per step over its device time per step."""
+    kinds = {"shape": (shape_flops(nsup).sum(), "shape.cu"), "row": (pair_flops(nsup).sum(), "assemble.cu")}
+    top = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    if top not in kinds:
+        return None
+    flops, src = kinds[top]
+    nl, tot = prof[top]
+    step_ms = tot / steps
+    ach = flops / (step_ms / 1e3) / 1e12
+    peak = peak_gflops / 1e3
+    return {"bound": "alu", "kernel": top, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": _traffic_for(top, os.path.join(ROOT, "paper_1802_04256_gb300", "csrc", src), workload),
+            "peak_source": "FP64 DFMA throughput measured in this run (rpim_probe_dfma)",
+            "algorithmic_flops_per_step": flops, "launches_per_step": nl / steps, "kernel_ms_per_step": step_ms,
+            "avg_launch_ms": tot / nl}
+
+
+def _time_steps(inp, steps, stream, shape="rpim"):
+    """Device time per assembly step (CUDA events on the launching stream)
+    and per-kernel device times (the library's own events)."""
+    import torch
+    import paper_1802_04256_gb300 as R
     torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    R.rpim_profile_read(reset=True)
+    R.rpim_profile_enable(True)
+    l0 = R.rpim_kernel_launches()
+    e0, e1 = _events(2)
+    e0.record(stream)
+    for _ in range(steps):
+        inp.step(shape)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    R.rpim_profile_enable(False)
+    prof = R.rpim_profile_read(reset=True)
+    return e0.elapsed_time(e1) / steps, prof, (R.rpim_kernel_launches() - l0) / steps
+
+
+# --------------------------------------------------------------------------- stages 2 and 3
+def _solve(inp, stream, peak_gflops, precond="jacobi", fixed_iters=0, tip=None, rtol=1e-10, max_iter=200000):
+    """Penalty (alpha = 1e8 max diag K) and PCG to rtol, timed once with CUDA
+    events (the assembly that feeds it is not timed); per-kernel times of the
+    iteration from 256 more iterations with event timing."""
+    import torch
+    import paper_1802_04256_gb300 as R
+    pat = inp.pattern()
+    K, f = inp.assemble(pat)
+    torch.cuda.synchronize()
+    s0, s1 = _events(2)
     s0.record(stream)
-    alpha = pat.apply_penalty(K, f, dofs, vals)
+    alpha = pat.apply_penalty(K, f, inp.dofs, inp.vals)
     if fixed_iters > 0:   # a fixed number of iterations (profiling runs)
-        u, iters, relres = pat.solve_pcg(K, f, rtol=0.0, max_iter=fixed_iters, check=False)
+        u, iters, relres = pat.solve_pcg(K, f, rtol=0.0, max_iter=fixed_iters, check=False, precond=precond)
     else:
-        u, iters, relres = pat.solve_pcg(K, f, rtol=1e-10, max_iter=200000)
+        u, iters, relres = pat.solve_pcg(K, f, rtol=rtol, max_iter=max_iter, precond=precond)
     s1.record(stream)
     torch.cuda.synchronize()
     solve_ms = s0.elapsed_time(s1)
-    tip = int(np.nonzero(np.all(np.abs(p.nominal - [8.0, 0.5, 0.5]) < 1e-9, axis=1))[0][0])
-    nnzb = pat.nnz_blocks
-    # per-kernel times of the iteration: 256 more iterations with event timing
-    import paper_1802_04256_gb300 as R
+    nnzb, n_nodes = pat.nnz_blocks, inp.p.n_nodes
     R.rpim_profile_read(reset=True)
     R.rpim_profile_enable(True)
-    pat.solve_pcg(K, f, u.clone(), rtol=0.0, max_iter=256, check=False)
+    pat.solve_pcg(K, f, u.clone(), rtol=0.0, max_iter=256, check=False, precond=precond)
     R.rpim_profile_enable(False)
     prof = R.rpim_profile_read(reset=True)
-    spmv_bytes = nnzb * (72 + 4) + p.n_nodes * (8 + 24 + 24)
+    spmv_bytes = nnzb * (72 + 4) + n_nodes * (8 + 24 + 24)
     roof = None
     if "pcg_spmv" in prof:
         # 9 FMA per 3x3 block: on this chip the FP64 time of a product
@@ -293,60 +403,66 @@ def _solve(pat, p, E, nu, lxyz, lf, tt, stream, peak_gflops, fixed_iters=0):
         roof.update({"kernel": "pcg_spmv", "algorithmic_bytes_per_launch": spmv_bytes,
                      "algorithmic_flops_per_launch": 18 * nnzb, "hbm_GBps": spmv_bytes / t / 1e9,
                      "hbm_frac": spmv_bytes / t / 1e9 / HBM_PEAK, "avg_launch_ms": tot / c})
-    out = {"pcg_iterations": iters, "relres": relres, "ms": solve_ms, "solves_per_s": 1e3 / solve_ms,
-           "ms_per_iteration": solve_ms / max(iters, 1), "penalty_alpha": alpha,
-           "tip_deflection": -u[3 * tip + 2].item(), "timoshenko": 0.20700,
-           "spmv_algorithmic_bytes": spmv_bytes, "spmv_flops": 18 * nnzb, "spmv_roofline": roof,
-           "iteration_kernel_ms": {k: round(v[1] / v[0], 4) for k, v in prof.items()}}
+    out = {"precond": precond, "pcg_iterations": iters, "relres": relres, "rtol": rtol, "ms": solve_ms,
+           "solves_per_s": 1e3 / solve_ms, "ms_per_iteration": solve_ms / max(iters, 1), "penalty_alpha": alpha,
+           "spmv_roofline": roof, "iteration_kernel_ms": {k: round(v[1] / v[0], 4) for k, v in prof.items()}}
+    if tip is not None:
+        out["tip_deflection"] = -u[3 * tip + 2].item()
     del K, f, u
     pat.free()
     return out
 
 
+def _solves(inp, stream, peak_gflops, args, tip=None):
+    """The full solve with each preconditioner."""
+    if args.no_solve:
+        return None
+    return {pc: _solve(inp, stream, peak_gflops, pc, args.solve_iters, tip) for pc in args.precond.split(",")}
+
+
 # --------------------------------------------------------------------------- MLS variant
-def _mls(p, xyz, lo, hi, E, nu, lxyz, lf, stream, peak_gflops, steps=3):
+def _mls(inp, stream, peak_gflops, steps=3):
     """The same assembly step with MLS shape functions (linear basis,
-    cubic-spline weight; the variant Sec. 4 plans): rpim_build_pattern +
-    rpim_pattern_set_shape(MLS) + rpim_assemble + rpim_add_point_loads,
-    device-resident inputs, CUDA events on the launching stream, per-kernel
-    device times from the library's own event timing."""
-    import torch
-    import paper_1802_04256_gb300 as R
-
-    def step():
-        pat = R.Pattern(xyz, lo, hi, p.alpha_s, p.alpha_c, p.q, p.h, shape="mls")
-        K, f = pat.assemble(E, nu)
-        pat.add_point_loads(lxyz, lf, f)
-        pat.free()
-
+    cubic-spline weight; the variant Sec. 4 plans), device-resident inputs."""
     for _ in range(2):
-        step()
-    torch.cuda.synchronize()
-    R.rpim_profile_read(reset=True)
-    R.rpim_profile_enable(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    R.rpim_profile_enable(False)
-    prof = R.rpim_profile_read(reset=True)
-    ms = e0.elapsed_time(e1) / steps
-    pat = R.Pattern(xyz, lo, hi, p.alpha_s, p.alpha_c, p.q, p.h)
-    nsup = np.diff(pat.points()[2].cpu().numpy())
-    pat.free()
+        inp.step("mls")
+    ms, prof, _ = _time_steps(inp, steps, stream, "mls")
+    nsup, _ = _support_sizes(inp)
     roof = None
     if "row" in prof:
         nl, tot = prof["row"]
         ach = pair_flops(nsup).sum() / (tot / steps / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": "row", "achieved": ach, "peak": peak_gflops / 1e3, "unit": "TFLOP/s",
                 "frac": ach * 1e3 / peak_gflops, "peak_source": "FP64 DFMA throughput measured in this run"}
-    return {"step": "rpim_build_pattern + rpim_pattern_set_shape(MLS) + rpim_assemble + rpim_add_point_loads",
-            "workload": WORKLOAD.replace("MQ alpha_c 4.0 q 1.03", "MLS linear basis, cubic-spline weight"),
-            "steps": steps, "ms_per_step": ms, "pts_per_s": p.n_points / (ms / 1e3),
+    return {"step": "rpim_build_pattern + rpim_pattern_set_shape(MLS) + rpim_assemble + rpim_add_traction",
+            "workload": WORKLOADS["cantilever"][0].replace("MQ alpha_c 4.0 q 1.03",
+                                                          "MLS linear basis, cubic-spline weight"),
+            "steps": steps, "ms_per_step": ms, "pts_per_s": inp.p.n_points / (ms / 1e3),
             "kernel_ms_per_step": {k: round(v[1] / steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
             "roofline_row_kernel": roof}
+
+
+# --------------------------------------------------------------------------- other workloads
+def _config(name, dev, stream, peak_gflops, args, steps, warm, cpu_s, tip=None):
+    """One workload: assembly pts/s with its roofline, full solves/s, and the
+    oracle on the host cores (all cores and one thread)."""
+    desc, make = WORKLOADS[name]
+    p = make()
+    inp = Inputs(p, dev)
+    for _ in range(warm):
+        inp.step()
+    ms, prof, launches = _time_steps(inp, steps, stream)
+    nsup, nnzb = _support_sizes(inp)
+    out = {"workload": desc, "n_nodes": p.n_nodes, "n_points": p.n_points, "steps": steps, "ms_per_step": ms,
+           "pts_per_s": p.n_points / (ms / 1e3), "gpu_launches_per_step": launches,
+           "roofline": _roofline(prof, steps, nsup, peak_gflops, name),
+           "support": {"min": int(nsup.min()), "max": int(nsup.max()), "mean": float(nsup.mean())},
+           "nnz_blocks": nnzb,
+           "kernel_ms_per_step": {k: round(v[1] / steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+    out["solve"] = _solves(inp, stream, peak_gflops, args, tip)
+    if not args.no_cpu_baseline and cpu_s > 0:
+        out["cpu_baseline"] = cpu_baseline(p, cpu_s)
+    return out, inp
 
 
 # --------------------------------------------------------------------------- differentiable solve
@@ -359,25 +475,24 @@ def _backanalysis(dev, stream, rtol=1e-10):
     import torch
     import paper_1802_04256_gb300 as R
     p = gen.backanalysis_config()
-    tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
-    pat = R.Pattern.from_problem(p)
+    inp = Inputs(p, dev)
+    pat = inp.pattern()
     f_ext = torch.zeros(3 * p.n_nodes, dtype=torch.float64, device=dev)
-    pat.add_point_loads(tt(p.load_xyz), tt(p.load_force), f_ext)
-    dofs, vals = tt(p.fixed_dofs, torch.int64), tt(p.fixed_vals)
+    pat.add_traction(*inp.faces, f_ext)
+    tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
     obs = tt(p.meta["obs_nodes"], torch.int64)
-    E0, nu0 = tt(p.E), tt(p.nu)
-    alpha = R.penalty_alpha(pat, E0, nu0)
+    alpha = R.penalty_alpha(pat, inp.E, inp.nu)
     with torch.no_grad():   # observations: displacements of the hidden field
-        u_obs = R.solve(pat, tt(p.meta["E_hidden"]), tt(p.meta["nu_hidden"]), f_ext, dofs, vals, alpha,
+        u_obs = R.solve(pat, tt(p.meta["E_hidden"]), tt(p.meta["nu_hidden"]), f_ext, inp.dofs, inp.vals, alpha,
                         rtol=rtol).view(-1, 3)[obs].clone()
 
     def one():
-        E = E0.clone().requires_grad_()
-        nu = nu0.clone().requires_grad_()
-        e0, e1, e2 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        E = inp.E.clone().requires_grad_()
+        nu = inp.nu.clone().requires_grad_()
+        e0, e1, e2 = _events(3)
         torch.cuda.synchronize()
         e0.record(stream)
-        u = R.solve(pat, E, nu, f_ext, dofs, vals, alpha, rtol=rtol)
+        u = R.solve(pat, E, nu, f_ext, inp.dofs, inp.vals, alpha, rtol=rtol)
         loss = 0.5 * ((u.view(-1, 3)[obs] - u_obs) ** 2).sum()
         e1.record(stream)
         loss.backward()
@@ -388,40 +503,31 @@ def _backanalysis(dev, stream, rtol=1e-10):
     one()
     fwd, bwd, gE, gn = one()
     pat.free()
-    return {"workload": "back-analysis block 64x32x32 (65,536 nodes, 524,288 points), log-normal E field, "
-                        "500 observed nodes", "parameters": 2 * p.n_points, "rtol": rtol,
-            "forward_ms": fwd, "backward_ms": bwd, "gradients_per_s": 1e3 / (fwd + bwd),
+    return {"workload": WORKLOADS["backanalysis"][0] + ", 500 observed nodes", "parameters": 2 * p.n_points,
+            "rtol": rtol, "forward_ms": fwd, "backward_ms": bwd, "gradients_per_s": 1e3 / (fwd + bwd),
             "max_abs_dL_dE": gE, "max_abs_dL_dnu": gn,
-            "step": "forward: rpim_assemble + rpim_apply_penalty_alpha + rpim_solve_pcg; "
+            "step": "forward: rpim_assemble + rpim_add_vector + rpim_apply_penalty_alpha + rpim_solve_pcg; "
                     "backward: rpim_solve_pcg (adjoint) + rpim_grad_material"}
 
 
 # --------------------------------------------------------------------------- batched vs per-instance
-def _batched(n_sel, dev, stream, reps=1, warm=1):
+def _batched(n_sel, dev, stream, reps=1, warm=1, small_nodes=2000):
     """Blocks of the 512-instance batched workload (node counts log-uniform in
     500-20,000, alpha_s uniform in [2, 3.5]), every (512 / n_sel)-th one:
-    one batched pattern + assembly + loads + per-instance penalty + batched
-    PCG, against the same instances through the plain entry points one after
-    another. Device-resident inputs; CUDA events on the launching stream."""
+    one batched pattern + assembly + tractions + per-instance penalty +
+    batched PCG, against the same instances through the plain entry points
+    one after another. Device-resident inputs; CUDA events on the launching
+    stream. Also the assembly of every block below `small_nodes` nodes, the
+    regime where per-instance launches under-fill the GPU."""
     import torch
     import paper_1802_04256_gb300 as R
     allp = gen.batched_configs()
     sel = allp[::max(1, len(allp) // n_sel)][:n_sel]
     tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
-    offs = np.concatenate([[0], np.cumsum([p.n_nodes for p in sel])])
-    inst = [(p.n_nodes, p.alpha_s, p.h) for p in sel]
-    cat = lambda name: np.concatenate([getattr(p, name) for p in sel])
-    bx, blo, bhi, bE, bnu = tt(cat("xyz")), tt(cat("cell_lo")), tt(cat("cell_hi")), tt(cat("E")), tt(cat("nu"))
-    blx, blf = tt(cat("load_xyz")), tt(cat("load_force"))
-    bli = tt(np.concatenate([np.full(len(p.load_xyz), k, np.int32) for k, p in enumerate(sel)]), torch.int32)
-    bdofs = tt(np.concatenate([p.fixed_dofs + 3 * offs[k] for k, p in enumerate(sel)]), torch.int64)
-    bvals = tt(cat("fixed_vals"))
-    single = [dict(x=tt(p.xyz), lo=tt(p.cell_lo), hi=tt(p.cell_hi), E=tt(p.E), nu=tt(p.nu), lx=tt(p.load_xyz),
-                   lf=tt(p.load_force), dofs=tt(p.fixed_dofs, torch.int64), vals=tt(p.fixed_vals)) for p in sel]
     rtol = 1e-10
 
     def timed(fn):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(2)
         torch.cuda.synchronize()
         e0.record(stream)
         out = fn()
@@ -429,37 +535,59 @@ def _batched(n_sel, dev, stream, reps=1, warm=1):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), out
 
-    def b_assemble():
-        pat = R.Pattern(bx, blo, bhi, None, sel[0].alpha_c, sel[0].q, None, instances=inst)
-        K, f = pat.assemble(bE, bnu)
-        pat.add_point_loads(blx, blf, f, inst=bli)
-        return pat, K, f
+    class Batch:
+        def __init__(self, probs):
+            self.probs = probs
+            self.offs = np.concatenate([[0], np.cumsum([p.n_nodes for p in probs])])
+            self.inst = [(p.n_nodes, p.alpha_s, p.h) for p in probs]
+            cat = lambda name: np.concatenate([getattr(p, name) for p in probs])
+            self.x, self.lo, self.hi, self.E, self.nu = (tt(cat("xyz")), tt(cat("cell_lo")), tt(cat("cell_hi")),
+                                                         tt(cat("E")), tt(cat("nu")))
+            fl, fh, fa, fc, fi = gen.concat_faces(probs)
+            self.faces = (tt(fl), tt(fh), tt(fa, torch.int8), tt(fc))
+            self.finst = tt(fi, torch.int32)
+            self.dofs = tt(np.concatenate([p.fixed_dofs + 3 * self.offs[k] for k, p in enumerate(probs)]),
+                           torch.int64)
+            self.vals = tt(cat("fixed_vals"))
+            self.npts = int(sum(p.n_points for p in probs))
+
+        def pattern(self):
+            return R.Pattern(self.x, self.lo, self.hi, None, self.probs[0].alpha_c, self.probs[0].q, None,
+                             instances=self.inst)
+
+        def assemble(self):
+            pat = self.pattern()
+            K, f = pat.assemble(self.E, self.nu)
+            pat.add_traction(*self.faces, f, inst=self.finst)
+            return pat, K, f
+
+    bat = Batch(sel)
+    single = [Inputs(p, dev) for p in sel]
 
     def b_solve(pat, K, f):
-        pat.apply_penalty(K, f, bdofs, bvals)
+        pat.apply_penalty(K, f, bat.dofs, bat.vals)
         return pat.solve_pcg_batched(K, f, rtol=rtol, max_iter=500000)
 
-    def s_assemble(p, d):
-        pat = R.Pattern(d["x"], d["lo"], d["hi"], p.alpha_s, p.alpha_c, p.q, p.h)
-        K, f = pat.assemble(d["E"], d["nu"])
-        pat.add_point_loads(d["lx"], d["lf"], f)
-        return pat, K, f
-
     def s_solve(pat, K, f, d):
-        pat.apply_penalty(K, f, d["dofs"], d["vals"])
+        pat.apply_penalty(K, f, d.dofs, d.vals)
         return pat.solve_pcg(K, f, rtol=rtol, max_iter=500000)
 
     def run_batched():
-        ta, (pat, K, f) = timed(b_assemble)
+        ta, (pat, K, f) = timed(bat.assemble)
         ts, (u, its, rrs) = timed(lambda: b_solve(pat, K, f))
         pat.free()
         return ta, ts, u, its
 
+    def s_assemble(d):
+        pat = d.pattern()
+        K, f = d.assemble(pat)
+        return pat, K, f
+
     def run_single():
         ta = ts = 0.0
         us, its = [], []
-        for p, d in zip(sel, single):
-            a, (pat, K, f) = timed(lambda: s_assemble(p, d))
+        for d in single:
+            a, (pat, K, f) = timed(lambda: s_assemble(d))
             s, (u, it, rr) = timed(lambda: s_solve(pat, K, f, d))
             pat.free()
             ta, ts = ta + a, ts + s
@@ -469,7 +597,7 @@ def _batched(n_sel, dev, stream, reps=1, warm=1):
 
     # setup, untimed: tune the bucket bounds and the shape kernel's launch
     # shapes on this batch's support sizes (process-wide: both arms use them)
-    tp = R.Pattern(bx, blo, bhi, None, sel[0].alpha_c, sel[0].q, None, instances=inst)
+    tp = bat.pattern()
     bounds = tp.autotune_buckets(max_points=200000)
     tp.autotune(max_points=20000)
     tp.free()
@@ -486,25 +614,25 @@ def _batched(n_sel, dev, stream, reps=1, warm=1):
     sa, ss = min(r[0] for r in sres), min(r[1] for r in sres)
     ub, itb = bres[-1][2], bres[-1][3]
     us, its = sres[-1][2], sres[-1][3]
+    offs = bat.offs
     du = max(float(torch.linalg.norm(ub[3 * offs[k]:3 * offs[k + 1]] - us[k]) / torch.linalg.norm(us[k]))
              for k in range(len(sel)))
-    npts = int(sum(p.n_points for p in sel))
+    npts = bat.npts
 
     # re-assembly with new material, patterns built beforehand (the repeated
     # assembly of a parameter study or a back-analysis): the batched pattern
     # replays its captured graph (one persistent shape launch over all
     # buckets); the per-instance arm calls rpim_assemble on each instance's
     # own pattern. Only the assembly calls are timed.
-    pat = R.Pattern(bx, blo, bhi, None, sel[0].alpha_c, sel[0].q, None, instances=inst)
-    Kb, fb = pat.assemble_graphed(bE, bnu)
+    pat = bat.pattern()
+    Kb, fb = pat.assemble_graphed(bat.E, bat.nu)
+    pat.assemble_graphed(bat.E, bat.nu, K=Kb, f=fb)
     l0 = R.rpim_kernel_launches()
-    rb = [timed(lambda: pat.assemble_graphed(bE, bnu, K=Kb, f=fb))[0] for _ in range(2)]
+    rb = [timed(lambda: pat.assemble_graphed(bat.E, bat.nu, K=Kb, f=fb))[0] for _ in range(2)]
     lrb = (R.rpim_kernel_launches() - l0) / 2
-    # per-kernel device times of one more assembly (plain launches while
-    # timing is on) and the algorithmic flops of the batch's supports
     R.rpim_profile_read(reset=True)
     R.rpim_profile_enable(True)
-    pat.assemble_graphed(bE, bnu, K=Kb, f=fb)
+    pat.assemble_graphed(bat.E, bat.nu, K=Kb, f=fb)
     R.rpim_profile_enable(False)
     kprof = R.rpim_profile_read(reset=True)
     nsup = np.diff(pat.points()[2].cpu().numpy())
@@ -512,29 +640,16 @@ def _batched(n_sel, dev, stream, reps=1, warm=1):
     pat.free()
     del Kb, fb
     rs, lrs = 0.0, 0
-    for p, d in zip(sel, single):
-        pt = R.Pattern(d["x"], d["lo"], d["hi"], p.alpha_s, p.alpha_c, p.q, p.h)
-        K1, f1 = pt.assemble(d["E"], d["nu"])
+    for d in single:
+        pt = d.pattern()
+        K1, f1 = pt.assemble(d.E, d.nu)
+        pt.assemble(d.E, d.nu, K=K1, f=f1)
         l0 = R.rpim_kernel_launches()
-        rs += min(timed(lambda: pt.assemble(d["E"], d["nu"], K=K1, f=f1))[0] for _ in range(2))
+        rs += min(timed(lambda: pt.assemble(d.E, d.nu, K=K1, f=f1))[0] for _ in range(2))
         lrs += (R.rpim_kernel_launches() - l0) / 2
         pt.free()
         del K1, f1
-    # the same per-instance re-assembly with the unbucketed kernel: one shape
-    # launch per instance sized for that instance's largest support (every
-    # point gets the largest point's shared-memory buffers and launch shape)
-    ru = 0.0
-    R.rpim_set_shape_schedule(False)
-    for p, d in zip(sel, single):
-        pt = R.Pattern(d["x"], d["lo"], d["hi"], p.alpha_s, p.alpha_c, p.q, p.h)
-        R.rpim_pattern_set_buckets(pt.handle, [1 << 29])
-        K1, f1 = pt.assemble(d["E"], d["nu"])
-        ru += min(timed(lambda: pt.assemble(d["E"], d["nu"], K=K1, f=f1))[0] for _ in range(2))
-        pt.free()
-        del K1, f1
-    R.rpim_set_shape_schedule(True)
     reasm = {"batched_graph_ms": min(rb), "per_instance_ms": rs, "speedup": rs / min(rb),
-             "per_instance_unbucketed_ms": ru, "speedup_vs_unbucketed": ru / min(rb),
              "batched_pts_per_s": npts / (min(rb) / 1e3), "per_instance_pts_per_s": npts / (rs / 1e3),
              "kernel_launches": {"batched": lrb, "per_instance": lrs},
              "kernel_ms": {k: round(v[1] / v[0], 3) for k, v in sorted(kprof.items(), key=lambda kv: -kv[1][1])},
@@ -543,20 +658,110 @@ def _batched(n_sel, dev, stream, reps=1, warm=1):
              "shape_tflops": fl_shape / (kprof["shape"][1] / 1e3) / 1e12 if "shape" in kprof else None,
              "support_sizes": {"min": int(nsup.min()), "max": int(nsup.max()), "mean": float(nsup.mean())},
              "step": "rpim_assemble_graphed on the batched pattern vs rpim_assemble per instance "
-                     "(patterns built beforehand, not timed); unbucketed: one support-size bucket and one "
-                     "shape launch per instance"}
+                     "(patterns built beforehand, not timed), both warm"}
+
+    # every block of the 512 below small_nodes: assembly (pattern + assemble +
+    # tractions), batched vs per instance, both warm
+    small = [p for p in allp if p.n_nodes < small_nodes]
+    sbat = Batch(small)
+    ssingle = [Inputs(p, dev) for p in small]
+    tp = sbat.pattern()
+    tp.autotune(max_points=20000)
+    tp.free()
+
+    def small_b():
+        pat, K, f = sbat.assemble()
+        pat.free()
+
+    def small_s():
+        for d in ssingle:
+            d.step()
+
+    small_b(), small_s()
+    l0 = R.rpim_kernel_launches()
+    tb = min(timed(small_b)[0] for _ in range(2))
+    lsb = (R.rpim_kernel_launches() - l0) / 2
+    l0 = R.rpim_kernel_launches()
+    tsg = min(timed(small_s)[0] for _ in range(2))
+    lss = (R.rpim_kernel_launches() - l0) / 2
+    snpts = sbat.npts
+    small_out = {"instances": len(small), "n_nodes": int(sum(p.n_nodes for p in small)), "n_points": snpts,
+                 "batched_ms": tb, "per_instance_ms": tsg, "speedup": tsg / tb,
+                 "batched_pts_per_s": snpts / (tb / 1e3), "per_instance_pts_per_s": snpts / (tsg / 1e3),
+                 "kernel_launches": {"batched": lsb, "per_instance": lss},
+                 "step": "build pattern + assemble + tractions of every block below %d nodes" % small_nodes}
     return {"instances": len(sel), "of": len(allp), "selection": "every %d-th block of the 512-block workload"
             % max(1, len(allp) // n_sel), "n_nodes": int(offs[-1]), "n_points": npts,
             "node_range": [int(min(p.n_nodes for p in sel)), int(max(p.n_nodes for p in sel))],
+            "warmup_runs_each_arm": warm,
             "assembly": {"batched_ms": ba, "per_instance_ms": sa, "speedup": sa / ba,
                          "batched_pts_per_s": npts / (ba / 1e3), "per_instance_pts_per_s": npts / (sa / 1e3)},
             "solve": {"batched_ms": bs, "per_instance_ms": ss, "speedup": ss / bs, "rtol": rtol,
                       "iterations_max": int(max(itb)), "iterations_sum_per_instance": int(sum(its))},
             "end_to_end": {"batched_ms": ba + bs, "per_instance_ms": sa + ss, "speedup": (sa + ss) / (ba + bs)},
             "kernel_launches": {"batched": lb, "per_instance": ls},
-            "reassembly": reasm, "bucket_bounds": bounds,
+            "reassembly": reasm, "small_blocks": small_out, "bucket_bounds": bounds,
             "u_max_rel_diff_batched_vs_per_instance": du,
-            "step": "build pattern + assemble + surface loads (assembly); penalty + Jacobi-PCG to 1e-10 (solve)"}
+            "target_5x": "not met on this workload (FP64-bound blocks fill the GPU alone)",
+            "step": "build pattern + assemble + tractions (assembly); penalty + Jacobi-PCG to 1e-10 (solve)"}
+
+
+# --------------------------------------------------------------------------- end to end
+def _e2e(p, dev, stream, n_steps, dist):
+    """The headline step through host buffers: pinned host inputs copied to
+    the device, the C ABI calls, and K and f copied back into pinned host
+    memory on a second stream (overlapped with the next step's assembly, as
+    a caller streaming problems would run it), all inside the timed region."""
+    import torch
+    import paper_1802_04256_gb300 as R
+    arrays = dict(xyz=p.xyz, lo=p.cell_lo, hi=p.cell_hi, E=p.E, nu=p.nu)
+    if np.any(p.body):
+        arrays["body"] = p.body
+    if p.n_faces:
+        arrays.update(fl=p.face_lo, fh=p.face_hi, fc=p.face_coef)
+    host = {k: torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).pin_memory() for k, v in arrays.items()}
+    if p.n_faces:
+        host["fa"] = torch.from_numpy(np.ascontiguousarray(p.face_axis, dtype=np.int8)).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    Kh = None
+    copy_stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        nonlocal Kh
+        d = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+        pat = R.Pattern(d["xyz"], d["lo"], d["hi"], p.alpha_s, p.alpha_c, p.q, p.h)
+        K, f = pat.assemble(d["E"], d["nu"], d.get("body"))
+        if p.n_faces:
+            pat.add_traction(d["fl"], d["fh"], d["fa"], d["fc"], f)
+        if Kh is None:
+            Kh = (torch.empty(K.shape, dtype=K.dtype, pin_memory=True),
+                  torch.empty(f.shape, dtype=f.dtype, pin_memory=True))
+        done = torch.cuda.Event()
+        done.record(stream)
+        copy_stream.wait_event(done)
+        with torch.cuda.stream(copy_stream):
+            Kh[0].copy_(K, non_blocking=True)
+            Kh[1].copy_(f, non_blocking=True)
+        K.record_stream(copy_stream)
+        f.record_stream(copy_stream)
+        pat.free()
+        return K.numel() * 8 + f.numel() * 8
+
+    step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(n_steps):
+        d2h = step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = 1e3 * (time.perf_counter() - t0) / n_steps
+    del Kh
+    return ms, h2d, d2h
 
 
 # --------------------------------------------------------------------------- our arm
@@ -570,34 +775,26 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     R.lib()
-    p = gen.cantilever_config()
-    tt = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
-    xyz, lo, hi, E, nu = tt(p.xyz), tt(p.cell_lo), tt(p.cell_hi), tt(p.E), tt(p.nu)
-    lxyz, lf = tt(p.load_xyz), tt(p.load_force)
+    desc, make = WORKLOADS[args.workload]
+    p = make()
+    inp = Inputs(p, dev)
     stream = torch.cuda.current_stream()
-
-    def step():
-        pat = R.Pattern(xyz, lo, hi, p.alpha_s, p.alpha_c, p.q, p.h)
-        K, f = pat.assemble(E, nu)
-        pat.add_point_loads(lxyz, lf, f)
-        pat.free()
-        return K, f
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # setup, untimed: launch shapes of the shape kernel picked by the
-    # autotuner on this workload's support-size buckets (results are bitwise
-    # independent of the launch shape)
+    # setup, untimed: bucket bounds and launch shapes of the shape kernel
+    # picked by the autotuners on this workload's support sizes (results are
+    # bitwise independent of both)
     tuned = bounds = None
     if not args.no_autotune:
-        tp = R.Pattern(xyz, lo, hi, p.alpha_s, p.alpha_c, p.q, p.h)
-        bounds = tp.autotune_buckets(max_points=100000)
-        tuned = tp.autotune(max_points=20000)
+        tp = inp.pattern()
+        bounds = tp.autotune_buckets(max_points=60000)
+        tuned = tp.autotune(max_points=args.tune_points)
         tp.free()
     for _ in range(args.warmup):
-        step()
+        inp.step()
     torch.cuda.synchronize()
     # FP64 peak of this GPU, measured warm (best of two best-of-5 runs)
     peak_gflops = max(R.rpim_probe_dfma(5), R.rpim_probe_dfma(5))
@@ -612,10 +809,10 @@ def run_ours(args, rank, world, local_rank):
     launches0 = R.rpim_kernel_launches()
     barrier()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(2)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        inp.step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -626,113 +823,69 @@ def run_ours(args, rank, world, local_rank):
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
     value = whole_job_rate(p.n_points, world, ms)
 
-    # ---- roofline of the dominant kernel (largest device time)
-    pat = R.Pattern(xyz, lo, hi, p.alpha_s, p.alpha_c, p.q, p.h)
-    _, _, soff, _ = pat.points()
-    nsup = np.diff(soff.cpu().numpy())
-    kinds = {"shape": (shape_flops(nsup).sum(), "shape.cu"), "row": (pair_flops(nsup).sum(), "assemble.cu")}
-    top = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
-    roof = None
-    if top in kinds:
-        # the shape kernel runs once per support-size bucket: the algorithmic
-        # flops of one step (all points) over the kernel's device time per step
-        flops, src = kinds[top]
-        nl, tot = prof[top]
-        step_ms = tot / args.steps
-        ach = flops / (step_ms / 1e3) / 1e12
-        peak = peak_gflops / 1e3
-        roof = {"bound": "alu", "kernel": top, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": _traffic_for(top, os.path.join(ROOT, "paper_1802_04256_gb300", "csrc", src)),
-                "peak_source": "FP64 DFMA throughput measured in this run (rpim_probe_dfma)",
-                "algorithmic_flops_per_step": flops, "launches_per_step": nl / args.steps,
-                "kernel_ms_per_step": step_ms, "avg_launch_ms": tot / nl}
+    nsup, nnzb = _support_sizes(inp)
+    roof = _roofline(prof, args.steps, nsup, peak_gflops, args.workload)
+    if roof and clk:
+        roof["peak_nominal_at_clock"] = SMS * DFMA_PER_CLK * 2 * clk["sm_mhz"] * 1e6 / 1e12
     kernel_ms = {k: round(v[1] / args.steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     kernel_share = {k: round(v[1] / max(sum(x[1] for x in prof.values()), 1e-9), 4)
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
-    # ---- stage 2 + 3 once: penalty and PCG (full solve)
-    solve = None
-    nnzb = pat.nnz_blocks
-    if args.no_solve:
-        pat.free()
-    else:
-        solve = _solve(pat, p, E, nu, lxyz, lf, tt, stream, peak_gflops, args.solve_iters)
+    # ---- stages 2 + 3: penalty and PCG (full solves)
+    solve = _solves(inp, stream, peak_gflops, args)
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
-                dict(xyz=p.xyz, lo=p.cell_lo, hi=p.cell_hi, E=p.E, nu=p.nu, lx=p.load_xyz, lf=p.load_force).items()}
-        h2d = sum(v.numel() * v.element_size() for v in host.values())
-        Kh = None
-        # the device->host copy of a step's K and f runs on its own stream,
-        # overlapped with the next step's assembly (pipelined as a caller
-        # would run a stream of problems); record_stream keeps the caching
-        # allocator from reusing K and f before their copy has finished
-        copy_stream = torch.cuda.Stream(device=dev)
-
-        def e2e_step():
-            nonlocal Kh
-            d = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
-            pat = R.Pattern(d["xyz"], d["lo"], d["hi"], p.alpha_s, p.alpha_c, p.q, p.h)
-            K, f = pat.assemble(d["E"], d["nu"])
-            pat.add_point_loads(d["lx"], d["lf"], f)
-            if Kh is None:
-                Kh = (torch.empty(K.shape, dtype=K.dtype, pin_memory=True),
-                      torch.empty(f.shape, dtype=f.dtype, pin_memory=True))
-            done = torch.cuda.Event()
-            done.record(stream)
-            copy_stream.wait_event(done)
-            with torch.cuda.stream(copy_stream):
-                Kh[0].copy_(K, non_blocking=True)
-                Kh[1].copy_(f, non_blocking=True)
-            K.record_stream(copy_stream)
-            f.record_stream(copy_stream)
-            pat.free()
-            return K.numel() * 8 + f.numel() * 8
-
-        e2e_step()
-        torch.cuda.synchronize()
-        n_e2e = max(2, min(args.steps, 5))
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        d2h = 0
-        for _ in range(n_e2e):
-            d2h = e2e_step()
-        torch.cuda.synchronize()
-        barrier()
-        e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / n_e2e, dist, dev)
+        e2e_ms, h2d, d2h = _e2e(p, dev, stream, args.e2e_steps, dist)
+        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
         e2e = {"value": whole_job_rate(p.n_points, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": args.e2e_steps}
+    del inp
 
-    mls = None
-    if not args.no_mls:
-        mls = _mls(p, xyz, lo, hi, E, nu, lxyz, lf, stream, peak_gflops)
+    # ---- the other workloads (rank 0 only: context, not the headline)
+    configs = None
+    if rank == 0 and not args.no_configs:
+        configs = {}
+        cube, _ = _config("cube", dev, stream, peak_gflops, args, steps=10, warm=3, cpu_s=3.0)
+        configs["cube"] = cube
+        tip = int(np.nonzero(np.all(np.abs(gen.cantilever_config().nominal - [8.0, 0.5, 0.5]) < 1e-9,
+                                    axis=1))[0][0])
+        cant, cinp = _config("cantilever", dev, stream, peak_gflops, args, steps=5, warm=2, cpu_s=5.0, tip=tip)
+        if cant.get("solve"):
+            for s in cant["solve"].values():
+                s["timoshenko"] = 0.20700
+        configs["cantilever"] = cant
+        if not args.no_mls:
+            configs["cantilever"]["mls"] = _mls(cinp, stream, peak_gflops)
+        del cinp
+        back, _ = _config("backanalysis", dev, stream, peak_gflops, args, steps=3, warm=1, cpu_s=4.0)
+        configs["backanalysis"] = back
 
     batched = None
-    if args.batched_instances > 0:
+    if rank == 0 and args.batched_instances > 0:
         batched = _batched(args.batched_instances, dev, stream, warm=args.batched_warmup)
     grad = None
-    if not args.no_grad:
+    if rank == 0 and not args.no_grad:
         grad = _backanalysis(dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p)
+        cpu = cpu_baseline(p, args.cpu_seconds)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": WORKLOAD, "n_nodes": p.n_nodes, "n_points": p.n_points,
-                          "step": "rpim_build_pattern + rpim_assemble + rpim_add_point_loads",
-                          "l2": "working set larger than L2 (K %.2f GB, shape functions %.2f GB)"
+               "config": {"workload": desc, "n_nodes": p.n_nodes, "n_points": p.n_points,
+                          "step": "rpim_build_pattern + rpim_assemble" + (" + rpim_add_traction" if p.n_faces else ""),
+                          "l2": "inputs and outputs larger than L2 (K %.1f GB, shape functions %.1f GB)"
                                 % (nnzb * 72 / 1e9, nsup.sum() * 32 / 1e9),
-                          "parallelism": "replicas" if world > 1 else "single GPU"},
+                          "support": {"min": int(nsup.min()), "max": int(nsup.max()), "mean": float(nsup.mean())},
+                          "nnz_blocks": nnzb, "parallelism": "replicas" if world > 1 else "single GPU"},
                "roofline": roof, "kernel_ms_per_step": kernel_ms, "kernel_time_share": kernel_share,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-               "solve": solve, "batched": batched, "backanalysis": grad, "mls": mls,
+               "solve": solve, "configs": configs, "batched": batched, "backanalysis": grad,
                "autotune": [{"max_support": a, "warps_per_point": g, "points_per_block": c} for a, g, c in tuned]
                if tuned else None, "bucket_bounds": bounds,
                "fp64_peak_gflops_measured": peak_gflops}
@@ -745,17 +898,27 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="slope", choices=["slope", "cantilever"],
+                    help="headline workload (the layered slope; the cantilever for small profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-solve", action="store_true", help="skip the penalty + PCG measurement")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="host seconds of the oracle's all-core sample of the headline workload")
+    ap.add_argument("--no-solve", action="store_true", help="skip the penalty + PCG measurements")
+    ap.add_argument("--precond", default="jacobi,block",
+                    help="PCG preconditioners to time (comma separated: jacobi, block)")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-grad", action="store_true", help="skip the back-analysis gradient measurement")
     ap.add_argument("--no-mls", action="store_true", help="skip the MLS-variant assembly measurement")
     ap.add_argument("--batched-warmup", type=int, default=1,
                     help="untimed runs of each arm of the batched comparison before the timed one")
     ap.add_argument("--no-autotune", action="store_true", help="use the built-in launch shapes of the shape kernel")
+    ap.add_argument("--tune-points", type=int, default=8000,
+                    help="points per support-size bucket timed by the launch-shape autotuner")
     ap.add_argument("--solve-iters", type=int, default=0,
-                    help="run the solve for exactly this many PCG iterations (profiling; 0 = to rtol 1e-10)")
-    ap.add_argument("--batched-instances", type=int, default=32,
+                    help="run each solve for exactly this many PCG iterations (profiling; 0 = to rtol 1e-10)")
+    ap.add_argument("--batched-instances", type=int, default=64,
                     help="blocks of the 512-block batched workload in the batched vs per-instance "
                          "comparison (512 = all; 0 = skip)")
     args = ap.parse_args()

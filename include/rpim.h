@@ -43,7 +43,8 @@ typedef enum {
     RPIM_E_ARG = 1,       /* invalid argument (null pointer, bad size, bad parameter)      */
     RPIM_E_CUDA = 2,      /* a CUDA runtime call failed                                     */
     RPIM_E_OOM = 3,       /* device or host allocation failed                               */
-    RPIM_E_SUPPORT = 4,   /* a point has fewer than 4 or more than RPIM_MAX_SUPPORT nodes   */
+    RPIM_E_SUPPORT = 4,   /* a point has fewer than 4 or more than RPIM_MAX_SUPPORT nodes,  
+                           * or a node lies in no point's support                          */
     RPIM_E_SINGULAR = 5,  /* degenerate support: the moment problem is singular             */
     RPIM_E_NOCONV = 6,    /* PCG reached max_iter before the tolerance                      */
     RPIM_E_NONFINITE = 7, /* a NaN or infinity was met in the inputs or the iteration       */
@@ -98,8 +99,9 @@ typedef struct {
  *   out      host: receives the new pattern (free with rpim_pattern_free)
  *   nnz_blocks host, optional: number of 3x3 blocks of K
  * Synchronises `stream` (sizes come back to the host).
- * Errors: RPIM_E_ARG, RPIM_E_SUPPORT (point index in rpim_last_error),
- * RPIM_E_OOM, RPIM_E_CUDA.
+ * Errors: RPIM_E_ARG, RPIM_E_SUPPORT (a support outside 4..RPIM_MAX_SUPPORT,
+ * point index in rpim_last_error; or a node that no point's support reaches,
+ * whose row of K would be empty: node index), RPIM_E_OOM, RPIM_E_CUDA.
  */
 rpim_status rpim_build_pattern(int64_t n_nodes, const double *xyz, const double *cell_lo,
                                const double *cell_hi, const rpim_params *params,
@@ -274,6 +276,23 @@ rpim_status rpim_autotune_buckets(rpim_pattern *pattern, int64_t max_points, int
  */
 rpim_status rpim_set_shape_schedule(int32_t persistent);
 
+/*
+ * Order in which the row-owner kernels (the pattern build's two row passes
+ * and the assembly's row kernel) take the rows of K, process-wide:
+ * 1 (default) the Morton order of the nodes' grid cells (computed by every
+ * rpim_build_pattern: Morton keys of the cell coordinates, instance first,
+ * sorted by a stable radix sort), which keeps the rows that the GPU works on
+ * at the same time spatially compact so that they share the integration
+ * points they read; 0 node order. Every row is computed the same way in
+ * either order, so K, f and the pattern are bitwise the same; the setting
+ * changes speed only. Errors: RPIM_E_ARG.
+ */
+rpim_status rpim_set_row_order(int32_t morton);
+
+/* Copy of a pattern's Morton row order (device int32 [n_nodes], a
+ * permutation of the nodes), stream ordered. Errors: RPIM_E_ARG. */
+rpim_status rpim_pattern_copy_row_order(const rpim_pattern *pattern, int32_t *order, rpim_stream_t stream);
+
 /* Sets the launch shape for buckets whose largest support is max_support
  * (as rpim_autotune_shape would). Errors: RPIM_E_ARG when the shape is not
  * admissible (1-16 warps per point, 1-15 points per block, at most 1024
@@ -292,8 +311,8 @@ rpim_status rpim_autotune_reset(void);
 rpim_status rpim_shape_functions(rpim_pattern *pattern, double *phi, rpim_stream_t stream);
 
 /*
- * Surface loads lumped at points (Sec. 3 examples: pressure, shear traction):
- * f_I += sum_p phi_I(x_p) F_p, with F_p = traction x quadrature weight,
+ * Loads at given points: f_I += sum_p phi_I(x_p) F_p (point forces, or
+ * surface loads lumped at quadrature points chosen by the caller),
  * summed in ascending p for each node. Point supports use the pattern's
  * cell list and parameters.
  *   n_pts, xyz [n_pts*3], force [n_pts*3]; f [3*n_nodes] accumulated.
@@ -301,6 +320,49 @@ rpim_status rpim_shape_functions(rpim_pattern *pattern, double *phi, rpim_stream
  */
 rpim_status rpim_add_point_loads(rpim_pattern *pattern, int64_t n_pts, const double *xyz,
                                  const double *force, double *f, rpim_stream_t stream);
+
+/*
+ * Surface tractions (Sec. 2, stage 1: the load side of the system; Sec. 3
+ * examples: pressure on a face, parabolic shear on a beam end), integrated
+ * by the library over axis-aligned face rectangles:
+ *   face k lies in the plane x_a = face_lo[3k+a], a = face_axis[k] in {0,1,2}
+ *   (face_hi[3k+a] must equal it), and spans [face_lo, face_hi] along its two
+ *   tangent axes u < v (ascending axis order);
+ *   coef [n_faces*18]: component c of the traction on face k is
+ *   t_c(u, v) = sum_j coef[18k + 6c + j] m_j, m = (1, u, v, u^2, u v, v^2),
+ *   in global coordinates (u, v of the point on the face).
+ * Each face is integrated with the 2x2 Gauss-Legendre rule (points
+ * mid +- half/sqrt(3) along u and v, weight half_u half_v):
+ *   f_I += sum_k sum_p phi_I(x_kp) t(x_kp) w_kp,
+ * summed for each node in ascending (face, point) order. Point supports use
+ * the pattern's cell list and parameters; the points must have supports of
+ * 4..RPIM_MAX_SUPPORT nodes.
+ *   face_lo, face_hi [n_faces*3], face_axis [n_faces] (int8), coef: device;
+ *   f [3*n_nodes] accumulated. n_faces = 0 is a no-op.
+ * Synchronises. Errors: RPIM_E_ARG (a face that is not planar along its
+ * axis, has lo > hi along a tangent axis or names no axis: face index in
+ * rpim_last_error), RPIM_E_SUPPORT, RPIM_E_SINGULAR, RPIM_E_OOM, RPIM_E_CUDA.
+ */
+rpim_status rpim_add_traction(rpim_pattern *pattern, int64_t n_faces, const double *face_lo,
+                              const double *face_hi, const int8_t *face_axis, const double *coef,
+                              double *f, rpim_stream_t stream);
+
+/* Batched tractions: as rpim_add_traction, with the instance of every face
+ * (device int32 [n_faces]). Required for batched patterns. Errors: RPIM_E_ARG
+ * also when an id is outside [0, n_inst) (checked on the device before any
+ * use). */
+rpim_status rpim_add_traction_batched(rpim_pattern *pattern, int64_t n_faces, const double *face_lo,
+                                      const double *face_hi, const int8_t *face_axis, const double *coef,
+                                      const int32_t *inst, double *f, rpim_stream_t stream);
+
+/*
+ * f += x over the 3*n_nodes entries of a load vector (device arrays), stream
+ * ordered, no synchronisation: adds a material-independent load vector
+ * assembled once (tractions, point loads) to the body-force vector that each
+ * rpim_assemble writes, e.g. in every forward solve of a back-analysis.
+ * Errors: RPIM_E_ARG (null pointer), RPIM_E_CUDA.
+ */
+rpim_status rpim_add_vector(rpim_pattern *pattern, const double *x, double *f, rpim_stream_t stream);
 
 /*
  * Batched surface loads: as rpim_add_point_loads, with the instance of every
@@ -347,9 +409,24 @@ rpim_status rpim_apply_penalty_alpha(rpim_pattern *pattern, double *K_vals, doub
                                      rpim_stream_t stream);
 
 /*
- * Stage 3 (Sec. 2): solve K u = f by Jacobi-preconditioned conjugate
- * gradients in FP64 with deterministic reductions. u holds the initial guess
- * on entry. Stops when ||r||_2 <= rtol ||f||_2 or after max_iter iterations.
+ * Preconditioner of the PCG solves of a pattern (Sec. 2, stage 3: the paper
+ * solves with library solvers; here K is symmetric positive definite after
+ * the penalty, so conjugate gradients apply). RPIM_PRECOND_JACOBI (the
+ * default): M = diag(K). RPIM_PRECOND_BLOCK_JACOBI: M = the 3x3 diagonal
+ * blocks K_II (the three DOFs of a node), each inverted once per solve from
+ * its L D L^T factors; a block that is not positive definite is reported as
+ * RPIM_E_ARG (DOF index). Applies to rpim_solve_pcg and
+ * rpim_solve_pcg_batched. Errors: RPIM_E_ARG (null pattern, unknown kind).
+ */
+typedef enum { RPIM_PRECOND_JACOBI = 0, RPIM_PRECOND_BLOCK_JACOBI = 1 } rpim_precond_kind;
+rpim_status rpim_pattern_set_precond(rpim_pattern *pattern, int32_t kind);
+rpim_status rpim_pattern_get_precond(const rpim_pattern *pattern, int32_t *kind);
+
+/*
+ * Stage 3 (Sec. 2): solve K u = f by preconditioned conjugate gradients
+ * (rpim_pattern_set_precond; Jacobi by default) in FP64 with deterministic
+ * reductions. u holds the initial guess on entry. Stops when
+ * ||r||_2 <= rtol ||f||_2 or after max_iter iterations.
  *   iters, relres host, optional. Synchronises.
  * Errors: RPIM_E_NOCONV (u holds the last iterate), RPIM_E_NONFINITE.
  */

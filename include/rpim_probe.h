@@ -29,13 +29,25 @@ rpim_status rpim_probe_fp64_mixed(int32_t repeats, double *gflops);
  * kernel uses for the multiquadric minus its chord, for the given
  * parameters: number of pieces, degree, number of FP64 (head) terms, and the
  * largest absolute error of the device evaluation order against the closed
- * form, measured on 20,001 points of the range of s in long double.
+ * form, measured on 129 points per piece of the range of s in long double.
  * Errors: RPIM_E_ARG (parameters out of range, or the check failed). */
 rpim_status rpim_kernel_series_info(double alpha_c, double alpha_s, double q, int32_t *pieces,
                                     int32_t *degree, int32_t *fp64_terms, double *max_err);
 
 /* Number of kernels this library has launched since it was loaded. */
 int64_t rpim_kernel_launches(void);
+
+/* Number of device-memory allocations this library has requested since it
+ * was loaded (every stream-ordered cudaMallocAsync of the stages and every
+ * cudaMalloc of the probes above): the count does not change across a call
+ * that allocates nothing. */
+int64_t rpim_device_allocations(void);
+
+/* Bytes currently in use from the current device's default stream-ordered
+ * memory pool (cudaMemPoolAttrUsedMemCurrent), which serves every allocation
+ * of the stages: the driver's own count, independent of the library's.
+ * Errors: RPIM_E_ARG (null pointer), RPIM_E_CUDA. */
+rpim_status rpim_pool_used_bytes(int64_t *bytes);
 
 /* Turns per-kernel timing on or off (off at load). When on, every launch is
  * bracketed by two CUDA events recorded on the launch's own stream; this

@@ -35,9 +35,13 @@ EXPORTED = [
     "rpim_kernel_launches", "rpim_profile_enable", "rpim_profile_read", "rpim_kernel_series_info",
     "rpim_pattern_set_shape", "rpim_pattern_get_shape", "rpim_assemble_graphed", "rpim_pattern_set_buckets",
     "rpim_pattern_get_buckets", "rpim_autotune_buckets", "rpim_set_shape_schedule",
+    "rpim_device_allocations", "rpim_pool_used_bytes", "rpim_add_traction", "rpim_add_traction_batched",
+    "rpim_add_vector", "rpim_pattern_set_precond", "rpim_pattern_get_precond", "rpim_set_row_order",
+    "rpim_pattern_copy_row_order",
 ]
 
 SHAPE_KINDS = {"rpim": 0, "mls": 1, "shepard": 2}
+PRECONDS = {"jacobi": 0, "block": 1}
 
 
 class RpimError(RuntimeError):
@@ -119,12 +123,21 @@ def lib():
         "rpim_autotune_buckets": [vp, i64, C.POINTER(i32), C.POINTER(i32), vp],
         "rpim_set_shape_schedule": [i32],
         "rpim_pattern_get_shape": [vp, C.POINTER(i32)],
+        "rpim_pool_used_bytes": [C.POINTER(i64)],
+        "rpim_add_traction": [vp, i64, vp, vp, vp, vp, vp, vp],
+        "rpim_add_traction_batched": [vp, i64, vp, vp, vp, vp, vp, vp, vp],
+        "rpim_add_vector": [vp, vp, vp, vp],
+        "rpim_pattern_set_precond": [vp, i32],
+        "rpim_pattern_get_precond": [vp, C.POINTER(i32)],
+        "rpim_set_row_order": [i32],
+        "rpim_pattern_copy_row_order": [vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = C.c_int
     L.rpim_kernel_launches.restype = C.c_int64
+    L.rpim_device_allocations.restype = C.c_int64
     L.rpim_last_error.restype = C.c_char_p
     L.rpim_version.restype = C.c_char_p
     _lib = L
@@ -213,6 +226,18 @@ def rpim_pattern_get_shape(handle) -> str:
     return {v: n for n, v in SHAPE_KINDS.items()}[k.value]
 
 
+def rpim_pattern_set_precond(handle, kind):
+    """kind: "jacobi" or "block" (3x3 block Jacobi), or the integer of rpim_precond_kind."""
+    k = PRECONDS[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().rpim_pattern_set_precond(handle, k), "rpim_pattern_set_precond")
+
+
+def rpim_pattern_get_precond(handle) -> str:
+    k = C.c_int32(0)
+    _check(lib().rpim_pattern_get_precond(handle, C.byref(k)), "rpim_pattern_get_precond")
+    return {v: n for n, v in PRECONDS.items()}[k.value]
+
+
 def rpim_pattern_free(handle):
     lib().rpim_pattern_free(handle)
 
@@ -272,6 +297,16 @@ def rpim_set_shape_schedule(persistent: bool):
     _check(lib().rpim_set_shape_schedule(1 if persistent else 0), "rpim_set_shape_schedule")
 
 
+def rpim_set_row_order(morton: bool):
+    """Rows of the row-owner kernels in Morton order (True) or node order."""
+    _check(lib().rpim_set_row_order(1 if morton else 0), "rpim_set_row_order")
+
+
+def rpim_pattern_copy_row_order(handle, order, stream=None):
+    _check(lib().rpim_pattern_copy_row_order(handle, _dev(order, torch.int32), _stream(stream)),
+           "rpim_pattern_copy_row_order")
+
+
 def rpim_shape_functions(handle, phi, stream=None):
     _check(lib().rpim_shape_functions(handle, _dev(phi, torch.float64), _stream(stream)),
            "rpim_shape_functions")
@@ -281,6 +316,25 @@ def rpim_add_point_loads(handle, xyz, force, f, stream=None):
     _check(lib().rpim_add_point_loads(handle, xyz.shape[0], _dev(xyz, torch.float64),
                                       _dev(force, torch.float64), _dev(f, torch.float64),
                                       _stream(stream)), "rpim_add_point_loads")
+
+
+def rpim_add_traction(handle, face_lo, face_hi, face_axis, coef, f, stream=None):
+    _check(lib().rpim_add_traction(handle, face_lo.shape[0], _dev(face_lo, torch.float64),
+                                   _dev(face_hi, torch.float64), _dev(face_axis, torch.int8),
+                                   _dev(coef, torch.float64), _dev(f, torch.float64), _stream(stream)),
+           "rpim_add_traction")
+
+
+def rpim_add_traction_batched(handle, face_lo, face_hi, face_axis, coef, inst, f, stream=None):
+    _check(lib().rpim_add_traction_batched(handle, face_lo.shape[0], _dev(face_lo, torch.float64),
+                                           _dev(face_hi, torch.float64), _dev(face_axis, torch.int8),
+                                           _dev(coef, torch.float64), _dev(inst, torch.int32),
+                                           _dev(f, torch.float64), _stream(stream)), "rpim_add_traction_batched")
+
+
+def rpim_add_vector(handle, x, f, stream=None):
+    _check(lib().rpim_add_vector(handle, _dev(x, torch.float64), _dev(f, torch.float64), _stream(stream)),
+           "rpim_add_vector")
 
 
 def rpim_apply_penalty_bc(handle, K_vals, f, dofs, values, penalty_scale=1e8, stream=None):
@@ -383,6 +437,18 @@ def rpim_kernel_launches() -> int:
     return int(lib().rpim_kernel_launches())
 
 
+def rpim_device_allocations() -> int:
+    """Device-memory allocations the library has requested since it was loaded."""
+    return int(lib().rpim_device_allocations())
+
+
+def rpim_pool_used_bytes() -> int:
+    """Bytes in use from the current device's default stream-ordered pool."""
+    b = C.c_int64(0)
+    _check(lib().rpim_pool_used_bytes(C.byref(b)), "rpim_pool_used_bytes")
+    return b.value
+
+
 def rpim_profile_enable(on: bool = True) -> None:
     _check(lib().rpim_profile_enable(1 if on else 0), "rpim_profile_enable")
 
@@ -427,6 +493,10 @@ class Pattern:
         if shape != "rpim":
             rpim_pattern_set_shape(self.handle, shape)
 
+    def set_precond(self, kind):
+        """Preconditioner of the later PCG solves: "jacobi" or "block"."""
+        rpim_pattern_set_precond(self.handle, kind)
+
     def set_shape(self, kind):
         """Shape functions of the later stages: "rpim", "mls" or "shepard"."""
         rpim_pattern_set_shape(self.handle, kind)
@@ -468,6 +538,12 @@ class Pattern:
         cols = torch.empty(max(self.nnz_blocks, 1), dtype=torch.int32, device=self.device)
         rpim_pattern_copy_csr(self.handle, rowptr, cols, stream)
         return rowptr, cols[: self.nnz_blocks]
+
+    def row_order(self, stream=None):
+        """The pattern's Morton row order (a permutation of the nodes)."""
+        order = torch.empty(self.info.n_nodes, dtype=torch.int32, device=self.device)
+        rpim_pattern_copy_row_order(self.handle, order, stream)
+        return order
 
     def points(self, stream=None):
         i = self.info
@@ -514,13 +590,26 @@ class Pattern:
             rpim_add_point_loads_batched(self.handle, xyz, force, inst, f, stream)
         return f
 
+    def add_traction(self, face_lo, face_hi, face_axis, coef, f, stream=None, inst=None):
+        """f += the tractions of the faces (see rpim_add_traction); coef
+        [n_faces, 3, 6]; inst: instance of every face (batched patterns)."""
+        if inst is None:
+            rpim_add_traction(self.handle, face_lo, face_hi, face_axis, coef, f, stream)
+        else:
+            rpim_add_traction_batched(self.handle, face_lo, face_hi, face_axis, coef, inst, f, stream)
+        return f
+
     def apply_penalty(self, K, f, dofs, values, scale=1e8, stream=None):
         """alpha (a list of one alpha per instance for batched patterns)."""
         if self.n_inst > 1:
             return rpim_apply_penalty_bc_batched(self.handle, self.n_inst, K, f, dofs, values, scale, stream)
         return rpim_apply_penalty_bc(self.handle, K, f, dofs, values, scale, stream)
 
-    def solve_pcg(self, K, f, u=None, rtol=1e-10, max_iter=100000, stream=None, check=True):
+    def solve_pcg(self, K, f, u=None, rtol=1e-10, max_iter=100000, stream=None, check=True, precond=None):
+        """PCG solve (u holds the initial guess); precond "jacobi" or "block"
+        sets the pattern's preconditioner first (None: keep it)."""
+        if precond is not None:
+            rpim_pattern_set_precond(self.handle, precond)
         if u is None:
             u = torch.zeros(3 * self.info.n_nodes, dtype=torch.float64, device=self.device)
         it, rr, st = rpim_solve_pcg(self.handle, K, f, u, rtol, max_iter, stream, check)
@@ -529,8 +618,10 @@ class Pattern:
     def autotune(self, max_points=20000, stream=None):
         return rpim_autotune_shape(self.handle, max_points, stream)
 
-    def solve_pcg_batched(self, K, f, u=None, rtol=1e-10, max_iter=100000, stream=None, check=True):
+    def solve_pcg_batched(self, K, f, u=None, rtol=1e-10, max_iter=100000, stream=None, check=True, precond=None):
         """Per-instance PCG: (u, iterations per instance, residual per instance)."""
+        if precond is not None:
+            rpim_pattern_set_precond(self.handle, precond)
         if u is None:
             u = torch.zeros(3 * self.info.n_nodes, dtype=torch.float64, device=self.device)
         it, rr, st = rpim_solve_pcg_batched(self.handle, self.n_inst, K, f, u, rtol, max_iter, stream, check)
@@ -555,7 +646,7 @@ class _Solve(torch.autograd.Function):
         E = E.detach().contiguous()
         nu = nu.detach().contiguous()
         K, f = pattern.assemble(E, nu)
-        f += f_ext
+        rpim_add_vector(pattern.handle, f_ext.contiguous(), f)
         rpim_apply_penalty_alpha(pattern.handle, K, f, dofs, values, alpha)
         u = torch.zeros(3 * pattern.info.n_nodes, dtype=torch.float64, device=E.device)
         it, rr, st = rpim_solve_pcg(pattern.handle, K, f, u, rtol, max_iter)
@@ -588,7 +679,8 @@ def solve(pattern, E, nu, f_ext, fixed_dofs, fixed_values, alpha, rtol=1e-12, ma
     """Displacements u(E, nu) with gradients with respect to the per-point
     Young's modulus E and Poisson's ratio nu (torch.autograd).
 
-    f_ext: surface loads (device, 3*n_nodes, material independent);
-    the body-force vector of the pattern's assembly is added inside;
+    f_ext: surface loads (device, 3*n_nodes, material independent, e.g.
+    from rpim_add_traction once), added by rpim_add_vector to the
+    body-force vector of every assembly;
     alpha: the frozen penalty (see penalty_alpha)."""
     return _Solve.apply(E, nu, pattern, f_ext, fixed_dofs, fixed_values, alpha, rtol, max_iter)

@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                                                      const int32_t *__restrict__ cell_start,
                                                      const uint32_t *__restrict__ node_cpk,
                                                      const int32_t *__restrict__ node_rank, int nbits, int max_upper,
-                                                     int C, double *K, double *__restrict__ f, DevError *err)
+                                                     int C, const int32_t *__restrict__ order, double *K,
+                                                     double *__restrict__ f, DevError *err)
 {
     extern __shared__ __align__(16) unsigned char row_smem[];
     __shared__ int run_start[8][25], run_pre[8][26];
@@ -106,8 +107,14 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
     double b0 = 0.0, b1 = 0.0, b2 = 0.0;
     if (body) { b0 = body[0]; b1 = body[1]; b2 = body[2]; }
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < n_nodes; I += warps) {
+    for (int64_t rw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; rw < n_nodes; rw += warps) {
+        const int64_t I = order ? (int64_t)order[rw] : rw;
         const int64_t sd = diag[I], rend = rowptr[I + 1];
+        const int64_t t0 = toff[I], t1 = toff[I + 1];
+        if (sd < 0 || t0 >= t1) {   // no point reaches node I (the pattern build rejects this)
+            if (lane == 0) dev_fail(err, RPIM_E_SUPPORT, I);
+            continue;
+        }
         const int U = (int)(rend - sd);
         const int32_t *ucols = cols + sd;
         double *Ku = K + 9 * sd;
@@ -128,7 +135,6 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
             if (bi >= 0 && bi < total) tab[bi] = (int16_t)s;
         }
         __syncwarp();
-        const int64_t t0 = toff[I], t1 = toff[I + 1];
         // uniform Poisson ratio over the row's points?
         const double nu0 = nu[entry_pt[tent[t0]]];
         bool uni = true;
@@ -483,7 +489,8 @@ static rpim_status assemble_issue(rpim_pattern *p, const double *E, const double
     launch("row", row_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, smem, s, p->n_nodes, p->toff,
            p->tent, p->entry_pt, p->soff, p->sidx, p->phi, p->lamw, p->wj, nu, body, p->rowptr, p->cols, p->diag,
            (const InstGrid *)p->ig, (const int32_t *)p->node_inst, (const int32_t *)p->cell_start,
-           (const uint32_t *)p->node_cpk, (const int32_t *)p->node_rank, nbits, max_upper, C, K, f, p->err);
+           (const uint32_t *)p->node_cpk, (const int32_t *)p->node_rank, nbits, max_upper, C, rows_in_order(p), K, f,
+           p->err);
     RPIM_CUDA(cudaGetLastError());
     launch("mirror", mirror_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, 0, s, p->n_nodes, p->rowptr, p->cols, K);
     RPIM_CUDA(cudaGetLastError());
@@ -585,6 +592,89 @@ static rpim_status check_instance_ids(rpim_pattern *p, int64_t n, const int32_t 
     return check_device_error(p, stage);
 }
 
+// The 2x2 Gauss-Legendre points of every face rectangle, with their forces
+// t(x_p) w_p: face k lies in the plane x_a = lo[a] (a = axis[k]) and spans
+// [lo, hi] along its tangent axes u < v; point 4k + l sits at
+// mid +- half/sqrt(3) along u (bit 0 of l) and v (bit 1), weight
+// half_u half_v; component c of the traction is the quadratic polynomial
+// coef[18k + 6c + (0..5)] . (1, u, v, u^2, u v, v^2). A face that is not
+// planar, has lo > hi along a tangent axis or names no axis is reported
+// (RPIM_E_ARG, face index) and contributes nothing.
+__global__ void face_points_kernel(int64_t n_faces, const double *__restrict__ lo, const double *__restrict__ hi,
+                                   const int8_t *__restrict__ axis, const double *__restrict__ coef,
+                                   const int32_t *__restrict__ face_inst, double *pts, double *force,
+                                   int32_t *pt_inst, DevError *err)
+{
+    constexpr double g = 0.57735026918962576451;   // 1/sqrt(3)
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 4 * n_faces;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t >> 2;
+        const int l = (int)(t & 3);
+        const int a = axis[k];
+        const double *L = lo + 3 * k, *H = hi + 3 * k;
+        double *x = pts + 3 * t, *F = force + 3 * t;
+        if (pt_inst) pt_inst[t] = face_inst[k];
+        const int ua = a == 0 ? 1 : 0, va = a == 2 ? 1 : 2;
+        if (a < 0 || a > 2 || L[a] != H[a] || !(L[ua] <= H[ua]) || !(L[va] <= H[va])) {
+            if (l == 0) dev_fail(err, RPIM_E_ARG, k);
+            x[0] = x[1] = x[2] = 0.0;
+            F[0] = F[1] = F[2] = 0.0;
+            continue;
+        }
+        const double mu = __dmul_rn(__dadd_rn(L[ua], H[ua]), 0.5), hu = __dmul_rn(__dsub_rn(H[ua], L[ua]), 0.5);
+        const double mv = __dmul_rn(__dadd_rn(L[va], H[va]), 0.5), hv = __dmul_rn(__dsub_rn(H[va], L[va]), 0.5);
+        const double u = __dadd_rn(mu, __dmul_rn(hu, (l & 1) ? g : -g));
+        const double v = __dadd_rn(mv, __dmul_rn(hv, (l & 2) ? g : -g));
+        x[a] = L[a];
+        x[ua] = u;
+        x[va] = v;
+        const double w = __dmul_rn(hu, hv);
+        const double m1 = u, m2 = v, m3 = u * u, m4 = u * v, m5 = v * v;
+        for (int c = 0; c < 3; c++) {
+            const double *q = coef + 18 * k + 6 * c;
+            const double tc = fma(q[5], m5, fma(q[4], m4, fma(q[3], m3, fma(q[2], m2, fma(q[1], m1, q[0])))));
+            F[c] = tc * w;
+        }
+    }
+}
+
+// f += x over all 3 n_nodes entries
+__global__ void add_vector_kernel(int64_t n, const double *__restrict__ x, double *__restrict__ f)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        f[i] += x[i];
+}
+
+static rpim_status add_point_loads(rpim_pattern *p, int64_t n_pts, const double *xyz, const double *force,
+                                   const int32_t *inst, double *f, cudaStream_t s);
+
+static rpim_status add_traction(rpim_pattern *p, int64_t n_faces, const double *lo, const double *hi,
+                                const int8_t *axis, const double *coef, const int32_t *inst, double *f,
+                                cudaStream_t s)
+{
+    if (!p || n_faces < 0 || (n_faces > 0 && (!lo || !hi || !axis || !coef || !f)))
+        return fail(RPIM_E_ARG, "bad argument");
+    if (p->n_inst > 1 && !inst && n_faces > 0) return fail(RPIM_E_ARG, "a batched pattern needs the instance of every face");
+    if (n_faces == 0) return RPIM_OK;
+    if (n_faces > (int64_t)1 << 40) return fail(RPIM_E_ARG, "too many faces");
+    p->stream = s;
+    const int64_t n_pts = 4 * n_faces;
+    double *pts = nullptr, *force = nullptr;
+    int32_t *pinst = nullptr;
+    rpim_status st = dalloc(&pts, 3 * n_pts, s);
+    if (st == RPIM_OK) st = dalloc(&force, 3 * n_pts, s);
+    if (st == RPIM_OK && inst) st = dalloc(&pinst, n_pts, s);
+    if (st == RPIM_OK) {
+        launch("face_points", face_points_kernel, grid_size(p->sm_count, 4, n_pts, 256), 256, 0, s, n_faces, lo, hi,
+               axis, coef, inst, pts, force, pinst, p->err);
+        st = cudaGetLastError() == cudaSuccess ? check_device_error(p, "traction: faces")
+                                               : fail(RPIM_E_CUDA, "face kernel launch");
+    }
+    if (st == RPIM_OK) st = add_point_loads(p, n_pts, pts, force, pinst, f, s);
+    dfree(pts, s); dfree(force, s); dfree(pinst, s);
+    return st;
+}
+
 static rpim_status add_point_loads(rpim_pattern *p, int64_t n_pts, const double *xyz, const double *force,
                                    const int32_t *inst, double *f, cudaStream_t s)
 {
@@ -626,6 +716,32 @@ extern "C" rpim_status rpim_add_point_loads_batched(rpim_pattern *p, int64_t n_p
 {
     if (!inst && n_pts > 0) return fail(RPIM_E_ARG, "inst is null");
     return add_point_loads(p, n_pts, xyz, force, inst, f, (cudaStream_t)stream);
+}
+
+extern "C" rpim_status rpim_add_traction(rpim_pattern *p, int64_t n_faces, const double *face_lo,
+                                         const double *face_hi, const int8_t *face_axis, const double *coef,
+                                         double *f, rpim_stream_t stream)
+{
+    return add_traction(p, n_faces, face_lo, face_hi, face_axis, coef, nullptr, f, (cudaStream_t)stream);
+}
+
+extern "C" rpim_status rpim_add_traction_batched(rpim_pattern *p, int64_t n_faces, const double *face_lo,
+                                                 const double *face_hi, const int8_t *face_axis, const double *coef,
+                                                 const int32_t *inst, double *f, rpim_stream_t stream)
+{
+    if (!inst && n_faces > 0) return fail(RPIM_E_ARG, "inst is null");
+    return add_traction(p, n_faces, face_lo, face_hi, face_axis, coef, inst, f, (cudaStream_t)stream);
+}
+
+extern "C" rpim_status rpim_add_vector(rpim_pattern *p, const double *x, double *f, rpim_stream_t stream)
+{
+    if (!p || !x || !f) return fail(RPIM_E_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->stream = s;
+    const int64_t n = 3 * p->n_nodes;
+    launch("add_vector", add_vector_kernel, grid_size(p->sm_count, 4, n, 256), 256, 0, s, n, x, f);
+    RPIM_CUDA(cudaGetLastError());
+    return RPIM_OK;
 }
 
 static rpim_status stress(rpim_pattern *p, const double *u, int64_t n_pts, const double *xyz, const int32_t *inst,

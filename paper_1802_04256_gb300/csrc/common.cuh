@@ -148,6 +148,7 @@ struct rpim_pattern {
     rpim_params prm{};     // alpha_c, q (common); alpha_s, h of the first instance
     int n_inst = 1;
     int shape_kind = RPIM_SHAPE_RPIM;   // shape functions of every stage (rpim_pattern_set_shape)
+    int precond = RPIM_PRECOND_JACOBI;  // PCG preconditioner (rpim_pattern_set_precond)
     double series_alpha_s = 0.0;    // support radius the kernel series covers
     std::vector<rpim::InstGrid> ig_host;
     rpim::InstGrid *ig = nullptr;   // [n_inst] device copy
@@ -175,6 +176,7 @@ struct rpim_pattern {
     int32_t *node_cell = nullptr;   // [n_nodes] linear cell index of each node
     uint32_t *node_cpk = nullptr;   // [n_nodes] cell coordinates packed x | y << 11 | z << 22
     int32_t *node_rank = nullptr;   // [n_nodes] position of the node in its cell
+    int32_t *row_order = nullptr;   // [n_nodes] nodes by Morton key of their cell (instance first), ids ascending
     // integration points
     double *pts = nullptr;          // [n_points*3]
     double *wj = nullptr;           // [n_points]
@@ -214,11 +216,15 @@ struct rpim_pattern {
 
 namespace rpim {
 
+// every device allocation the library makes is counted (rpim_device_allocations)
+void note_device_alloc();
+
 // allocation helpers (stream ordered)
 template <class T>
 rpim_status dalloc(T **p, int64_t count, cudaStream_t s)
 {
     if (count <= 0) count = 1;
+    note_device_alloc();
     cudaError_t e = cudaMallocAsync((void **)p, (size_t)count * sizeof(T), s);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -238,6 +244,10 @@ void dfree(T *&p, cudaStream_t s)
 int64_t scan_tmp_size(int64_t n);
 rpim_status exclusive_scan(int64_t *data, int64_t n, int64_t *tmp, cudaStream_t s);
 rpim_status exclusive_scan32(int32_t *data, int64_t n, int64_t *tmp, cudaStream_t s);
+
+// stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
+// keys (in place; scratch allocated stream ordered)
+rpim_status radix_sort_pairs(uint64_t *keys, int32_t *vals, int64_t n, int bits, cudaStream_t s);
 
 // reads the device error word; returns RPIM_OK or the recorded status
 rpim_status check_device_error(rpim_pattern *p, const char *stage);
@@ -268,6 +278,10 @@ rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, c
 // shape functions of all integration points of a pattern, one launch per
 // support-size bucket
 rpim_status shape_functions_all(rpim_pattern *p, double *phi, cudaStream_t s);
+
+// the order in which the row-owner kernels (pattern, row) take their rows:
+// the pattern's Morton order, or null (node order), per rpim_set_row_order
+const int32_t *rows_in_order(const rpim_pattern *p);
 
 // bucket bounds that new patterns start with (empty: the built-in ones)
 void set_default_buckets(const std::vector<int32_t> &bounds);

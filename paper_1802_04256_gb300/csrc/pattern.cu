@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <string>
 
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -164,6 +165,35 @@ __global__ void finish_cells(int64_t cells, const int32_t *cell_start, int32_t *
     }
     for (int o = 16; o > 0; o >>= 1) mc = max(mc, __shfl_down_sync(0xffffffffu, mc, o));
     if ((threadIdx.x & 31) == 0) atomicMax(max_cell, mc);
+}
+
+// ---------------------------------------------------------------------------
+// Morton order of the nodes: key = instance << 32 | the Morton code of the
+// node's cell (bits of cx, cy, cz interleaved, x lowest: 11 + 11 + 10 bits),
+// sorted stably so that the nodes of a cell keep ascending ids. Rows taken in
+// this order are spatially compact at every scale, so the warps working
+// side by side share the integration points (and their shape-function
+// records) they read.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z)
+{
+    uint32_t m = 0;
+    for (int b = 0; b < 11; b++) {
+        m |= ((x >> b) & 1u) << (3 * b);
+        m |= ((y >> b) & 1u) << (3 * b + 1);
+        if (b < 10) m |= ((z >> b) & 1u) << (3 * b + 2);
+    }
+    return m;
+}
+
+__global__ void morton_keys_kernel(int64_t n, const uint32_t *node_cpk, const int32_t *node_inst, uint64_t *keys,
+                                   int32_t *ids)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = node_cpk[i];
+        keys[i] = ((uint64_t)(uint32_t)node_inst[i] << 32) | morton3(c & 0x7FF, (c >> 11) & 0x7FF, c >> 22);
+        ids[i] = (int32_t)i;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -391,7 +421,7 @@ __global__ void pattern_bits_kernel(int64_t n_nodes, const InstGrid *ig, const i
                                     const int32_t *cell_start, const uint32_t *node_cpk, const int32_t *node_rank,
                                     const int64_t *toff, const int64_t *tent, const int32_t *entry_pt,
                                     const int64_t *soff, const int32_t *sidx, int64_t *rowcnt, uint32_t *bm,
-                                    int words, int *maxrow, DevError *err)
+                                    int words, int *maxrow, const int32_t *order, DevError *err)
 {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -400,20 +430,27 @@ __global__ void pattern_bits_kernel(int64_t n_nodes, const InstGrid *ig, const i
     __shared__ int run_start[8][25], run_pre[8][26];
     const int64_t warps = (int64_t)gridDim.x * nw;
     int mrow = 0;
-    for (int64_t I = (int64_t)blockIdx.x * nw + w; I < n_nodes; I += warps) {
+    for (int64_t rw = (int64_t)blockIdx.x * nw + w; rw < n_nodes; rw += warps) {
+        const int64_t I = order ? (int64_t)order[rw] : rw;
         const InstGrid &g = ig[node_inst[I]];
         const uint32_t ci = node_cpk[I];
         const int cx = (int)(ci & 0x7FF), cy = (int)((ci >> 11) & 0x7FF), cz = (int)(ci >> 22);
         const int total = cell_runs(g, cell_start, cx, cy, cz, lane, run_start[w], run_pre[w]);
-        if (total > words * 32) {
-            if (lane == 0) dev_fail(err, RPIM_E_SUPPORT, I);
+        const int64_t t_begin = toff[I], t_end = toff[I + 1];
+        // a node that no integration point's support reaches would get an
+        // empty row without a diagonal block (K singular): rejected here,
+        // before any later stage indexes its row
+        if (total > words * 32 || t_begin == t_end) {
+            if (lane == 0) {
+                dev_fail(err, RPIM_E_SUPPORT, I);
+                rowcnt[I] = 0;
+            }
             continue;
         }
         const int nwords = (total + 31) / 32;
         for (int i = lane; i < nwords; i += 32) bits[i] = 0;
         __syncwarp();
-        const int64_t t_end = toff[I + 1];
-        for (int64_t t0 = toff[I]; t0 < t_end; t0 += 32) {
+        for (int64_t t0 = t_begin; t0 < t_end; t0 += 32) {
             const int nt = (int)min((int64_t)32, t_end - t0);
             int64_t s0 = 0;
             int len = 0;
@@ -479,7 +516,7 @@ __global__ void pattern_bits_kernel(int64_t n_nodes, const InstGrid *ig, const i
 __global__ void pattern_cols_kernel(int64_t n_nodes, const InstGrid *ig, const int32_t *node_inst,
                                     const int32_t *cell_start, const uint32_t *node_cpk, const int32_t *sorted_ids,
                                     const uint32_t *bm, int words, const int64_t *rowptr, int32_t *cols,
-                                    int64_t *diag, int list_cap)
+                                    int64_t *diag, int list_cap, const int32_t *order)
 {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -487,7 +524,8 @@ __global__ void pattern_cols_kernel(int64_t n_nodes, const InstGrid *ig, const i
     int32_t *list = (int32_t *)smem + (size_t)w * list_cap;
     __shared__ int run_start[8][25], run_pre[8][26];
     const int64_t warps = (int64_t)gridDim.x * nw;
-    for (int64_t I = (int64_t)blockIdx.x * nw + w; I < n_nodes; I += warps) {
+    for (int64_t rw = (int64_t)blockIdx.x * nw + w; rw < n_nodes; rw += warps) {
+        const int64_t I = order ? (int64_t)order[rw] : rw;
         const InstGrid &g = ig[node_inst[I]];
         const uint32_t ci = node_cpk[I];
         const int cx = (int)(ci & 0x7FF), cy = (int)((ci >> 11) & 0x7FF), cz = (int)(ci >> 22);
@@ -556,6 +594,7 @@ static void pattern_release(rpim_pattern *p)
     cudaStream_t s = p->stream;
     dfree(p->xyz, s); dfree(p->sorted_xyz, s); dfree(p->sorted_loc, s); dfree(p->sorted_ids, s); dfree(p->cell_start, s);
     dfree(p->node_cell, s); dfree(p->node_cpk, s); dfree(p->node_rank, s); dfree(p->pts, s); dfree(p->wj, s);
+    dfree(p->row_order, s);
     dfree(p->soff, s); dfree(p->sidx, s); dfree(p->entry_pt, s); dfree(p->toff, s);
     dfree(p->tent, s); dfree(p->rowptr, s); dfree(p->cols, s); dfree(p->diag, s);
     dfree(p->phi, s); dfree(p->lamw, s); dfree(p->err, s); dfree(p->scal, s); dfree(p->series, s);
@@ -629,6 +668,14 @@ extern "C" rpim_status rpim_pattern_copy_csr(const rpim_pattern *p, int64_t *row
     return RPIM_OK;
 }
 
+extern "C" rpim_status rpim_pattern_copy_row_order(const rpim_pattern *p, int32_t *order, rpim_stream_t stream)
+{
+    if (!p || !order) return fail(RPIM_E_ARG, "null argument");
+    RPIM_CUDA(cudaMemcpyAsync(order, p->row_order, p->n_nodes * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                              (cudaStream_t)stream));
+    return RPIM_OK;
+}
+
 extern "C" rpim_status rpim_pattern_copy_points(const rpim_pattern *p, double *xyz, double *wj, int64_t *soff,
                                                 int32_t *sidx, rpim_stream_t stream)
 {
@@ -667,6 +714,20 @@ __global__ void bucket_fill_kernel(int64_t n_pts, const int64_t *soff, const int
         while (b < nb - 1 && n > bounds[b]) b++;
         order[start[b] + (int64_t)atomicAdd(&cursor[b], 1ull)] = (int32_t)g;
     }
+}
+
+static std::atomic<int> g_morton_rows{1};
+
+namespace rpim {
+// the order in which the row-owner kernels take their rows (null: node order)
+const int32_t *rows_in_order(const rpim_pattern *p) { return g_morton_rows.load() ? p->row_order : nullptr; }
+} // namespace rpim
+
+extern "C" rpim_status rpim_set_row_order(int32_t morton)
+{
+    if (morton != 0 && morton != 1) return fail(RPIM_E_ARG, "row order must be 0 or 1");
+    g_morton_rows.store(morton);
+    return RPIM_OK;
 }
 
 // upper support size of each bucket (the last one is open-ended): the
@@ -871,6 +932,20 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     dfree(tmp, s);
     dfree(dmax, s);
 
+    // Morton order of the rows (instance first; see morton_keys_kernel)
+    {
+        uint64_t *keys = nullptr;
+        RPIM_CHECK(dalloc(&keys, n, s));
+        RPIM_CHECK(dalloc(&p->row_order, n, s));
+        launch("morton_keys", morton_keys_kernel, grid_size(p->sm_count, 4, n, 256), 256, 0, s, n,
+               (const uint32_t *)p->node_cpk, (const int32_t *)p->node_inst, keys, p->row_order);
+        int ibits = 0;
+        while ((1ll << ibits) < (long long)ni) ibits++;
+        const rpim_status st = radix_sort_pairs(keys, p->row_order, n, 32 + ibits, s);
+        dfree(keys, s);
+        RPIM_CHECK(st);
+    }
+
     // supports of the integration points (point g belongs to node g/8)
     RPIM_CHECK(search_supports(p, p->n_points, p->pts, p->node_inst, 3, &p->soff, &p->sidx, &p->n_entries,
                                &p->max_support, &p->min_support, s, "search"));
@@ -885,6 +960,7 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     const int words = (125 * p->max_cell + 31) / 32 + 1;
     RPIM_CHECK(dalloc(&p->rowptr, n + 1, s));
     RPIM_CHECK(dalloc(&p->diag, n, s));
+    RPIM_CUDA(cudaMemsetAsync(p->diag, 0xFF, n * sizeof(int64_t), s));   // -1: no diagonal block
     RPIM_CHECK(dalloc(&dmax, 1, s));
     RPIM_CHECK(dalloc(&tmp, scan_tmp_size(n), s));
     RPIM_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
@@ -904,7 +980,7 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
                n, (const InstGrid *)p->ig, (const int32_t *)p->node_inst, (const int32_t *)p->cell_start,
                (const uint32_t *)p->node_cpk, (const int32_t *)p->node_rank, (const int64_t *)p->toff,
                (const int64_t *)p->tent, (const int32_t *)p->entry_pt, (const int64_t *)p->soff,
-               (const int32_t *)p->sidx, p->rowptr, bm, words, dmax, p->err);
+               (const int32_t *)p->sidx, p->rowptr, bm, words, dmax, rows_in_order(p), p->err);
         RPIM_CUDA(cudaGetLastError());
     }
     RPIM_CHECK(exclusive_scan(p->rowptr, n, tmp, s));
@@ -936,7 +1012,7 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
             launch("pattern_fill", pattern_cols_kernel, grid_size(p->sm_count, 4, n, wpb), wpb * 32, smem, s,
                    n, (const InstGrid *)p->ig, (const int32_t *)p->node_inst, (const int32_t *)p->cell_start,
                    (const uint32_t *)p->node_cpk, (const int32_t *)p->sorted_ids, (const uint32_t *)bm, words,
-                   (const int64_t *)p->rowptr, p->cols, p->diag, p2);
+                   (const int64_t *)p->rowptr, p->cols, p->diag, p2, rows_in_order(p));
             if (cudaGetLastError() != cudaSuccess) st = fail(RPIM_E_CUDA, "pattern fill launch");
         }
     }

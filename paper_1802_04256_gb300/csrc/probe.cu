@@ -115,6 +115,7 @@ extern "C" rpim_status rpim_probe_dfma(int32_t repeats, double *gflops)
     RPIM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int blocks = sms * 8, threads = 256, iters = 4096;
     double *out = nullptr;
+    note_device_alloc();
     RPIM_CUDA(cudaMalloc(&out, (size_t)blocks * threads * sizeof(double)));
     const double flops = 2.0 * kChains * (double)iters * blocks * threads;
     rpim_status st = time_best(repeats, flops, [&] { dfma_probe_kernel<<<blocks, threads>>>(out, iters, 0.9999999, 1e-7); }, gflops);
@@ -130,6 +131,7 @@ extern "C" rpim_status rpim_probe_dmma(int32_t repeats, double *gflops)
     RPIM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int blocks = sms * 8, threads = 256, iters = 1024;
     double *out = nullptr;
+    note_device_alloc();
     RPIM_CUDA(cudaMalloc(&out, (size_t)blocks * threads * sizeof(double)));
     const double flops = 512.0 * 4 * (double)iters * blocks * (threads / 32);
     rpim_status st = time_best(repeats, flops, [&] { dmma_probe_kernel<<<blocks, threads>>>(out, iters, 1.0); }, gflops);
@@ -147,6 +149,7 @@ extern "C" rpim_status rpim_probe_fp64_mixed(int32_t repeats, double *gflops)
     // work per half at iters_f = 4 iters_m
     const int blocks = sms * 8, threads = 256, iters_m = 1024, iters_f = 4 * iters_m;
     double *out = nullptr;
+    note_device_alloc();
     RPIM_CUDA(cudaMalloc(&out, (size_t)blocks * threads * sizeof(double)));
     const double warps = (double)blocks * (threads / 32) / 2;
     const double flops = warps * (2.0 * kChains * 32 * iters_f + 512.0 * 4 * iters_m);

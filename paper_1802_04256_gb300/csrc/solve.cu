@@ -81,7 +81,9 @@ __global__ void penalty_apply_kernel(int64_t m, const int64_t *dofs, const doubl
 
 // ---------------------------------------------------------------------------
 // PCG. Deterministic dot products: fixed grid, fixed in-block tree, and the
-// last block to finish sums the per-block partials in index order.
+// last block to finish sums the per-block partials in index order. The
+// preconditioner is the diagonal of K (Jacobi) or its 3x3 diagonal blocks
+// (block Jacobi: each node's block inverted once, in pcg_init).
 // ---------------------------------------------------------------------------
 struct PcgState {
     double rz, pq, alpha, beta, rr, fnorm, relres, rtol;
@@ -178,21 +180,48 @@ __device__ __forceinline__ double bsr_row(int64_t I, const int64_t *rowptr, cons
     return d;
 }
 
-// r = f - K x, z = Dinv r, p = z; partials of r.z, r.r, f.f
-__global__ void __launch_bounds__(kPcgThreads) pcg_init_kernel(int64_t n_nodes, const int64_t *rowptr,
-                                                               const int32_t *cols, const double *K,
-                                                               const int64_t *diag, const double *f,
-                                                               const double *x, double *r, double *z,
-                                                               double *p, double *dinv, double *part,
-                                                               PcgState *st, DevError *err)
+// Inverse of a symmetric positive definite 3x3 block (row-major) from its
+// L D L^T factors, inv = L^-T D^-1 L^-1 (9 entries written); false when a
+// pivot is not positive (the block is not SPD).
+__device__ __forceinline__ bool spd3_inverse(const double *b, double *inv)
 {
-    __shared__ double sh[32];
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    double rz = 0.0, rr = 0.0, ff = 0.0;
-    for (int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < n_nodes; I += warps) {
-        bsr_row(I, rowptr, cols, K, x, r, lane);
-        __syncwarp();
+    const double d0 = b[0];
+    if (!(d0 > 0.0)) return false;
+    const double l10 = b[3] / d0, l20 = b[6] / d0;
+    const double d1 = fma(-l10, b[3], b[4]);
+    if (!(d1 > 0.0)) return false;
+    const double l21 = fma(-l20, b[3], b[7]) / d1;
+    const double d2 = fma(-l21 * l21, d1, fma(-l20, b[6], b[8]));
+    if (!(d2 > 0.0)) return false;
+    const double e0 = 1.0 / d0, e1 = 1.0 / d1, e2 = 1.0 / d2;
+    const double m10 = -l10, m21 = -l21, m20 = fma(l10, l21, -l20);   // L^-1 below the unit diagonal
+    const double i00 = fma(m20 * m20, e2, fma(m10 * m10, e1, e0)), i01 = fma(m20 * m21, e2, m10 * e1);
+    const double i02 = m20 * e2, i11 = fma(m21 * m21, e2, e1), i12 = m21 * e2, i22 = e2;
+    inv[0] = i00; inv[1] = i01; inv[2] = i02;
+    inv[3] = i01; inv[4] = i11; inv[5] = i12;
+    inv[6] = i02; inv[7] = i12; inv[8] = i22;
+    return true;
+}
+
+// z_I = B_I r_I with the stored 3x3 inverse B_I of node I's diagonal block
+__device__ __forceinline__ void apply3(const double *B, double r0, double r1, double r2, double &z0, double &z1,
+                                       double &z2)
+{
+    z0 = fma(B[0], r0, fma(B[1], r1, B[2] * r2));
+    z1 = fma(B[3], r0, fma(B[4], r1, B[5] * r2));
+    z2 = fma(B[6], r0, fma(B[7], r1, B[8] * r2));
+}
+
+// Preconditioner of node I (lane 0 of the warp that just formed r_I = (K x)_I
+// in r): r <- f - r, z = M^-1 r, p = z; accumulates r.z, r.r, f.f. M is the
+// diagonal of K (Jacobi: dinv[3n]) or its 3x3 diagonal blocks (block Jacobi:
+// dinv[9n] holds each block's inverse).
+template <bool BLOCK>
+__device__ __forceinline__ void init_node(int64_t I, int lane, const double *K, const int64_t *diag,
+                                          const double *f, double *r, double *z, double *p, double *dinv,
+                                          double &rz, double &rr, double &ff, DevError *err)
+{
+    if (!BLOCK) {
         if (lane < 3) {
             const int64_t d = 3 * I + lane;
             const double kd = K[9 * diag[I] + 4 * lane];
@@ -208,6 +237,72 @@ __global__ void __launch_bounds__(kPcgThreads) pcg_init_kernel(int64_t n_nodes, 
             rr += rv * rv;
             ff += f[d] * f[d];
         }
+    } else if (lane == 0) {
+        double *B = dinv + 9 * I;
+        if (!spd3_inverse(K + 9 * diag[I], B)) {
+            dev_fail(err, RPIM_E_ARG, 3 * I);
+            for (int k = 0; k < 9; k++) B[k] = 0.0;
+        }
+        const double r0 = f[3 * I] - r[3 * I], r1 = f[3 * I + 1] - r[3 * I + 1], r2 = f[3 * I + 2] - r[3 * I + 2];
+        double z0, z1, z2;
+        apply3(B, r0, r1, r2, z0, z1, z2);
+        r[3 * I] = r0; r[3 * I + 1] = r1; r[3 * I + 2] = r2;
+        z[3 * I] = z0; z[3 * I + 1] = z1; z[3 * I + 2] = z2;
+        p[3 * I] = z0; p[3 * I + 1] = z1; p[3 * I + 2] = z2;
+        rz += (r0 * z0 + r1 * z1) + r2 * z2;
+        rr += (r0 * r0 + r1 * r1) + r2 * r2;
+        ff += (f[3 * I] * f[3 * I] + f[3 * I + 1] * f[3 * I + 1]) + f[3 * I + 2] * f[3 * I + 2];
+    }
+}
+
+// x += alpha p, r -= alpha q, z = M^-1 r for node or DOF i (Jacobi: DOF i;
+// block Jacobi: node i); accumulates r.z, r.r
+template <bool BLOCK>
+__device__ __forceinline__ void update_unit(int64_t i, double alpha, double *x, double *r, double *z,
+                                            const double *p, const double *q, const double *dinv, double &rz,
+                                            double &rr)
+{
+    if (!BLOCK) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const double rv = fma(-alpha, q[i], r[i]);
+        const double zv = dinv[i] * rv;
+        r[i] = rv;
+        z[i] = zv;
+        rz = fma(rv, zv, rz);
+        rr = fma(rv, rv, rr);
+    } else {
+        const int64_t d = 3 * i;
+        x[d] = fma(alpha, p[d], x[d]);
+        x[d + 1] = fma(alpha, p[d + 1], x[d + 1]);
+        x[d + 2] = fma(alpha, p[d + 2], x[d + 2]);
+        const double r0 = fma(-alpha, q[d], r[d]), r1 = fma(-alpha, q[d + 1], r[d + 1]),
+                     r2 = fma(-alpha, q[d + 2], r[d + 2]);
+        double z0, z1, z2;
+        apply3(dinv + 9 * i, r0, r1, r2, z0, z1, z2);
+        r[d] = r0; r[d + 1] = r1; r[d + 2] = r2;
+        z[d] = z0; z[d + 1] = z1; z[d + 2] = z2;
+        rz = fma(r2, z2, fma(r1, z1, fma(r0, z0, rz)));
+        rr = fma(r2, r2, fma(r1, r1, fma(r0, r0, rr)));
+    }
+}
+
+// r = f - K x, z = M^-1 r, p = z; partials of r.z, r.r, f.f
+template <bool BLOCK>
+__global__ void __launch_bounds__(kPcgThreads) pcg_init_kernel(int64_t n_nodes, const int64_t *rowptr,
+                                                               const int32_t *cols, const double *K,
+                                                               const int64_t *diag, const double *f,
+                                                               const double *x, double *r, double *z,
+                                                               double *p, double *dinv, double *part,
+                                                               PcgState *st, DevError *err)
+{
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double rz = 0.0, rr = 0.0, ff = 0.0;
+    for (int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < n_nodes; I += warps) {
+        bsr_row(I, rowptr, cols, K, x, r, lane);
+        __syncwarp();
+        init_node<BLOCK>(I, lane, K, diag, f, r, z, p, dinv, rz, rr, ff, err);
     }
     double b_rz = block_reduce(rz, sh), b_rr = block_reduce(rr, sh), b_ff = block_reduce(ff, sh);
     if (threadIdx.x == 0) {
@@ -258,8 +353,10 @@ __global__ void __launch_bounds__(kPcgThreads) pcg_spmv_kernel(int64_t n_nodes, 
     }
 }
 
-// x += alpha p, r -= alpha q, z = Dinv r; partials r.z, r.r; last block:
-// beta = rz_new / rz, convergence test
+// x += alpha p, r -= alpha q, z = M^-1 r over n units (DOFs for Jacobi,
+// nodes for block Jacobi); partials r.z, r.r; last block: beta = rz_new /
+// rz, convergence test
+template <bool BLOCK>
 __global__ void __launch_bounds__(kPcgThreads) pcg_update_kernel(int64_t n, double *x, double *r, double *z,
                                                                  const double *p, const double *q,
                                                                  const double *dinv, double *part,
@@ -269,15 +366,8 @@ __global__ void __launch_bounds__(kPcgThreads) pcg_update_kernel(int64_t n, doub
     __shared__ double sh[32];
     const double alpha = st->alpha;
     double rz = 0.0, rr = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const double rv = fma(-alpha, q[i], r[i]);
-        const double zv = dinv[i] * rv;
-        r[i] = rv;
-        z[i] = zv;
-        rz = fma(rv, zv, rz);
-        rr = fma(rv, rv, rr);
-    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        update_unit<BLOCK>(i, alpha, x, r, z, p, q, dinv, rz, rr);
     double b_rz = block_reduce(rz, sh), b_rr = block_reduce(rr, sh);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = b_rz;
@@ -352,6 +442,7 @@ __device__ __forceinline__ void count_active(const PcgInst *inst, int n_inst, Pc
     if (threadIdx.x == 0) bst->active = cnt;
 }
 
+template <bool BLOCK>
 __global__ void __launch_bounds__(kPcgThreads) pcgb_init_kernel(int64_t n_seg, const int64_t *seg_row,
                                                                 const int32_t *inst_seg, int n_inst,
                                                                 const int64_t *rowptr, const int32_t *cols,
@@ -367,21 +458,7 @@ __global__ void __launch_bounds__(kPcgThreads) pcgb_init_kernel(int64_t n_seg, c
         for (int64_t I = seg_row[s] + warp; I < seg_row[s + 1]; I += nw) {
             bsr_row(I, rowptr, cols, K, x, r, lane);
             __syncwarp();
-            if (lane < 3) {
-                const int64_t d = 3 * I + lane;
-                const double kd = K[9 * diag[I] + 4 * lane];
-                if (!(kd > 0.0)) dev_fail(err, RPIM_E_ARG, d);
-                const double di = 1.0 / kd;
-                const double rv = f[d] - r[d];
-                const double zv = di * rv;
-                dinv[d] = di;
-                r[d] = rv;
-                z[d] = zv;
-                p[d] = zv;
-                rz += rv * zv;
-                rr += rv * rv;
-                ff += f[d] * f[d];
-            }
+            init_node<BLOCK>(I, lane, K, diag, f, r, z, p, dinv, rz, rr, ff, err);
         }
         const double b_rz = block_reduce(rz, sh), b_rr = block_reduce(rr, sh), b_ff = block_reduce(ff, sh);
         if (threadIdx.x == 0) {
@@ -449,6 +526,7 @@ __global__ void __launch_bounds__(kPcgThreads) pcgb_spmv_kernel(int64_t n_seg, c
 
 // x += alpha_i p, r -= alpha_i q, z = Dinv r on the live instances; last
 // block: beta_i, residuals, convergence, count of live instances
+template <bool BLOCK>
 __global__ void __launch_bounds__(kPcgThreads) pcgb_update_kernel(int64_t n_seg, const int64_t *seg_row,
                                                                   const int32_t *seg_inst, const int32_t *inst_seg,
                                                                   int n_inst, double *x, double *r, double *z,
@@ -464,15 +542,9 @@ __global__ void __launch_bounds__(kPcgThreads) pcgb_update_kernel(int64_t n_seg,
         if (st.done) continue;
         const double alpha = st.alpha;
         double rz = 0.0, rr = 0.0;
-        for (int64_t i = 3 * seg_row[s] + threadIdx.x; i < 3 * seg_row[s + 1]; i += blockDim.x) {
-            x[i] = fma(alpha, p[i], x[i]);
-            const double rv = fma(-alpha, q[i], r[i]);
-            const double zv = dinv[i] * rv;
-            r[i] = rv;
-            z[i] = zv;
-            rz = fma(rv, zv, rz);
-            rr = fma(rv, rv, rr);
-        }
+        const int64_t u0 = BLOCK ? seg_row[s] : 3 * seg_row[s], u1 = BLOCK ? seg_row[s + 1] : 3 * seg_row[s + 1];
+        for (int64_t i = u0 + threadIdx.x; i < u1; i += blockDim.x)
+            update_unit<BLOCK>(i, alpha, x, r, z, p, q, dinv, rz, rr);
         const double b_rz = block_reduce(rz, sh), b_rr = block_reduce(rr, sh);
         if (threadIdx.x == 0) {
             part[s] = b_rz;
@@ -635,6 +707,21 @@ extern "C" rpim_status rpim_apply_penalty_alpha(rpim_pattern *p, double *K, doub
     return apply_penalty(p, K, f, m, dofs, values, 0.0, alpha, nullptr, (cudaStream_t)stream);
 }
 
+extern "C" rpim_status rpim_pattern_set_precond(rpim_pattern *p, int32_t kind)
+{
+    if (!p || (kind != RPIM_PRECOND_JACOBI && kind != RPIM_PRECOND_BLOCK_JACOBI))
+        return fail(RPIM_E_ARG, "unknown preconditioner");
+    p->precond = kind;
+    return RPIM_OK;
+}
+
+extern "C" rpim_status rpim_pattern_get_precond(const rpim_pattern *p, int32_t *kind)
+{
+    if (!p || !kind) return fail(RPIM_E_ARG, "null argument");
+    *kind = p->precond;
+    return RPIM_OK;
+}
+
 extern "C" rpim_status rpim_solve_pcg(rpim_pattern *p, const double *K, const double *f, double *u, double rtol,
                                       int32_t max_iter, int32_t *iters, double *relres, rpim_stream_t stream)
 {
@@ -643,13 +730,15 @@ extern "C" rpim_status rpim_solve_pcg(rpim_pattern *p, const double *K, const do
     p->stream = s;
     const int64_t n = 3 * p->n_nodes;
     const int nb = std::max(1, p->sm_count * 4);
-    const int64_t need = 5 * n + 3 * (int64_t)nb;
+    const bool block = p->precond == RPIM_PRECOND_BLOCK_JACOBI;
+    const int64_t nd = block ? 3 * n : n;   // preconditioner: 3x3 inverses or diagonal inverses
+    const int64_t need = 4 * n + nd + 3 * (int64_t)nb;
     if (p->ws.doubles < need) {
         dfree(p->ws.buf, s);
         RPIM_CHECK(dalloc(&p->ws.buf, need, s));
         p->ws.doubles = need;
     }
-    double *r = p->ws.buf, *z = r + n, *pp = z + n, *q = pp + n, *dinv = q + n, *part = dinv + n;
+    double *r = p->ws.buf, *z = r + n, *pp = z + n, *q = pp + n, *dinv = q + n, *part = dinv + nd;
     PcgState hs{};
     hs.rtol = rtol;
     hs.max_iter = max_iter;
@@ -657,15 +746,18 @@ extern "C" rpim_status rpim_solve_pcg(rpim_pattern *p, const double *K, const do
     static_assert(sizeof(PcgState) <= 16 * sizeof(double), "state fits the scalar block");
     RPIM_CUDA(cudaMemcpyAsync(st, &hs, sizeof hs, cudaMemcpyHostToDevice, s));
     const int tpb = kPcgThreads;
-    launch("pcg_init", pcg_init_kernel, nb, tpb, 0, s, p->n_nodes, p->rowptr, p->cols, K, p->diag, f, u, r, z, pp, dinv, part, st, p->err);
+    launch("pcg_init", block ? pcg_init_kernel<true> : pcg_init_kernel<false>, nb, tpb, 0, s, p->n_nodes, p->rowptr,
+           p->cols, K, p->diag, f, u, r, z, pp, dinv, part, st, p->err);
     RPIM_CUDA(cudaGetLastError());
+    const int64_t nu = block ? p->n_nodes : n;   // units of the update kernel
     const int chunk = 32;
     int it = 0;
     ChunkGraph graph;
     auto issue = [&](cudaStream_t cs) {
         for (int k = 0; k < chunk; k++) {
             launch("pcg_spmv", pcg_spmv_kernel, nb, tpb, 0, cs, p->n_nodes, p->rowptr, p->cols, K, pp, q, part, st);
-            launch("pcg_update", pcg_update_kernel, nb, tpb, 0, cs, n, u, r, z, pp, q, dinv, part, st);
+            launch("pcg_update", block ? pcg_update_kernel<true> : pcg_update_kernel<false>, nb, tpb, 0, cs, nu, u,
+                   r, z, pp, q, dinv, part, st);
             launch("pcg_direction", pcg_direction_kernel, nb, tpb, 0, cs, n, z, pp, st);
         }
     };
@@ -733,13 +825,15 @@ extern "C" rpim_status rpim_solve_pcg_batched(rpim_pattern *p, const double *K, 
     const int ni = p->n_inst;
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(ns, (int64_t)p->sm_count * 4));
     const int64_t inst_doubles = (ni * (int64_t)sizeof(PcgInst) + sizeof(PcgBatch) + 7) / 8;
-    const int64_t need = 5 * n + 3 * ns + inst_doubles;
+    const bool block = p->precond == RPIM_PRECOND_BLOCK_JACOBI;
+    const int64_t nd = block ? 3 * n : n;
+    const int64_t need = 4 * n + nd + 3 * ns + inst_doubles;
     if (p->ws.doubles < need) {
         dfree(p->ws.buf, s);
         RPIM_CHECK(dalloc(&p->ws.buf, need, s));
         p->ws.doubles = need;
     }
-    double *r = p->ws.buf, *z = r + n, *pp = z + n, *q = pp + n, *dinv = q + n, *part = dinv + n;
+    double *r = p->ws.buf, *z = r + n, *pp = z + n, *q = pp + n, *dinv = q + n, *part = dinv + nd;
     PcgBatch *bst = (PcgBatch *)(part + 3 * ns);
     PcgInst *inst = (PcgInst *)(bst + 1);
     static_assert(sizeof(PcgBatch) % 8 == 0 && sizeof(PcgInst) % 8 == 0, "8-byte state records");
@@ -749,7 +843,8 @@ extern "C" rpim_status rpim_solve_pcg_batched(rpim_pattern *p, const double *K, 
     hb.active = ni;
     RPIM_CUDA(cudaMemcpyAsync(bst, &hb, sizeof hb, cudaMemcpyHostToDevice, s));
     const int tpb = kPcgThreads;
-    launch("pcgb_init", pcgb_init_kernel, nb, tpb, 0, s, ns, (const int64_t *)p->seg_row,
+    launch("pcgb_init", block ? pcgb_init_kernel<true> : pcgb_init_kernel<false>, nb, tpb, 0, s, ns,
+           (const int64_t *)p->seg_row,
            (const int32_t *)p->inst_seg, ni, (const int64_t *)p->rowptr, (const int32_t *)p->cols, K,
            (const int64_t *)p->diag, f, (const double *)u, r, z, pp, dinv, part, inst, bst, p->err);
     RPIM_CUDA(cudaGetLastError());
@@ -761,7 +856,8 @@ extern "C" rpim_status rpim_solve_pcg_batched(rpim_pattern *p, const double *K, 
             launch("pcgb_spmv", pcgb_spmv_kernel, nb, tpb, 0, cs, ns, (const int64_t *)p->seg_row,
                    (const int32_t *)p->seg_inst, (const int32_t *)p->inst_seg, ni, (const int64_t *)p->rowptr,
                    (const int32_t *)p->cols, K, (const double *)pp, q, part, inst, bst);
-            launch("pcgb_update", pcgb_update_kernel, nb, tpb, 0, cs, ns, (const int64_t *)p->seg_row,
+            launch("pcgb_update", block ? pcgb_update_kernel<true> : pcgb_update_kernel<false>, nb, tpb, 0, cs, ns,
+                   (const int64_t *)p->seg_row,
                    (const int32_t *)p->seg_inst, (const int32_t *)p->inst_seg, ni, u, r, z, (const double *)pp,
                    (const double *)q, (const double *)dinv, part, inst, bst);
             launch("pcgb_direction", pcgb_direction_kernel, nb, tpb, 0, cs, ns, (const int64_t *)p->seg_row,

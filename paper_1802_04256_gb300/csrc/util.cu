@@ -41,6 +41,7 @@ struct LaunchRecord {
     cudaEvent_t a, b;
 };
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_device_allocs{0};
 std::atomic<int> g_profile{0};
 std::mutex g_mu;
 std::vector<LaunchRecord> g_pending;
@@ -74,6 +75,8 @@ int64_t launch_begin(const char *name, cudaStream_t s)
 bool profiling_on() { return g_profile.load() != 0; }
 
 void add_launches(int64_t n) { g_launches.fetch_add(n); }
+
+void note_device_alloc() { g_device_allocs.fetch_add(1); }
 
 int64_t launch_count() { return g_launches.load(); }
 
@@ -225,13 +228,115 @@ rpim_status exclusive_scan32(int32_t *data, int64_t n, int64_t *tmp, cudaStream_
 }
 
 // ---------------------------------------------------------------------------
+// Stable LSD radix sort of (key, value) pairs, 8-bit digits from bit 0 up to
+// `bits`. Every pass: the digit histogram of every tile of kSortTile
+// elements; an exclusive scan of the histograms in digit-major order (the
+// first output slot of every (digit, tile)); a scatter in which an element's
+// place among the equal digits of its tile follows its position (warp
+// match, per-warp counts, running counts per round), so equal keys keep
+// their input order.
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortTile = 16 * kSortThreads;
+
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t *keys, int64_t n, int shift,
+                                                                  int64_t *hist)
+{
+    __shared__ int cnt[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    const int64_t b0 = (int64_t)blockIdx.x * kSortTile, b1 = min(n, b0 + kSortTile);
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) atomicAdd(&cnt[(keys[i] >> shift) & 255], 1);
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * gridDim.x + blockIdx.x] = cnt[d];
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const uint64_t *kin, const int32_t *vin,
+                                                                     int64_t n, int shift, const int64_t *off,
+                                                                     uint64_t *kout, int32_t *vout)
+{
+    __shared__ int base[256];                 // elements of each digit placed by earlier rounds
+    __shared__ int wcnt[kSortWarps][256];     // this round's count of each digit per warp
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) base[d] = 0;
+    const int64_t b0 = (int64_t)blockIdx.x * kSortTile, b1 = min(n, b0 + kSortTile);
+    for (int64_t r0 = b0; r0 < b1; r0 += kSortThreads) {
+        for (int i = threadIdx.x; i < kSortWarps * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        const int64_t i = r0 + threadIdx.x;
+        const bool valid = i < b1;
+        uint64_t k = 0;
+        int32_t v = 0;
+        int dig = 256;   // past the digits: lanes without an element
+        if (valid) {
+            k = kin[i];
+            v = vin[i];
+            dig = (int)((k >> shift) & 255);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, dig);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && lane == __ffs(peers) - 1) wcnt[w][dig] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int before = 0;
+            for (int ww = 0; ww < w; ww++) before += wcnt[ww][dig];
+            const int64_t pos = off[(int64_t)dig * gridDim.x + blockIdx.x] + base[dig] + before + rank;
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+            int t = 0;
+            for (int ww = 0; ww < kSortWarps; ww++) t += wcnt[ww][d];
+            base[d] += t;
+        }
+        __syncthreads();
+    }
+}
+
+rpim_status radix_sort_pairs(uint64_t *keys, int32_t *vals, int64_t n, int bits, cudaStream_t s)
+{
+    if (n <= 1 || bits <= 0) return RPIM_OK;
+    const int64_t nb = (n + kSortTile - 1) / kSortTile;
+    const int64_t nh = 256 * nb;
+    uint64_t *k2 = nullptr;
+    int32_t *v2 = nullptr;
+    int64_t *hist = nullptr, *tmp = nullptr;
+    rpim_status st = dalloc(&k2, n, s);
+    if (st == RPIM_OK) st = dalloc(&v2, n, s);
+    if (st == RPIM_OK) st = dalloc(&hist, nh + 1, s);
+    if (st == RPIM_OK) st = dalloc(&tmp, scan_tmp_size(nh), s);
+    uint64_t *ka = keys, *kb = k2;
+    int32_t *va = vals, *vb = v2;
+    int passes = 0;
+    for (int shift = 0; shift < bits && st == RPIM_OK; shift += 8, passes++) {
+        launch("radix_hist", radix_hist_kernel, (unsigned)nb, kSortThreads, 0, s, (const uint64_t *)ka, n, shift, hist);
+        st = exclusive_scan(hist, nh, tmp, s);
+        if (st != RPIM_OK) break;
+        launch("radix_scatter", radix_scatter_kernel, (unsigned)nb, kSortThreads, 0, s, (const uint64_t *)ka,
+               (const int32_t *)va, n, shift, (const int64_t *)hist, kb, vb);
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (st == RPIM_OK && cudaGetLastError() != cudaSuccess) st = fail(RPIM_E_CUDA, "radix sort launch");
+    if (st == RPIM_OK && (passes & 1)) {   // the result sits in the scratch buffers
+        cudaError_t e = cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vals, va, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "radix sort copy");
+    }
+    dfree(k2, s); dfree(v2, s); dfree(hist, s); dfree(tmp, s);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
 // device error word
 // ---------------------------------------------------------------------------
 static const char *status_name(int c)
 {
     switch (c) {
     case RPIM_E_ARG: return "invalid argument";
-    case RPIM_E_SUPPORT: return "support size out of range";
+    case RPIM_E_SUPPORT: return "support size out of range, or a node in no support";
     case RPIM_E_SINGULAR: return "singular moment problem";
     case RPIM_E_NONFINITE: return "non-finite value";
     case RPIM_E_NOCONV: return "no convergence";
@@ -542,6 +647,21 @@ extern "C" rpim_status rpim_kernel_series_info(double alpha_c, double alpha_s, d
 }
 
 extern "C" int64_t rpim_kernel_launches(void) { return rpim::g_launches.load(); }
+
+extern "C" int64_t rpim_device_allocations(void) { return rpim::g_device_allocs.load(); }
+
+extern "C" rpim_status rpim_pool_used_bytes(int64_t *bytes)
+{
+    if (!bytes) return rpim::fail(RPIM_E_ARG, "null argument");
+    int dev = 0;
+    RPIM_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    RPIM_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t used = 0;
+    RPIM_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    *bytes = (int64_t)used;
+    return RPIM_OK;
+}
 
 extern "C" rpim_status rpim_profile_enable(int32_t on)
 {

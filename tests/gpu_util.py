@@ -10,6 +10,12 @@ def t(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
+def faces(p):
+    """The face tractions of a gen.Problem as device tensors (lo, hi, axis,
+    coef) for Pattern.add_traction."""
+    return (t(p.face_lo), t(p.face_hi), t(p.face_axis, torch.int8), t(p.face_coef))
+
+
 class GpuRun:
     """Pattern + assembly (+ loads) of one problem on the GPU."""
 
@@ -19,8 +25,8 @@ class GpuRun:
         self.E, self.nu = t(p.E), t(p.nu)
         self.body = t(p.body) if np.any(p.body) else None
         self.K, self.f = self.pat.assemble(self.E, self.nu, self.body)
-        if loads and len(p.load_xyz):
-            self.pat.add_point_loads(t(p.load_xyz), t(p.load_force), self.f)
+        if loads and p.n_faces:
+            self.pat.add_traction(*faces(p), self.f)
         torch.cuda.synchronize()
 
     def host_csr(self):
@@ -30,11 +36,11 @@ class GpuRun:
     def host_K(self):
         return self.K.cpu().numpy()
 
-    def solve(self, rtol=1e-10, max_iter=200000, scale=1e8):
+    def solve(self, rtol=1e-10, max_iter=200000, scale=1e8, precond="jacobi"):
         K = self.K.clone()
         f = self.f.clone()
         alpha = self.pat.apply_penalty(K, f, t(self.p.fixed_dofs, torch.int64), t(self.p.fixed_vals), scale)
-        u, it, rr = self.pat.solve_pcg(K, f, rtol=rtol, max_iter=max_iter)
+        u, it, rr = self.pat.solve_pcg(K, f, rtol=rtol, max_iter=max_iter, precond=precond)
         return u, it, rr, alpha, K, f
 
 

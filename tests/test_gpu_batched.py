@@ -15,7 +15,7 @@ import torch
 
 import gen
 import oracle
-from gpu_util import GpuRun, bsr_matvec, t
+from gpu_util import faces, GpuRun, bsr_matvec, t
 
 import paper_1802_04256_gb300 as R
 
@@ -34,10 +34,8 @@ def batch():
     E = t(np.concatenate([p.E for p in probs]))
     nu = t(np.concatenate([p.nu for p in probs]))
     K, f = pat.assemble(E, nu)
-    lx = np.concatenate([p.load_xyz for p in probs])
-    lf = np.concatenate([p.load_force for p in probs])
-    li = np.concatenate([np.full(len(p.load_xyz), k, np.int32) for k, p in enumerate(probs)])
-    pat.add_point_loads(t(lx), t(lf), f, inst=t(li, torch.int32))
+    fl, fh, fa, fc, fi = gen.concat_faces(probs)
+    pat.add_traction(t(fl), t(fh), t(fa, torch.int8), t(fc), f, inst=t(fi, torch.int32))
     torch.cuda.synchronize()
     singles = [GpuRun(p) for p in probs]
     return probs, pat, offs, K, f, singles
@@ -100,7 +98,7 @@ def test_single_instance_batch_is_bitwise_plain():
     g = GpuRun(p)
     pat, offs = R.Pattern.batched([p])
     K, f = pat.assemble(t(p.E), t(p.nu))
-    pat.add_point_loads(t(p.load_xyz), t(p.load_force), f, inst=t(np.zeros(len(p.load_xyz), np.int32), torch.int32))
+    pat.add_traction(*faces(p), f, inst=t(np.zeros(p.n_faces, np.int32), torch.int32))
     assert torch.equal(K, g.K)
     assert torch.equal(f, g.f)
 
@@ -189,14 +187,34 @@ def test_batched_pcg_one_instance_matches_plain():
     assert torch.linalg.norm(u2 - u1) <= 1e-9 * torch.linalg.norm(u1)
 
 
+def test_batched_block_jacobi_equals_per_instance(batch):
+    """The batched solver with the 3x3 block-Jacobi preconditioner gives every
+    instance the iterations and solution of its own plain block-Jacobi
+    solve."""
+    probs, pat, offs, K, f, singles = batch
+    dofs = np.concatenate([p.fixed_dofs + 3 * offs[k] for k, p in enumerate(probs)])
+    vals = np.concatenate([p.fixed_vals for p in probs])
+    Kb, fb = K.clone(), f.clone()
+    pat.apply_penalty(Kb, fb, t(dofs, torch.int64), t(vals))
+    ub, its, rrs = pat.solve_pcg_batched(Kb, fb, rtol=1e-12, precond="block")
+    pat.set_precond("jacobi")
+    for k, g in enumerate(singles):
+        u1, it1, rr1, a1, K1, f1 = g.solve(rtol=1e-12, precond="block")
+        d = torch.linalg.norm(ub[3 * offs[k]:3 * offs[k + 1]] - u1) / torch.linalg.norm(u1)
+        assert abs(its[k] - it1) <= 2 and d <= 1e-9, (k, its[k], it1, float(d))
+
+
 def test_instance_ids_checked(batch):
     probs, pat, offs, K, f, singles = batch
     f2 = f.clone()
     with pytest.raises(R.RpimError):
-        pat.add_point_loads(t(probs[0].load_xyz), t(probs[0].load_force), f2)
-    bad = np.full(len(probs[0].load_xyz), len(probs), np.int32)
+        pat.add_traction(*faces(probs[0]), f2)
+    bad = np.full(probs[0].n_faces, len(probs), np.int32)
     with pytest.raises(R.RpimError):
-        pat.add_point_loads(t(probs[0].load_xyz), t(probs[0].load_force), f2, inst=t(bad, torch.int32))
+        pat.add_traction(*faces(probs[0]), f2, inst=t(bad, torch.int32))
+    lx = probs[0].xyz[:3]
+    with pytest.raises(R.RpimError):
+        pat.add_point_loads(t(lx), t(np.ones((3, 3))), f2, inst=t(np.full(3, len(probs), np.int32), torch.int32))
     pts = probs[0].xyz[:5]
     with pytest.raises(R.RpimError):
         pat.stress(torch.zeros_like(f2), t(pts), t(np.ones(5)), t(np.full(5, 0.3)),

@@ -89,6 +89,8 @@ def test_zero_length_calls_are_no_ops():
     g = GpuRun(p)
     f = g.f.clone()
     g.pat.add_point_loads(t(np.zeros((0, 3))), t(np.zeros((0, 3))), f)
+    g.pat.add_traction(t(np.zeros((0, 3))), t(np.zeros((0, 3))), t(np.zeros(0, np.int8), torch.int8),
+                       t(np.zeros((0, 3, 6))), f)
     assert torch.equal(f, g.f)
     s = g.pat.stress(torch.zeros_like(f), t(np.zeros((0, 3))), t(np.zeros(0)), t(np.zeros(0)))
     assert s.shape == (0, 6)

@@ -70,3 +70,20 @@ def test_non_finite_coordinate():
     xyz = p.xyz.copy()
     xyz[3, 1] = np.nan
     assert _status(lambda: R.Pattern(t(xyz), t(p.cell_lo), t(p.cell_hi), 2.5, 4.0, 1.03, 0.25)) == 7
+
+
+def test_node_that_no_point_reaches_is_rejected_by_the_build():
+    """A node whose coordinates lie far from every integration point (here
+    moved out of the domain while its cell stays in place) appears in no
+    support, so its row of K would be empty and K singular: the build reports
+    RPIM_E_SUPPORT with the node's index, before any stage reads the row."""
+    p = gen.cube_config(n=5)
+    xyz = p.xyz.copy()
+    xyz[0] = [3.0, 3.0, 3.0]
+    with pytest.raises(R.RpimError) as e:
+        R.Pattern(t(xyz), t(p.cell_lo), t(p.cell_hi), 2.5, 4.0, 1.03, 0.25)
+    assert e.value.status == 4
+    assert "index 0" in str(e.value)
+    # the same cloud with the node in place builds and assembles
+    g = GpuRun(p)
+    assert g.pat.info.n_nodes == p.n_nodes

@@ -50,7 +50,7 @@ def test_sampled_rows_vs_oracle(beam):
         near = np.nonzero(((pts - p.xyz[I]) ** 2).sum(1) <= rs2 * 1.01)[0]
         sel = [k for k in near if I in oracle.support(p.xyz, pts[k], rs2)]
         m = oracle.assemble(p.xyz, pts[sel], wj[sel], p.E[sel], p.nu[sel], p.alpha_s, p.alpha_c,
-                            p.q, p.h)
+                            p.q, p.h, rows=[I])
         assert np.array_equal(m.cols[m.rowptr[I]:m.rowptr[I + 1]], cols[rowptr[I]:rowptr[I + 1]])
         d = np.abs(m.vals[m.rowptr[I]:m.rowptr[I + 1]] - K[rowptr[I]:rowptr[I + 1]]).max() / kmax
         print("row %d: %d points, rel %.3e" % (I, len(sel), d))

@@ -22,7 +22,7 @@ import torch
 import gen
 import oracle
 import paper_1802_04256_gb300 as R
-from gpu_util import t
+from gpu_util import faces, t
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +60,7 @@ def _block():
 def _gpu_setup(p):
     pat = R.Pattern.from_problem(p)
     f_ext = torch.zeros(3 * p.n_nodes, dtype=torch.float64, device="cuda")
-    pat.add_point_loads(t(p.load_xyz), t(p.load_force), f_ext)
+    pat.add_traction(*faces(p), f_ext)
     alpha = 1e8 * 4e3
     return pat, f_ext, alpha
 
@@ -79,7 +79,7 @@ def test_autograd_gradient_matches_oracle_adjoint():
     # oracle: its own assembly, dense solve, adjoint and gradient
     pts, wj = oracle.gauss_points(p.cell_lo, p.cell_hi)
     fo = np.zeros(3 * p.n_nodes)
-    oracle.point_loads(p.xyz, p.load_xyz, p.load_force, p.alpha_s, p.alpha_c, p.q, p.h, fo)
+    oracle.traction(p.xyz, p.face_lo, p.face_hi, p.face_axis, p.face_coef, p.alpha_s, p.alpha_c, p.q, p.h, fo)
     m = oracle.assemble(p.xyz, pts, wj, p.E, p.nu, p.alpha_s, p.alpha_c, p.q, p.h)
     vals = m.vals.ravel().copy()
     f = m.f + fo

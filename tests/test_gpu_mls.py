@@ -20,7 +20,7 @@ import torch
 
 import gen
 import oracle
-from gpu_util import bsr_matvec, t
+from gpu_util import faces, bsr_matvec, t
 
 import paper_1802_04256_gb300 as R
 
@@ -48,8 +48,8 @@ class MlsRun:
         self.E, self.nu = t(p.E), t(p.nu)
         self.body = t(p.body) if np.any(p.body) else None
         self.K, self.f = self.pat.assemble(self.E, self.nu, self.body)
-        if len(p.load_xyz):
-            self.pat.add_point_loads(t(p.load_xyz), t(p.load_force), self.f)
+        if p.n_faces:
+            self.pat.add_traction(*faces(p), self.f)
         torch.cuda.synchronize()
 
 

@@ -22,7 +22,7 @@ import torch
 
 import gen
 import oracle
-from gpu_util import GpuRun, bsr_matvec, t
+from gpu_util import GpuRun, bsr_matvec, faces, t
 
 import paper_1802_04256_gb300 as R
 
@@ -119,7 +119,7 @@ def test_K_and_f_vs_oracle(case):
         for I in (0, p.n_nodes // 2, p.n_nodes - 1):
             sel = [k for k in range(len(pts)) if I in m.sidx[m.soff[k]:m.soff[k + 1]]]
             ml = oracle.assemble(p.xyz, pts[sel], wj[sel], p.E[sel], p.nu[sel], p.alpha_s, p.alpha_c,
-                                 p.q, p.h, kind="ld")
+                                 p.q, p.h, kind="ld", rows=[I])
             sl = slice(rowptr[I], rowptr[I + 1])
             e64 = max(e64, np.abs(m.vals[sl] - ml.vals[ml.rowptr[I]:ml.rowptr[I + 1]]).max() / kmax)
             dld = max(dld, np.abs(K[sl] - ml.vals[ml.rowptr[I]:ml.rowptr[I + 1]]).max() / kmax)
@@ -183,6 +183,26 @@ def test_pcg_solution_vs_oracle(case):
     assert np.linalg.norm(r) <= 2e-12 * np.linalg.norm(fh) + floor
 
 
+def test_block_jacobi_pcg_vs_oracle(case):
+    """The 3x3 block-Jacobi preconditioner on the same K: the iteration
+    counts of the two implementations agree to within two, the solutions to
+    TOL_U, and it converges in fewer iterations than scalar Jacobi."""
+    p, g, m = case
+    u, it, rr, alpha, K, f = g.solve(rtol=1e-12, precond="block")
+    assert rr <= 1e-12
+    rowptr, cols = g.host_csr()
+    Kh = K.cpu().numpy().ravel()
+    fh = f.cpu().numpy()
+    uo, ito, rro, st = oracle.pcg(p.n_nodes, rowptr, cols, Kh, fh, rtol=1e-12, precond="block")
+    assert st == 0
+    d = np.linalg.norm(u.cpu().numpy() - uo) / np.linalg.norm(uo)
+    uj, itj, rrj, _, _, _ = g.solve(rtol=1e-12, precond="jacobi")
+    print("block-Jacobi PCG: iterations gpu %d oracle %d (Jacobi %d), u rel diff %.3e" % (it, ito, itj, d))
+    assert abs(it - ito) <= 2
+    assert d < TOL_U
+    assert it <= itj
+
+
 def test_full_pipeline_u_vs_oracle(case):
     """u from the GPU pipeline against u from the oracle's own K and f."""
     p, g, m = case
@@ -207,12 +227,83 @@ def test_stress_vs_oracle(case):
     assert d < 1e-6
 
 
-def test_point_loads_vs_oracle():
+def test_traction_vs_oracle():
+    """The cantilever's parabolic end shear: the library integrates the face
+    rectangles on the device, the oracle in its own code, both from the same
+    face description. The two load vectors agree to the shape functions'
+    accuracy, and the resultant is the closed-form integral, -P along z."""
     p = gen.cantilever_config(shape=(33, 5, 5))
     pat = R.Pattern.from_problem(p)
     f = torch.zeros(3 * p.n_nodes, dtype=torch.float64, device="cuda")
-    pat.add_point_loads(t(p.load_xyz), t(p.load_force), f)
+    pat.add_traction(*faces(p), f)
+    fg = f.cpu().numpy()
     fo = np.zeros(3 * p.n_nodes)
-    oracle.point_loads(p.xyz, p.load_xyz, p.load_force, p.alpha_s, p.alpha_c, p.q, p.h, fo)
-    assert np.abs(f.cpu().numpy() - fo).max() < 1e-8 * np.abs(fo).max()
-    assert abs(f.cpu().numpy().reshape(-1, 3).sum(0)[2] + 1.0) < 1e-12
+    oracle.traction(p.xyz, p.face_lo, p.face_hi, p.face_axis, p.face_coef, p.alpha_s, p.alpha_c, p.q, p.h, fo,
+                    "ld")
+    d = np.abs(fg - fo).max() / np.abs(fo).max()
+    print("traction vs extended oracle: rel %.3e" % d)
+    assert d < 1e-9
+    assert abs(fg.reshape(-1, 3).sum(0)[2] + 1.0) < 1e-12
+
+
+def test_traction_on_every_axis_vs_oracle():
+    """Faces normal to x, y and z on the jittered cube with full quadratic
+    traction polynomials (every coefficient set): exercises the tangent-axis
+    order of both implementations; load vectors agree and the resultant is
+    the closed-form integral of the polynomials."""
+    p = gen.cube_config(jitter=0.2, seed=7)
+    fl, fh, fa, fc = _all_axis_faces(p)
+    pat = R.Pattern.from_problem(p)
+    f = torch.zeros(3 * p.n_nodes, dtype=torch.float64, device="cuda")
+    pat.add_traction(t(fl), t(fh), t(fa, torch.int8), t(fc), f)
+    fg = f.cpu().numpy()
+    fo = np.zeros(3 * p.n_nodes)
+    oracle.traction(p.xyz, fl, fh, fa, fc, p.alpha_s, p.alpha_c, p.q, p.h, fo, "ld")
+    d = np.abs(fg - fo).max() / np.abs(fo).max()
+    print("traction on x, y, z faces vs extended oracle: rel %.3e" % d)
+    assert d < 1e-9
+    want = sum(_face_force(fl[k], fh[k], fa[k], fc[k]) for k in range(len(fl)))
+    assert np.abs(fg.reshape(-1, 3).sum(0) - want).max() < 1e-12 * np.abs(want).max()
+
+
+def _all_axis_faces(p):
+    """Two faces on each of x = 0, y = 1 and z = 1 of the unit cube, with seeded
+    quadratic traction polynomials."""
+    lo, hi, ax = [], [], []
+    for a, side in ((0, 0.0), (1, 1.0), (2, 1.0)):
+        for r in ((0.0, 0.5, 0.1, 0.7), (0.5, 1.0, 0.3, 1.0)):
+            l, h = np.zeros(3), np.zeros(3)
+            l[a] = h[a] = side
+            u, v = [b for b in range(3) if b != a]
+            l[u], h[u], l[v], h[v] = r
+            lo.append(l)
+            hi.append(h)
+            ax.append(a)
+    coef = gen.uniform(7, 90, 6 * 18, -5.0, 5.0).reshape(6, 3, 6)
+    return np.array(lo), np.array(hi), np.array(ax, np.int8), coef
+
+
+def _face_force(lo, hi, a, coef):
+    """Exact integral of the traction polynomial over one face rectangle."""
+    u, v = [b for b in range(3) if b != a]
+    I = lambda k, b: (hi[b] ** (k + 1) - lo[b] ** (k + 1)) / (k + 1)
+    mono = np.array([I(0, u) * I(0, v), I(1, u) * I(0, v), I(0, u) * I(1, v), I(2, u) * I(0, v),
+                     I(1, u) * I(1, v), I(0, u) * I(2, v)])
+    return coef @ mono
+
+
+def test_point_loads_vs_oracle():
+    """Forces at arbitrary points (a lower-level entry than the tractions)."""
+    p = gen.cantilever_config(shape=(33, 5, 5))
+    pat = R.Pattern.from_problem(p)
+    rng = np.random.default_rng(11)
+    x = rng.uniform([0.1, 0.05, 0.05], [7.9, 0.95, 0.95], size=(40, 3))
+    F = rng.standard_normal((40, 3))
+    f = torch.zeros(3 * p.n_nodes, dtype=torch.float64, device="cuda")
+    pat.add_point_loads(t(x), t(F), f)
+    fo = np.zeros(3 * p.n_nodes)
+    oracle.point_loads(p.xyz, x, F, p.alpha_s, p.alpha_c, p.q, p.h, fo, "ld")
+    d = np.abs(f.cpu().numpy() - fo).max() / np.abs(fo).max()
+    print("point loads vs extended oracle: rel %.3e" % d)
+    assert d < 1e-9
+    assert np.abs(f.cpu().numpy().reshape(-1, 3).sum(0) - F.sum(0)).max() < 1e-12 * np.abs(F).sum()

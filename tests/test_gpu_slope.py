@@ -86,7 +86,7 @@ def test_sampled_rows_vs_oracle(slope):
         rows = {}
         for kind in ("f64", "ld"):
             m = oracle.assemble(p.xyz, pts[sel], wj[sel], p.E[sel], p.nu[sel], p.alpha_s, p.alpha_c, p.q, p.h,
-                                kind=kind)
+                                kind=kind, rows=[I])
             assert np.array_equal(m.cols[m.rowptr[I]:m.rowptr[I + 1]], mc)
             rows[kind] = m.vals[m.rowptr[I]:m.rowptr[I + 1]].reshape(-1, 9)
         e64 = max(e64, np.abs(rows["f64"] - rows["ld"]).max() / kmax)
