@@ -413,11 +413,12 @@ def _solve(inp, stream, peak_gflops, precond="jacobi", fixed_iters=0, tip=None, 
     return out
 
 
-def _solves(inp, stream, peak_gflops, args, tip=None):
+def _solves(inp, stream, peak_gflops, args, tip=None, preconds=None):
     """The full solve with each preconditioner."""
     if args.no_solve:
         return None
-    return {pc: _solve(inp, stream, peak_gflops, pc, args.solve_iters, tip) for pc in args.precond.split(",")}
+    pcs = preconds or args.precond.split(",")
+    return {pc: _solve(inp, stream, peak_gflops, pc, args.solve_iters, tip) for pc in pcs}
 
 
 # --------------------------------------------------------------------------- MLS variant
@@ -443,7 +444,7 @@ def _mls(inp, stream, peak_gflops, steps=3):
 
 
 # --------------------------------------------------------------------------- other workloads
-def _config(name, dev, stream, peak_gflops, args, steps, warm, cpu_s, tip=None):
+def _config(name, dev, stream, peak_gflops, args, steps, warm, cpu_s, tip=None, preconds=None):
     """One workload: assembly pts/s with its roofline, full solves/s, and the
     oracle on the host cores (all cores and one thread)."""
     desc, make = WORKLOADS[name]
@@ -459,7 +460,7 @@ def _config(name, dev, stream, peak_gflops, args, steps, warm, cpu_s, tip=None):
            "support": {"min": int(nsup.min()), "max": int(nsup.max()), "mean": float(nsup.mean())},
            "nnz_blocks": nnzb,
            "kernel_ms_per_step": {k: round(v[1] / steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
-    out["solve"] = _solves(inp, stream, peak_gflops, args, tip)
+    out["solve"] = _solves(inp, stream, peak_gflops, args, tip, preconds)
     if not args.no_cpu_baseline and cpu_s > 0:
         out["cpu_baseline"] = cpu_baseline(p, cpu_s)
     return out, inp
@@ -670,26 +671,42 @@ def _batched(n_sel, dev, stream, reps=1, warm=1, small_nodes=2000):
     tp.free()
 
     def small_b():
-        pat, K, f = sbat.assemble()
+        ta, (pat, K, f) = timed(sbat.assemble)
+
+        def solve():
+            pat.apply_penalty(K, f, sbat.dofs, sbat.vals)
+            return pat.solve_pcg_batched(K, f, rtol=rtol, max_iter=500000)
+
+        ts, _ = timed(solve)
         pat.free()
+        return ta, ts
 
     def small_s():
+        ta = ts = 0.0
         for d in ssingle:
-            d.step()
+            a, (pat, K, f) = timed(lambda: s_assemble(d))
+            s, _ = timed(lambda: s_solve(pat, K, f, d))
+            pat.free()
+            ta, ts = ta + a, ts + s
+        return ta, ts
 
     small_b(), small_s()
     l0 = R.rpim_kernel_launches()
-    tb = min(timed(small_b)[0] for _ in range(2))
+    tb = min((small_b() for _ in range(2)), key=sum)
     lsb = (R.rpim_kernel_launches() - l0) / 2
     l0 = R.rpim_kernel_launches()
-    tsg = min(timed(small_s)[0] for _ in range(2))
+    tsg = min((small_s() for _ in range(2)), key=sum)
     lss = (R.rpim_kernel_launches() - l0) / 2
     snpts = sbat.npts
     small_out = {"instances": len(small), "n_nodes": int(sum(p.n_nodes for p in small)), "n_points": snpts,
-                 "batched_ms": tb, "per_instance_ms": tsg, "speedup": tsg / tb,
-                 "batched_pts_per_s": snpts / (tb / 1e3), "per_instance_pts_per_s": snpts / (tsg / 1e3),
+                 "assembly": {"batched_ms": tb[0], "per_instance_ms": tsg[0], "speedup": tsg[0] / tb[0],
+                              "batched_pts_per_s": snpts / (tb[0] / 1e3),
+                              "per_instance_pts_per_s": snpts / (tsg[0] / 1e3)},
+                 "solve": {"batched_ms": tb[1], "per_instance_ms": tsg[1], "speedup": tsg[1] / tb[1], "rtol": rtol},
+                 "end_to_end": {"batched_ms": sum(tb), "per_instance_ms": sum(tsg), "speedup": sum(tsg) / sum(tb)},
                  "kernel_launches": {"batched": lsb, "per_instance": lss},
-                 "step": "build pattern + assemble + tractions of every block below %d nodes" % small_nodes}
+                 "step": "every block below %d nodes: build pattern + assemble + tractions (assembly); penalty "
+                         "+ Jacobi-PCG to 1e-10 (solve); both arms warm, best of two" % small_nodes}
     return {"instances": len(sel), "of": len(allp), "selection": "every %d-th block of the 512-block workload"
             % max(1, len(allp) // n_sel), "n_nodes": int(offs[-1]), "n_points": npts,
             "node_range": [int(min(p.n_nodes for p in sel)), int(max(p.n_nodes for p in sel))],
@@ -775,6 +792,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     R.lib()
+    R.rpim_set_row_order(args.row_order == "morton")
     desc, make = WORKLOADS[args.workload]
     p = make()
     inp = Inputs(p, dev)
@@ -851,16 +869,19 @@ def run_ours(args, rank, world, local_rank):
         configs["cube"] = cube
         tip = int(np.nonzero(np.all(np.abs(gen.cantilever_config().nominal - [8.0, 0.5, 0.5]) < 1e-9,
                                     axis=1))[0][0])
-        cant, cinp = _config("cantilever", dev, stream, peak_gflops, args, steps=5, warm=2, cpu_s=5.0, tip=tip)
+        cant, cinp = _config("cantilever", dev, stream, peak_gflops, args, steps=5, warm=2, cpu_s=5.0, tip=tip,
+                             preconds=["jacobi", "block"])
         if cant.get("solve"):
             for s in cant["solve"].values():
                 s["timoshenko"] = 0.20700
         configs["cantilever"] = cant
-        if not args.no_mls:
-            configs["cantilever"]["mls"] = _mls(cinp, stream, peak_gflops)
         del cinp
         back, _ = _config("backanalysis", dev, stream, peak_gflops, args, steps=3, warm=1, cpu_s=4.0)
         configs["backanalysis"] = back
+
+    mls = None
+    if rank == 0 and not args.no_mls:
+        mls = _mls(Inputs(gen.cantilever_config(), dev), stream, peak_gflops)
 
     batched = None
     if rank == 0 and args.batched_instances > 0:
@@ -885,7 +906,7 @@ def run_ours(args, rank, world, local_rank):
                           "nnz_blocks": nnzb, "parallelism": "replicas" if world > 1 else "single GPU"},
                "roofline": roof, "kernel_ms_per_step": kernel_ms, "kernel_time_share": kernel_share,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-               "solve": solve, "configs": configs, "batched": batched, "backanalysis": grad,
+               "solve": solve, "configs": configs, "mls": mls, "batched": batched, "backanalysis": grad,
                "autotune": [{"max_support": a, "warps_per_point": g, "points_per_block": c} for a, g, c in tuned]
                if tuned else None, "bucket_bounds": bounds,
                "fp64_peak_gflops_measured": peak_gflops}
@@ -901,13 +922,16 @@ def main():
     ap.add_argument("--workload", default="slope", choices=["slope", "cantilever"],
                     help="headline workload (the layered slope; the cantilever for small profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="host seconds of the oracle's all-core sample of the headline workload")
     ap.add_argument("--no-solve", action="store_true", help="skip the penalty + PCG measurements")
-    ap.add_argument("--precond", default="jacobi,block",
-                    help="PCG preconditioners to time (comma separated: jacobi, block)")
+    ap.add_argument("--precond", default="jacobi",
+                    help="PCG preconditioners of the headline solve (comma separated: jacobi, block); the "
+                         "cantilever's solve is timed with both")
+    ap.add_argument("--row-order", default="morton", choices=["morton", "node"],
+                    help="order in which the row-owner kernels take their rows (results are bitwise the same)")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-grad", action="store_true", help="skip the back-analysis gradient measurement")
     ap.add_argument("--no-mls", action="store_true", help="skip the MLS-variant assembly measurement")

@@ -34,6 +34,14 @@ rpim_status rpim_probe_fp64_mixed(int32_t repeats, double *gflops);
 rpim_status rpim_kernel_series_info(double alpha_c, double alpha_s, double q, int32_t *pieces,
                                     int32_t *degree, int32_t *fp64_terms, double *max_err);
 
+/* The reciprocal the RPIM shape kernel takes of its pivots and of the
+ * determinant of the pivot tetrahedron (Newton-Raphson from a
+ * single-precision seed): r[i] = 1/d[i] for device arrays d, r of n doubles,
+ * |d[i]| in [2^-126, 2^126] (d and 1/d single-precision normal). For
+ * checking its accuracy against correctly rounded division. Synchronises
+ * `stream`. Errors: RPIM_E_ARG, RPIM_E_CUDA. */
+rpim_status rpim_probe_recip(int64_t n, const double *d, double *r, rpim_stream_t stream);
+
 /* Number of kernels this library has launched since it was loaded. */
 int64_t rpim_kernel_launches(void);
 

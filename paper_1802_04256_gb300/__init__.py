@@ -37,7 +37,7 @@ EXPORTED = [
     "rpim_pattern_get_buckets", "rpim_autotune_buckets", "rpim_set_shape_schedule",
     "rpim_device_allocations", "rpim_pool_used_bytes", "rpim_add_traction", "rpim_add_traction_batched",
     "rpim_add_vector", "rpim_pattern_set_precond", "rpim_pattern_get_precond", "rpim_set_row_order",
-    "rpim_pattern_copy_row_order",
+    "rpim_pattern_copy_row_order", "rpim_probe_recip",
 ]
 
 SHAPE_KINDS = {"rpim": 0, "mls": 1, "shepard": 2}
@@ -131,6 +131,7 @@ def lib():
         "rpim_pattern_get_precond": [vp, C.POINTER(i32)],
         "rpim_set_row_order": [i32],
         "rpim_pattern_copy_row_order": [vp, vp, vp],
+        "rpim_probe_recip": [i64, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -421,6 +422,14 @@ def rpim_probe_dmma(repeats=5) -> float:
     g = C.c_double(0)
     _check(lib().rpim_probe_dmma(repeats, C.byref(g)), "rpim_probe_dmma")
     return g.value
+
+
+def rpim_probe_recip(d, stream=None):
+    """The shape kernel's reciprocal of every entry of d (device, float64)."""
+    r = torch.empty_like(d)
+    _check(lib().rpim_probe_recip(d.numel(), _dev(d, torch.float64), _dev(r, torch.float64), _stream(stream)),
+           "rpim_probe_recip")
+    return r
 
 
 def rpim_kernel_series_info(alpha_c=4.0, alpha_s=2.5, q=1.03):

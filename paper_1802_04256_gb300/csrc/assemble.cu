@@ -455,6 +455,7 @@ using namespace rpim;
 
 extern "C" rpim_status rpim_shape_functions(rpim_pattern *p, double *phi, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_shape_functions");
     if (!p || !phi) return fail(RPIM_E_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;
@@ -500,6 +501,7 @@ static rpim_status assemble_issue(rpim_pattern *p, const double *E, const double
 extern "C" rpim_status rpim_assemble(rpim_pattern *p, const double *E, const double *nu, const double *body,
                                      double *K, double *f, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_assemble");
     if (!p || !E || !nu || !K || !f) return fail(RPIM_E_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;
@@ -514,6 +516,7 @@ extern "C" rpim_status rpim_assemble(rpim_pattern *p, const double *E, const dou
 extern "C" rpim_status rpim_assemble_graphed(rpim_pattern *p, const double *E, const double *nu, const double *body,
                                              double *K, double *f, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_assemble_graphed");
     if (!p || !E || !nu || !K || !f) return fail(RPIM_E_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;
@@ -560,6 +563,7 @@ extern "C" rpim_status rpim_assemble_graphed(rpim_pattern *p, const double *E, c
 extern "C" rpim_status rpim_grad_material(rpim_pattern *p, const double *u, const double *lam, const double *E,
                                           const double *nu, double *dE, double *dnu, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_grad_material");
     if (!p || !u || !lam || !E || !nu || !dE || !dnu) return fail(RPIM_E_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;
@@ -707,6 +711,7 @@ static rpim_status add_point_loads(rpim_pattern *p, int64_t n_pts, const double 
 extern "C" rpim_status rpim_add_point_loads(rpim_pattern *p, int64_t n_pts, const double *xyz,
                                             const double *force, double *f, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_add_point_loads");
     return add_point_loads(p, n_pts, xyz, force, nullptr, f, (cudaStream_t)stream);
 }
 
@@ -714,6 +719,7 @@ extern "C" rpim_status rpim_add_point_loads_batched(rpim_pattern *p, int64_t n_p
                                                     const double *force, const int32_t *inst, double *f,
                                                     rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_add_point_loads_batched");
     if (!inst && n_pts > 0) return fail(RPIM_E_ARG, "inst is null");
     return add_point_loads(p, n_pts, xyz, force, inst, f, (cudaStream_t)stream);
 }
@@ -722,6 +728,7 @@ extern "C" rpim_status rpim_add_traction(rpim_pattern *p, int64_t n_faces, const
                                          const double *face_hi, const int8_t *face_axis, const double *coef,
                                          double *f, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_add_traction");
     return add_traction(p, n_faces, face_lo, face_hi, face_axis, coef, nullptr, f, (cudaStream_t)stream);
 }
 
@@ -729,12 +736,14 @@ extern "C" rpim_status rpim_add_traction_batched(rpim_pattern *p, int64_t n_face
                                                  const double *face_hi, const int8_t *face_axis, const double *coef,
                                                  const int32_t *inst, double *f, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_add_traction_batched");
     if (!inst && n_faces > 0) return fail(RPIM_E_ARG, "inst is null");
     return add_traction(p, n_faces, face_lo, face_hi, face_axis, coef, inst, f, (cudaStream_t)stream);
 }
 
 extern "C" rpim_status rpim_add_vector(rpim_pattern *p, const double *x, double *f, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_add_vector");
     if (!p || !x || !f) return fail(RPIM_E_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;
@@ -768,6 +777,7 @@ static rpim_status stress(rpim_pattern *p, const double *u, int64_t n_pts, const
 extern "C" rpim_status rpim_stress(rpim_pattern *p, const double *u, int64_t n_pts, const double *xyz,
                                    const double *E, const double *nu, double *sigma, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_stress");
     return stress(p, u, n_pts, xyz, nullptr, E, nu, sigma, (cudaStream_t)stream);
 }
 
@@ -775,6 +785,7 @@ extern "C" rpim_status rpim_stress_batched(rpim_pattern *p, const double *u, int
                                            const int32_t *inst, const double *E, const double *nu, double *sigma,
                                            rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_stress_batched");
     if (!inst && n_pts > 0) return fail(RPIM_E_ARG, "inst is null");
     return stress(p, u, n_pts, xyz, inst, E, nu, sigma, (cudaStream_t)stream);
 }

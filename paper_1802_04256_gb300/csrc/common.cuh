@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -23,6 +24,17 @@ rpim_status cuda_fail(cudaError_t e, const char *what);
         cudaError_t e_ = (call);                                \
         if (e_ != cudaSuccess) return ::rpim::cuda_fail(e_, #call); \
     } while (0)
+
+// An NVTX range around one call of the C ABI, named after the call, so that
+// profilers (Nsight Systems, ncu --nvtx) show the pipeline's stages; without
+// a tool attached a push/pop is a no-op call.
+struct StageRange {
+    explicit StageRange(const char *name) { nvtxRangePushA(name); }
+    ~StageRange() { nvtxRangePop(); }
+    StageRange(const StageRange &) = delete;
+    StageRange &operator=(const StageRange &) = delete;
+};
+#define RPIM_STAGE(name) ::rpim::StageRange rpim_stage_range_(name)
 
 #define RPIM_CHECK(st)                       \
     do {                                     \

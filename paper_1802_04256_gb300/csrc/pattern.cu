@@ -1089,6 +1089,7 @@ extern "C" rpim_status rpim_build_pattern(int64_t n_nodes, const double *xyz, co
                                           const double *cell_hi, const rpim_params *params,
                                           rpim_stream_t stream, rpim_pattern **out, int64_t *nnz_blocks)
 {
+    RPIM_STAGE("rpim_build_pattern");
     if (out) *out = nullptr;
     if (!params) return fail(RPIM_E_ARG, "params is null");
     if (n_nodes < 4 || n_nodes > INT32_MAX / 8 || !xyz || !cell_lo || !cell_hi)
@@ -1104,12 +1105,14 @@ extern "C" rpim_status rpim_build_pattern_batched(int32_t n_inst, const rpim_ins
                                                   double q, int32_t gauss_order, rpim_stream_t stream,
                                                   rpim_pattern **out, int64_t *nnz_blocks)
 {
+    RPIM_STAGE("rpim_build_pattern_batched");
     return create(n_inst, inst, xyz, cell_lo, cell_hi, alpha_c, q, gauss_order, stream, out, nnz_blocks);
 }
 
 extern "C" rpim_status rpim_pattern_set_buckets(rpim_pattern *p, int32_t n_bounds, const int32_t *bounds,
                                                 rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_pattern_set_buckets");
     if (!p || n_bounds < 1 || n_bounds > 31 || !bounds) return fail(RPIM_E_ARG, "bad bucket bounds");
     for (int i = 0; i < n_bounds; i++)
         if (bounds[i] < 1 || (i > 0 && bounds[i] <= bounds[i - 1])) return fail(RPIM_E_ARG, "bucket bounds must increase");

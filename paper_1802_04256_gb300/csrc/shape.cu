@@ -70,8 +70,10 @@ __device__ __forceinline__ bool positive_normal(double d)
 // Reciprocal by Newton-Raphson iteration r <- r (2 - d r) from a
 // single-precision seed: the relative error squares at each step
 // (2^-22 -> 2^-44 -> below double rounding), so two steps give a result
-// within an ulp or two of 1/d. d must be a positive double inside the
-// single-precision normal range.
+// within an ulp of 1/d (tested against correctly rounded division through
+// rpim_probe_recip). |d| must lie in [2^-126, 2^126], where both d and the
+// seed 1/d are single-precision normal numbers; either sign. (Pivots and
+// determinants in this kernel are of order 1e-9 to 1e3.)
 __device__ __forceinline__ double recip_nr(double d)
 {
     double r = f64_from_f32(__frcp_rn(f32_from_f64(d)));
@@ -547,6 +549,13 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
     group_sync(bar, GT);
 }
 
+// recip_nr over an array (the accuracy probe of rpim_probe_recip)
+__global__ void recip_probe_kernel(int64_t n, const double *__restrict__ d, double *__restrict__ r)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        r[i] = recip_nr(d[i]);
+}
+
 // One group of G warps per point. Every loop below is a flattened parallel
 // loop over the group's G*32 threads; the phases are separated by a named
 // barrier of the group. Groups of one block are independent.
@@ -850,6 +859,7 @@ using namespace rpim;
 extern "C" rpim_status rpim_autotune_shape(rpim_pattern *p, int64_t max_points, int32_t *table, int32_t *n_table,
                                            rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_autotune_shape");
     if (!p || max_points < 1) return fail(RPIM_E_ARG, "bad argument");
     if (p->shape_kind != RPIM_SHAPE_RPIM) {   // only the RPIM kernel has launch shapes to tune
         if (n_table) *n_table = 0;
@@ -912,6 +922,20 @@ extern "C" rpim_status rpim_autotune_shape(rpim_pattern *p, int64_t max_points, 
     return check_device_error(p, "autotune");
 }
 
+extern "C" rpim_status rpim_probe_recip(int64_t n, const double *d, double *r, rpim_stream_t stream)
+{
+    if (n < 0 || (n > 0 && (!d || !r))) return fail(RPIM_E_ARG, "bad argument");
+    if (n == 0) return RPIM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    RPIM_CUDA(cudaGetDevice(&dev));
+    RPIM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    launch("recip_probe", recip_probe_kernel, grid_size(sms, 4, n, 256), 256, 0, s, n, d, r);
+    RPIM_CUDA(cudaGetLastError());
+    RPIM_CUDA(cudaStreamSynchronize(s));
+    return RPIM_OK;
+}
+
 extern "C" rpim_status rpim_autotune_set(int32_t max_support, int32_t warps_per_point, int32_t points_per_block)
 {
     const int NC = std::max(8, (int)max_support);
@@ -947,6 +971,7 @@ extern "C" rpim_status rpim_set_shape_schedule(int32_t persistent)
 extern "C" rpim_status rpim_autotune_buckets(rpim_pattern *p, int64_t max_points, int32_t *bounds_out,
                                              int32_t *n_bounds_out, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_autotune_buckets");
     if (!p || max_points < 1) return fail(RPIM_E_ARG, "bad argument");
     if (p->shape_kind != RPIM_SHAPE_RPIM) {
         if (n_bounds_out) *n_bounds_out = 0;

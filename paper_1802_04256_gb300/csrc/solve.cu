@@ -148,7 +148,23 @@ __device__ __forceinline__ double bsr_row(int64_t I, const int64_t *rowptr, cons
 {
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     const int64_t r1 = rowptr[I + 1];
-    for (int64_t t = rowptr[I] + lane; t < r1; t += 32) {
+    int64_t t = rowptr[I] + lane;
+    // two blocks per lane and trip: both column indices, then both x
+    // gathers are in flight before the first product (the same sums in the
+    // same order as one block per trip)
+    for (; t + 32 < r1; t += 64) {
+        const int64_t J = cols[t], J2 = cols[t + 32];
+        const double *b = K + 9 * t, *c = K + 9 * (t + 32);
+        const double x0 = x[3 * J], x1 = x[3 * J + 1], x2 = x[3 * J + 2];
+        const double y0 = x[3 * J2], y1 = x[3 * J2 + 1], y2 = x[3 * J2 + 2];
+        a0 = fma(b[0], x0, fma(b[1], x1, fma(b[2], x2, a0)));
+        a1 = fma(b[3], x0, fma(b[4], x1, fma(b[5], x2, a1)));
+        a2 = fma(b[6], x0, fma(b[7], x1, fma(b[8], x2, a2)));
+        a0 = fma(c[0], y0, fma(c[1], y1, fma(c[2], y2, a0)));
+        a1 = fma(c[3], y0, fma(c[4], y1, fma(c[5], y2, a1)));
+        a2 = fma(c[6], y0, fma(c[7], y1, fma(c[8], y2, a2)));
+    }
+    if (t < r1) {
         const double *b = K + 9 * t;
         const int64_t J = cols[t];
         const double x0 = x[3 * J], x1 = x[3 * J + 1], x2 = x[3 * J + 2];
@@ -686,6 +702,7 @@ extern "C" rpim_status rpim_apply_penalty_bc(rpim_pattern *p, double *K, double 
                                              const double *values, double scale, double *alpha_out,
                                              rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_apply_penalty_bc");
     if (!p) return fail(RPIM_E_ARG, "null pattern");
     std::vector<double> a(p->n_inst);
     rpim_status st = apply_penalty(p, K, f, m, dofs, values, scale, -1.0, a.data(), (cudaStream_t)stream);
@@ -697,12 +714,14 @@ extern "C" rpim_status rpim_apply_penalty_bc_batched(rpim_pattern *p, double *K,
                                                      const int64_t *dofs, const double *values, double scale,
                                                      double *alpha_out, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_apply_penalty_bc_batched");
     return apply_penalty(p, K, f, m, dofs, values, scale, -1.0, alpha_out, (cudaStream_t)stream);
 }
 
 extern "C" rpim_status rpim_apply_penalty_alpha(rpim_pattern *p, double *K, double *f, int64_t m, const int64_t *dofs,
                                                 const double *values, double alpha, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_apply_penalty_alpha");
     if (!(alpha >= 0.0)) return fail(RPIM_E_ARG, "negative penalty");
     return apply_penalty(p, K, f, m, dofs, values, 0.0, alpha, nullptr, (cudaStream_t)stream);
 }
@@ -725,11 +744,12 @@ extern "C" rpim_status rpim_pattern_get_precond(const rpim_pattern *p, int32_t *
 extern "C" rpim_status rpim_solve_pcg(rpim_pattern *p, const double *K, const double *f, double *u, double rtol,
                                       int32_t max_iter, int32_t *iters, double *relres, rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_solve_pcg");
     if (!p || !K || !f || !u || max_iter < 0 || !(rtol >= 0)) return fail(RPIM_E_ARG, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;
     const int64_t n = 3 * p->n_nodes;
-    const int nb = std::max(1, p->sm_count * 4);
+    const int nb = std::max(1, p->sm_count * 6);   // six 256-thread blocks per SM fit the product's 40 registers
     const bool block = p->precond == RPIM_PRECOND_BLOCK_JACOBI;
     const int64_t nd = block ? 3 * n : n;   // preconditioner: 3x3 inverses or diagonal inverses
     const int64_t need = 4 * n + nd + 3 * (int64_t)nb;
@@ -817,6 +837,7 @@ extern "C" rpim_status rpim_solve_pcg_batched(rpim_pattern *p, const double *K, 
                                               double rtol, int32_t max_iter, int32_t *iters, double *relres,
                                               rpim_stream_t stream)
 {
+    RPIM_STAGE("rpim_solve_pcg_batched");
     if (!p || !K || !f || !u || max_iter < 0 || !(rtol >= 0)) return fail(RPIM_E_ARG, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     p->stream = s;

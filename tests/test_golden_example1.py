@@ -13,6 +13,7 @@ weight, base fixed, sides on rollers.
 import os
 
 import numpy as np
+import pytest
 
 import gen
 import oracle
@@ -52,3 +53,37 @@ def test_oracle_cube_carries_the_printed_bottom_stress():
     local = -np.dot(m.wj[low], sig[low, 2]) / m.wj[low].sum() / 1e6
     theory_there = gam * (H - m.pts[low, 2].mean()) / 1e6
     assert abs(local / theory_there - 1.0) < 0.2
+
+
+@pytest.mark.gpu
+def test_gpu_path_on_example1_cube():
+    """The library's whole path (pattern, assembly with gravity, penalty,
+    block-Jacobi PCG, stress recovery) on the same 100 m cube: displacements
+    within 1e-9 of the oracle pipeline's, stresses at the integration points
+    of the bottom layer within 1e-9 of the extended oracle's at the same
+    displacements, and the penalty reactions carry the printed bottom stress
+    (global equilibrium, a sanity check)."""
+    import torch
+    from gpu_util import GpuRun, t
+
+    v = _golden()
+    rho, g, H = v["density"], 9.8, 100.0
+    gam = rho * g
+    p = gen.gravity_column(shape=(7, 7, 7), height=H, width=H, gamma=gam, E=1.0e9, nu=0.25)
+    run = GpuRun(p)
+    u, it, rr, alpha, K, f = run.solve(rtol=1e-12, precond="block")
+    uh = u.cpu().numpy()
+    m, uo, ito, rro, ao = oracle.solve_problem(p, rtol=1e-12)
+    du = np.linalg.norm(uh - uo) / np.linalg.norm(uo)
+    base = p.fixed_dofs[p.fixed_dofs % 3 == 2]
+    mean_base_stress = -alpha * uh[base].sum() / (H * H) / 1e6
+    low = m.pts[:, 2] < m.pts[:, 2].min() + 1e-9
+    pts = m.pts[low]
+    sg = run.pat.stress(u, t(pts), t(p.E[low]), t(p.nu[low])).cpu().numpy()
+    so = oracle.stress(p.xyz, uh, pts, p.E[low], p.nu[low], p.alpha_s, p.alpha_c, p.q, p.h, "ld")
+    ds = np.abs(sg - so).max() / np.abs(so).max()
+    print("example 1 on the GPU: %d PCG iterations, u vs oracle %.2e, bottom-layer stress vs extended oracle %.2e, "
+          "mean base stress %.6f MPa (printed theory %.3f)" % (it, du, ds, mean_base_stress, v["bottom_stress_theory"]))
+    assert du < 1e-9
+    assert ds < 1e-9
+    assert abs(mean_base_stress - v["bottom_stress_theory"]) < 1e-3 * v["bottom_stress_theory"]

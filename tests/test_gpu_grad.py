@@ -132,3 +132,78 @@ def test_gradient_matches_central_differences_along_a_direction(full):
     print("%s: directional derivative adjoint %.9e fd %.9e rel %.2e" % ("full" if full else "small", an, fd,
                                                                        abs(an - fd) / abs(an)))
     assert abs(an - fd) <= TOL * abs(an)
+
+
+def test_per_parameter_central_differences_on_the_backanalysis_block():
+    """32 single parameters of the 64 x 32 x 32 back-analysis block (16 of E,
+    16 of nu, at seeded random integration points), each against a central
+    difference of L = 1/2 |u[obs] - u_obs|^2 at a step large enough to rise
+    above the solver's noise (at the relative step of 1e-6 the change of L is
+    about 1e-12 of L, below what two FP64 solves resolve). K is linear in
+    E_g and a single point's stiffness is about 1e-6 of K's, so L is linear
+    in E_g to about 1e-12 over a step of 5% of E_g: one central difference.
+    D is nonlinear in nu, so the nu differences (steps 2e-3 and 4e-3) are
+    Richardson-extrapolated (truncation O(h^4)). Both solves of a difference
+    start from the converged unperturbed solution (warm start) and run to a
+    relative residual of 1e-14; L+ - L- is formed as 1/2 (a+ - a-) . (a+ + a-),
+    a = u[obs] - u_obs, which avoids subtracting two nearly equal losses.
+    Tolerance: per entry, 1e-6 of the largest gradient of its kind among the
+    16 (the gradients' own scale, as in the other checks of this file)."""
+    p = gen.backanalysis_config()
+    pat = R.Pattern.from_problem(p)
+    pat.set_precond("block")
+    f_ext = torch.zeros(3 * p.n_nodes, dtype=torch.float64, device="cuda")
+    pat.add_traction(*faces(p), f_ext)
+    E0, nu0 = t(p.E), t(p.nu)
+    alpha = R.penalty_alpha(pat, E0, nu0)
+    dofs, vals = t(p.fixed_dofs, torch.int64), t(p.fixed_vals)
+    obs = torch.as_tensor(p.meta["obs_nodes"], device="cuda")
+    u_obs = torch.as_tensor(np.random.default_rng(21).normal(0.0, 1e-3, (len(obs), 3)), device="cuda")
+
+    def solve(E, nu, u0):
+        K, f = pat.assemble(E, nu)
+        R.rpim_add_vector(pat.handle, f_ext, f)
+        R.rpim_apply_penalty_alpha(pat.handle, K, f, dofs, vals, alpha)
+        u = u0.clone()
+        _, it, rr = pat.solve_pcg(K, f, u=u, rtol=1e-14, max_iter=400000, check=False)
+        assert rr <= 1e-13, rr
+        return u
+
+    E = E0.clone().requires_grad_()
+    nu = nu0.clone().requires_grad_()
+    u = R.solve(pat, E, nu, f_ext, dofs, vals, alpha, rtol=1e-14)
+    loss = 0.5 * ((u.view(-1, 3)[obs] - u_obs) ** 2).sum()
+    loss.backward()
+    gE, gnu = E.grad, nu.grad
+    u0 = u.detach()
+    rng = np.random.default_rng(33)
+    picks = [("E", g) for g in rng.choice(p.n_points, 16, replace=False)] + \
+            [("nu", g) for g in rng.choice(p.n_points, 16, replace=False)]
+    def central(kind, g, step):
+        us = []
+        for sgn in (1.0, -1.0):
+            Ep, nup = E0.clone(), nu0.clone()
+            (Ep if kind == "E" else nup)[g] += sgn * step
+            us.append(solve(Ep, nup, u0).view(-1, 3)[obs] - u_obs)
+        return float(0.5 * ((us[0] - us[1]) * (us[0] + us[1])).sum()) / (2 * step)
+
+    res = {"E": [], "nu": []}
+    for kind, g in picks:
+        g = int(g)
+        if kind == "E":
+            fd = central(kind, g, 5e-2 * float(E0[g]))
+        else:
+            fd = (4.0 * central(kind, g, 2e-3) - central(kind, g, 4e-3)) / 3.0
+        an = float((gE if kind == "E" else gnu)[g])
+        res[kind].append((g, an, fd))
+    worst = 0.0
+    for kind, rows in res.items():
+        scale = max(abs(an) for _, an, _ in rows)
+        for g, an, fd in rows:
+            d = abs(fd - an) / scale
+            worst = max(worst, d)
+            print("%s[%d]: adjoint %.9e central difference %.9e, |diff| / max|g| %.2e, rel %.2e"
+                  % (kind, g, an, fd, d, abs(fd - an) / abs(an)))
+    print("32 parameters: worst |diff| / max|g| %.2e" % worst)
+    assert worst <= 1e-6
+    pat.free()

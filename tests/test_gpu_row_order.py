@@ -46,7 +46,7 @@ def _host_keys(p):
 
 @pytest.mark.parametrize("name", ["cube", "beam"])
 def test_morton_row_order_is_sorted_and_results_are_bitwise_node_order(name):
-    p = gen.cube_config(jitter=0.2, seed=7) if name == "cube" else gen.cantilever_config(shape=(33, 9, 9))
+    p = gen.cube_config(jitter=0.2, seed=7) if name == "cube" else gen.cantilever_config(shape=(49, 7, 7))
     E, nu = t(p.E), t(p.nu)
     out = {}
     for morton in (1, 0):

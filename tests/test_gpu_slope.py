@@ -19,8 +19,10 @@ from gpu_util import GpuRun, t
 
 pytestmark = pytest.mark.gpu
 
+# twice the errors measured on a GB300 against the extended oracle: sampled
+# shape functions (4.2e-10, h units) and sampled K rows (4.7e-11 of max|K|)
+TOL_PHI_LD = 8.5e-10
 TOL_K_LD = 1e-10
-GAIN = 0.05
 
 
 @pytest.fixture(scope="module")
@@ -62,7 +64,7 @@ def test_sampled_supports_and_shape_functions(slope):
         f64 = oracle.shape(p.xyz, s, x, p.h, p.alpha_c, p.q, "f64") * scale[:, None]
         worst = max(worst, np.abs(mine - ld).max())
         e64 = max(e64, np.abs(f64 - ld).max())
-    tol = max(1e-9, GAIN * e64)
+    tol = TOL_PHI_LD
     print("phi: |gpu - ld| %.3e (tol %.1e), |f64 - ld| %.3e" % (worst, tol, e64))
     assert worst < tol
 
@@ -93,7 +95,7 @@ def test_sampled_rows_vs_oracle(slope):
         dld = max(dld, np.abs(mine - rows["ld"]).max() / kmax)
         d64 = max(d64, np.abs(mine - rows["f64"]).max() / kmax)
         print("row %d (%s): %d points, %d blocks" % (I, tx, len(sel), r1 - r0))
-    tol = max(TOL_K_LD, GAIN * e64)
+    tol = TOL_K_LD
     print("K rows: |gpu - ld| %.3e (tol %.1e), |f64 - ld| %.3e, |gpu - f64| %.3e" % (dld, tol, e64, d64))
     assert dld < tol
     assert d64 < e64 + tol

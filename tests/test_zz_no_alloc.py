@@ -79,13 +79,14 @@ def test_noalloc_stress_rejects_calls_beyond_its_point_limit(solved):
 
 
 def test_noalloc_stress_rejects_calls_beyond_its_entry_limit_then_recovers():
-    """2,000 points whose supports hold about 170 nodes each (support radius
-    3.4h on the 6x6x6 cube) need more than RPIM_NOALLOC_MAX_ENTRIES support
-    entries: the call returns RPIM_E_ARG after counting, writes nothing, and
-    the next call within the limits equals rpim_stress."""
+    """2,000 points whose supports hold about 144 nodes each (support radius
+    4.2h on the 6x6x6 cube, about 288,000 entries in all) need more than
+    RPIM_NOALLOC_MAX_ENTRIES support entries: the call returns RPIM_E_ARG
+    after counting, writes nothing, and the next call within the limits
+    equals rpim_stress."""
     p = gen.cube_config(jitter=0.2, seed=5)
-    p.alpha_s = 3.4
-    g = GpuRun(p, loads=False)
+    p.alpha_s = 4.2
+    pat = R.Pattern.from_problem(p)   # stress recovery needs the pattern only
     u = t(np.sin(np.arange(3 * p.n_nodes) * 0.37) * 1e-3)
     n = 2000
     xyz = t(_points(p, n, 4))
@@ -93,12 +94,13 @@ def test_noalloc_stress_rejects_calls_beyond_its_entry_limit_then_recovers():
     nu = t(np.full(n, 0.3))
     out = torch.zeros(n, 6, dtype=torch.float64, device="cuda")
     with pytest.raises(R.RpimError) as e:
-        _noalloc(g.pat, u, xyz, E, nu, out)
+        _noalloc(pat, u, xyz, E, nu, out)
     assert e.value.status == 1
     assert "entries" in str(e.value)
-    m = 300   # about 51,000 entries
+    m = 300   # about 43,000 entries
     xs, Es, nus = xyz[:m].contiguous(), E[:m].contiguous(), nu[:m].contiguous()
-    ref = g.pat.stress(u, xs, Es, nus)
+    ref = pat.stress(u, xs, Es, nus)
     out = torch.full_like(ref, float("nan"))
-    _noalloc(g.pat, u, xs, Es, nus, out)
+    _noalloc(pat, u, xs, Es, nus, out)
     assert (out - ref).abs().max().item() <= 1e-12 * ref.abs().max().item()
+    pat.free()
