@@ -140,9 +140,10 @@ def test_per_parameter_central_differences_on_the_backanalysis_block():
     difference of L = 1/2 |u[obs] - u_obs|^2 at a step large enough to rise
     above the solver's noise (at the relative step of 1e-6 the change of L is
     about 1e-12 of L, below what two FP64 solves resolve). K is linear in
-    E_g and a single point's stiffness is about 1e-6 of K's, so L is linear
-    in E_g to about 1e-12 over a step of 5% of E_g: one central difference.
-    D is nonlinear in nu, so the nu differences (steps 2e-3 and 4e-3) are
+    E_g and a single point's stiffness is about 1e-6 of K's, so the central
+    difference over 0.5% of E_g carries a truncation error of about 2e-7 of
+    the gradient (measured: 6.6e-7 at 1%, 1.7e-5 at 5%, the O(h^2) term). D
+    is nonlinear in nu, so the nu differences (steps 2e-3 and 4e-3) are
     Richardson-extrapolated (truncation O(h^4)). Both solves of a difference
     start from the converged unperturbed solution (warm start) and run to a
     relative residual of 1e-14; L+ - L- is formed as 1/2 (a+ - a-) . (a+ + a-),
@@ -191,7 +192,7 @@ def test_per_parameter_central_differences_on_the_backanalysis_block():
     for kind, g in picks:
         g = int(g)
         if kind == "E":
-            fd = central(kind, g, 5e-2 * float(E0[g]))
+            fd = central(kind, g, 5e-3 * float(E0[g]))
         else:
             fd = (4.0 * central(kind, g, 2e-3) - central(kind, g, 4e-3)) / 3.0
         an = float((gE if kind == "E" else gnu)[g])
