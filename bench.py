@@ -512,7 +512,7 @@ def _backanalysis(dev, stream, rtol=1e-10):
 
 
 # --------------------------------------------------------------------------- batched vs per-instance
-def _batched(n_sel, dev, stream, reps=1, warm=1, small_nodes=2000):
+def _batched(n_sel, dev, stream, reps=1, warm=1, small_nodes=2000, cpu=True):
     """Blocks of the 512-instance batched workload (node counts log-uniform in
     500-20,000, alpha_s uniform in [2, 3.5]), every (512 / n_sel)-th one:
     one batched pattern + assembly + tractions + per-instance penalty +
@@ -707,6 +707,20 @@ def _batched(n_sel, dev, stream, reps=1, warm=1, small_nodes=2000):
                  "kernel_launches": {"batched": lsb, "per_instance": lss},
                  "step": "every block below %d nodes: build pattern + assemble + tractions (assembly); penalty "
                          "+ Jacobi-PCG to 1e-10 (solve); both arms warm, best of two" % small_nodes}
+    # the oracle on host cores: a spread sample of the points of four blocks
+    # of the selection (smallest to largest), all cores and one thread
+    cpu_out = None
+    if cpu:
+        picks = sorted(sel, key=lambda p: p.n_nodes)
+        picks = [picks[int(i * (len(picks) - 1) / 3)] for i in range(4)]
+        runs = [cpu_baseline(p, 2.0, 1.0) for p in picks]
+        cpu_out = {"value": len(runs) / sum(1.0 / r["value"] for r in runs), "unit": UNIT, "cores": runs[0]["cores"],
+                   "kind": "oracle",
+                   "single_thread": {"value": len(runs) / sum(1.0 / r["single_thread"]["value"] for r in runs),
+                                     "unit": UNIT, "cores": 1},
+                   "sample": "four blocks of the selection (%s nodes), about 2 s of all-core and 1 s of one-thread "
+                             "oracle work each, rates combined as a harmonic mean"
+                             % ", ".join(str(p.n_nodes) for p in picks)}
     return {"instances": len(sel), "of": len(allp), "selection": "every %d-th block of the 512-block workload"
             % max(1, len(allp) // n_sel), "n_nodes": int(offs[-1]), "n_points": npts,
             "node_range": [int(min(p.n_nodes for p in sel)), int(max(p.n_nodes for p in sel))],
@@ -717,7 +731,7 @@ def _batched(n_sel, dev, stream, reps=1, warm=1, small_nodes=2000):
                       "iterations_max": int(max(itb)), "iterations_sum_per_instance": int(sum(its))},
             "end_to_end": {"batched_ms": ba + bs, "per_instance_ms": sa + ss, "speedup": (sa + ss) / (ba + bs)},
             "kernel_launches": {"batched": lb, "per_instance": ls},
-            "reassembly": reasm, "small_blocks": small_out, "bucket_bounds": bounds,
+            "reassembly": reasm, "small_blocks": small_out, "bucket_bounds": bounds, "cpu_baseline": cpu_out,
             "u_max_rel_diff_batched_vs_per_instance": du,
             "target_5x": "not met on this workload (FP64-bound blocks fill the GPU alone)",
             "step": "build pattern + assemble + tractions (assembly); penalty + Jacobi-PCG to 1e-10 (solve)"}
@@ -885,7 +899,8 @@ def run_ours(args, rank, world, local_rank):
 
     batched = None
     if rank == 0 and args.batched_instances > 0:
-        batched = _batched(args.batched_instances, dev, stream, warm=args.batched_warmup)
+        batched = _batched(args.batched_instances, dev, stream, warm=args.batched_warmup,
+                           cpu=not args.no_cpu_baseline)
     grad = None
     if rank == 0 and not args.no_grad:
         grad = _backanalysis(dev, stream)
@@ -927,7 +942,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="host seconds of the oracle's all-core sample of the headline workload")
     ap.add_argument("--no-solve", action="store_true", help="skip the penalty + PCG measurements")
-    ap.add_argument("--precond", default="jacobi",
+    ap.add_argument("--precond", default="jacobi,block",
                     help="PCG preconditioners of the headline solve (comma separated: jacobi, block); the "
                          "cantilever's solve is timed with both")
     ap.add_argument("--row-order", default="morton", choices=["morton", "node"],
