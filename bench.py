@@ -807,6 +807,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     R.lib()
     R.rpim_set_row_order(args.row_order == "morton")
+    R.rpim_set_shape_solver(args.solver)
     desc, make = WORKLOADS[args.workload]
     p = make()
     inp = Inputs(p, dev)
@@ -918,7 +919,8 @@ def run_ours(args, rank, world, local_rank):
                           "l2": "inputs and outputs larger than L2 (K %.1f GB, shape functions %.1f GB)"
                                 % (nnzb * 72 / 1e9, nsup.sum() * 32 / 1e9),
                           "support": {"min": int(nsup.min()), "max": int(nsup.max()), "mean": float(nsup.mean())},
-                          "nnz_blocks": nnzb, "parallelism": "replicas" if world > 1 else "single GPU"},
+                          "nnz_blocks": nnzb, "shape_solver": args.solver,
+                          "parallelism": "replicas" if world > 1 else "single GPU"},
                "roofline": roof, "kernel_ms_per_step": kernel_ms, "kernel_time_share": kernel_share,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                "solve": solve, "configs": configs, "mls": mls, "batched": batched, "backanalysis": grad,
@@ -948,6 +950,9 @@ def main():
     ap.add_argument("--row-order", default="morton", choices=["morton", "node"],
                     help="order in which the row-owner kernels take their rows (results are bitwise the same)")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads")
+    ap.add_argument("--solver", default="fp64", choices=["fp64", "refined"],
+                    help="solver of the moment system in the shape kernel (FP64 LDL', or float-float LDL' "
+                         "with one FP64 refinement step)")
     ap.add_argument("--no-grad", action="store_true", help="skip the back-analysis gradient measurement")
     ap.add_argument("--no-mls", action="store_true", help="skip the MLS-variant assembly measurement")
     ap.add_argument("--batched-warmup", type=int, default=1,

@@ -277,6 +277,29 @@ rpim_status rpim_autotune_buckets(rpim_pattern *pattern, int64_t max_points, int
 rpim_status rpim_set_shape_schedule(int32_t persistent);
 
 /*
+ * Solver of the reduced moment system S a_r = rhs inside the RPIM shape
+ * kernel (Sec. 1: the RPIM shape functions are the solution of the moment
+ * problem), process-wide:
+ *   RPIM_SOLVER_FP64 (0, default): S = L D L' factored in FP64.
+ *   RPIM_SOLVER_REFINED (1): L D L' factored in float-float arithmetic
+ *     (pairs of FP32 numbers, about 48 bits), then one step of iterative
+ *     refinement whose residual rhs - S a_r is formed in FP64 from S in
+ *     FP64, the correction solved with the same factors. The result has the
+ *     accuracy of the FP64 factorisation (the refinement contracts the
+ *     factorisation error by about cond(S) * 2^-46, cond(S) <= 1e7 here)
+ *     with about half its FP64 work, but three triangular solves instead of
+ *     one; the FP64 copy of S lives in a scratch array of the pattern
+ *     (multiprocessors x 228 KB, allocated with the pattern).
+ * The two solvers give different roundings, each deterministic and
+ * independent of the launch shape. Changing the solver invalidates captured
+ * assembly graphs (rpim_assemble_graphed recaptures). Errors: RPIM_E_ARG.
+ */
+#define RPIM_SOLVER_FP64 0
+#define RPIM_SOLVER_REFINED 1
+rpim_status rpim_set_shape_solver(int32_t solver);
+rpim_status rpim_get_shape_solver(int32_t *solver);
+
+/*
  * Order in which the row-owner kernels (the pattern build's two row passes
  * and the assembly's row kernel) take the rows of K, process-wide:
  * 1 (default) the Morton order of the nodes' grid cells (computed by every
@@ -494,6 +517,10 @@ rpim_status rpim_stress(rpim_pattern *pattern, const double *u, int64_t n_pts,
  *   allocation); make that first call before any stream capture.
  *   Every call uses the same array: calls that may overlap on the GPU (other
  *   streams, other host threads) race and must be serialised by the caller.
+ *   The refined shape solver (rpim_set_shape_solver) also uses the pattern's
+ *   own solver scratch, allocated when the pattern was built; like every
+ *   call on a pattern, the call must not overlap another call on the same
+ *   pattern.
  * Synchronises `stream`.
  */
 #define RPIM_NOALLOC_MAX_POINTS 2048

@@ -37,7 +37,7 @@ EXPORTED = [
     "rpim_pattern_get_buckets", "rpim_autotune_buckets", "rpim_set_shape_schedule",
     "rpim_device_allocations", "rpim_pool_used_bytes", "rpim_add_traction", "rpim_add_traction_batched",
     "rpim_add_vector", "rpim_pattern_set_precond", "rpim_pattern_get_precond", "rpim_set_row_order",
-    "rpim_pattern_copy_row_order", "rpim_probe_recip",
+    "rpim_pattern_copy_row_order", "rpim_probe_recip", "rpim_set_shape_solver", "rpim_get_shape_solver",
 ]
 
 SHAPE_KINDS = {"rpim": 0, "mls": 1, "shepard": 2}
@@ -122,6 +122,8 @@ def lib():
         "rpim_pattern_get_buckets": [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), i32],
         "rpim_autotune_buckets": [vp, i64, C.POINTER(i32), C.POINTER(i32), vp],
         "rpim_set_shape_schedule": [i32],
+        "rpim_set_shape_solver": [i32],
+        "rpim_get_shape_solver": [C.POINTER(i32)],
         "rpim_pattern_get_shape": [vp, C.POINTER(i32)],
         "rpim_pool_used_bytes": [C.POINTER(i64)],
         "rpim_add_traction": [vp, i64, vp, vp, vp, vp, vp, vp],
@@ -296,6 +298,22 @@ def rpim_autotune_buckets(handle, max_points=200000, stream=None):
 
 def rpim_set_shape_schedule(persistent: bool):
     _check(lib().rpim_set_shape_schedule(1 if persistent else 0), "rpim_set_shape_schedule")
+
+
+SOLVERS = {"fp64": 0, "refined": 1}
+
+
+def rpim_set_shape_solver(solver: str):
+    """Solver of the reduced moment system in the RPIM shape kernel: "fp64"
+    (FP64 LDL', the default) or "refined" (float-float LDL' with one FP64
+    refinement step)."""
+    _check(lib().rpim_set_shape_solver(SOLVERS[solver]), "rpim_set_shape_solver")
+
+
+def rpim_get_shape_solver() -> str:
+    v = C.c_int32(0)
+    _check(lib().rpim_get_shape_solver(C.byref(v)), "rpim_get_shape_solver")
+    return {b: a for a, b in SOLVERS.items()}[v.value]
 
 
 def rpim_set_row_order(morton: bool):

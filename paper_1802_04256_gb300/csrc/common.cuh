@@ -172,6 +172,11 @@ struct rpim_pattern {
     int32_t *bucket_order = nullptr;     // [n_points] point ids grouped by bucket
     std::vector<int32_t> bucket_bounds;  // upper support size of each bucket (last open-ended)
     unsigned long long *tile_counter = nullptr;  // [32] per-bucket work counters of the persistent shape kernel
+    // FP64 copies of the reduced moment matrices of the refined shape solver:
+    // one slice per resident point group (multiprocessors x their shared
+    // memory bounds every launch), allocated with the pattern
+    double *shape_scratch = nullptr;
+    int64_t shape_scratch_doubles = 0;
 
     int64_t n_nodes = 0, n_points = 0, n_entries = 0, nnzb = 0;
     int32_t max_support = 0, min_support = 0, max_row = 0;

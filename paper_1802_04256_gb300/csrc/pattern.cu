@@ -600,6 +600,7 @@ static void pattern_release(rpim_pattern *p)
     dfree(p->phi, s); dfree(p->lamw, s); dfree(p->err, s); dfree(p->scal, s); dfree(p->series, s);
     dfree(p->ws.buf, s);
     dfree(p->ig, s); dfree(p->node_inst, s); dfree(p->bucket_order, s); dfree(p->tile_counter, s);
+    dfree(p->shape_scratch, s);
     dfree(p->seg_row, s); dfree(p->seg_inst, s); dfree(p->inst_seg, s);
     if (p->asm_exec) cudaGraphExecDestroy(p->asm_exec);
     p->asm_exec = nullptr;
@@ -821,6 +822,12 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
     RPIM_CHECK(dalloc(&p->err, 1, s));
     RPIM_CUDA(cudaMemsetAsync(p->err, 0xFF, sizeof(DevError), s));
     RPIM_CHECK(dalloc(&p->scal, 16, s));
+    {
+        int smem_sm = 0;
+        RPIM_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device));
+        p->shape_scratch_doubles = (int64_t)p->sm_count * smem_sm / (int64_t)sizeof(double);
+        RPIM_CHECK(dalloc(&p->shape_scratch, p->shape_scratch_doubles, s));
+    }
     RPIM_CHECK(dalloc(&p->xyz, 3 * n, s));
     RPIM_CUDA(cudaMemcpyAsync(p->xyz, xyz, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     RPIM_CHECK(dalloc(&p->ig, ni, s));

@@ -67,6 +67,20 @@ __device__ __forceinline__ bool positive_normal(double d)
     return hi > 0x000FFFFF && hi < 0x7FF00000;
 }
 
+// Small integers to float and back without a conversion instruction (the
+// conversions do not run on the FP32 pipe): for 0 <= x < 2^23 the float
+// 2^23 + x has the bits 0x4B000000 | x, and adding 2^23 to 0 <= f < 2^22
+// leaves the nearest integer of f in the low mantissa bits.
+__device__ __forceinline__ float small_int_to_float(int x)
+{
+    return __fsub_rn(__int_as_float(0x4B000000 | x), 8388608.0f);
+}
+
+__device__ __forceinline__ int small_float_to_int(float f)
+{
+    return __float_as_int(__fadd_rn(f, 8388608.0f)) & 0x7FFFFF;
+}
+
 // Reciprocal by Newton-Raphson iteration r <- r (2 - d r) from a
 // single-precision seed: the relative error squares at each step
 // (2^-22 -> 2^-44 -> below double rounding), so two steps give a result
@@ -83,10 +97,115 @@ __device__ __forceinline__ double recip_nr(double d)
     return fma(r, e, r);
 }
 
+// ---------------------------------------------------------------------------
+// Double-single ("float-float") arithmetic for the refined solver: a value is
+// the unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi) / 2,
+// about 48 significant bits. Sums use Knuth's TwoSum and products Dekker's
+// exact product in its FMA form (fmaf(a, b, -a*b) is the rounding error of
+// a*b exactly); both are error-free transformations (Knuth, TAOCP vol. 2,
+// 4.2.2; Dekker, Numer. Math. 18, 1971). Every operation is spelled with the
+// round-to-nearest intrinsics, which the compiler neither contracts into
+// fused operations nor reorders. On this GPU an FP32 operation costs 1/64 of
+// an FP64 one, so the ~15 FP32 operations of a float-float multiply-add are
+// still several times cheaper than one FP64 FMA.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+// a + b for |a| >= |b| (or a == 0)
+__device__ __forceinline__ float2 fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ float2 ff_mul(float2 x, float2 y)
+{
+    const float p = __fmul_rn(x.x, y.x);
+    float e = __fmaf_rn(x.x, y.x, -p);
+    e = __fmaf_rn(x.x, y.y, e);
+    e = __fmaf_rn(x.y, y.x, e);
+    return fast_two_sum(p, e);
+}
+
+// c - x * y
+__device__ __forceinline__ float2 ff_fnma(float2 x, float2 y, float2 c)
+{
+    const float p = __fmul_rn(x.x, y.x);
+    float pe = __fmaf_rn(x.x, y.x, -p);
+    pe = __fmaf_rn(x.x, y.y, pe);
+    pe = __fmaf_rn(x.y, y.x, pe);
+    const float2 s = two_sum(c.x, -p);
+    const float e = __fadd_rn(s.y, __fsub_rn(c.y, pe));
+    return two_sum(s.x, e);
+}
+
+// hi + lo of a double on the integer pipe: hi is d truncated to 24 bits,
+// lo the next 24 bits of the remainder (truncated); d outside the FP32
+// normal range, and remainders below it, flush to zero.
+__device__ __forceinline__ float2 ff_from_f64(double d)
+{
+    const float hi = f32_from_f64(d);
+    if (hi == 0.0f) return make_float2(0.0f, 0.0f);
+    const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
+    const int e = (int)((hw >> 20) & 0x7FF) - 1023 - 52 + 127;   // biased FP32 exponent of the lowest bit
+    const unsigned rem = lw & 0x1FFFFFFFu;                         // the 29 bits below hi
+    float lo = 0.0f;
+    if (rem) {   // normalise rem by its leading bit (integer pipe)
+        const int lz = __clz(rem);          // 3..31
+        const int eb = e + (31 - lz);       // biased exponent of that bit
+        if (eb >= 1) {
+            const unsigned mant = lz >= 8 ? rem << (lz - 8) : rem >> (8 - lz);
+            lo = __uint_as_float(((unsigned)eb << 23) | (mant & 0x7FFFFFu));
+        }
+    }
+    return make_float2(hi, (hw & 0x80000000u) ? -lo : lo);
+}
+
+__device__ __forceinline__ double ff_to_f64(float2 a) { return f64_from_f32(a.x) + f64_from_f32(a.y); }
+
+// positive with a normal FP32 leading word (a usable pivot)
+__device__ __forceinline__ bool ff_pivot_ok(float2 a) { return a.x >= 1.17549435e-38f && a.x < 3.0e38f; }
+
+// 1/d for a positive pivot: the FP32 reciprocal q and one Newton step
+// q + q (1 - d q), the residual 1 - d q formed from Dekker's exact product
+// (relative error about 2^-46)
+__device__ __forceinline__ float2 ff_recip(float2 d)
+{
+    const float q = __frcp_rn(d.x);
+    const float p = __fmul_rn(d.x, q);
+    float pe = __fmaf_rn(d.x, q, -p);
+    pe = __fmaf_rn(d.y, q, pe);
+    const float r = __fsub_rn(__fsub_rn(1.0f, p), pe);   // 1 - p is exact (p lies within 2^-23 of 1)
+    return fast_two_sum(q, __fmul_rn(q, r));
+}
+
+// (i, j), i >= j, of the linear index u < 2^20 of a packed lower triangle,
+// from the single-instruction approximate square root (no conversion
+// instruction) and one integer correction each way
+__device__ __forceinline__ void tri_decode_fast(int u, int &i, int &j)
+{
+    float f;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"(small_int_to_float(8 * u + 1)));
+    int r = small_float_to_int(__fmul_rn(__fsub_rn(f, 1.0f), 0.5f));
+    if ((r + 1) * (r + 2) / 2 <= u) r++;
+    if (r * (r + 1) / 2 > u) r--;
+    i = r;
+    j = u - r * (r + 1) / 2;
+}
+
+// piece of s: floor((log2 s - log2_lo) / log2 r), clamped to the pieces, as
+// the nearest integer of f + 1/2 minus one (the argument of the rounding
+// stays >= 1/2; an f that is an exact integer may give the piece below, whose
+// series the host check also covers: it reaches |t| = 1.02)
 __device__ __forceinline__ int piece_of(const KernelSeries &ks, double s)
 {
-    const float f = (__log2f(f32_from_f64(s)) - ks.log2_lo) * ks.inv_log2r;
-    const int k = (int)f;
+    const float f = fminf(fmaxf((__log2f(f32_from_f64(s)) - ks.log2_lo) * ks.inv_log2r, 0.0f), 64.0f);
+    const int k = small_float_to_int(__fadd_rn(f, 0.5f)) - 1;
     return min(max(k, 0), ks.pieces - 1);
 }
 
@@ -125,6 +244,7 @@ struct PointSmem {
     double *Y;      // [4][NC]  A_rp then Y
     double *v;      // [4][NC]  v[rhs][j] (original order); column buffer later
     double *S;      // packed lower triangle of order NC: S, then 4 rhs rows
+                    // (float-float pairs in the refined solver)
     double *M;      // [16] P_p^{-T}, row-major
     double *App;    // [16]
     double *red;    // [4 * 16] per-warp partial sums of the pivot values
@@ -132,15 +252,28 @@ struct PointSmem {
     int *redj;      // [4 passes][16 warps] argmax indices
     int *r2o;       // [NC] rest index -> original index
     double *piv;    // [2] reciprocal of the next LDL' pivot (0 when not positive)
+    // refined solver only
+    double *rhs;    // [4][NC] reduced right-hand sides (FP64)
+    double *a;      // [4][NC] solution a_r (FP64)
+    float2 *ivs;    // [NC] reciprocal pivots
 };
 
-__host__ __device__ inline int64_t point_smem_doubles(int NC)
+// shared memory of one point group (doubles); the refined solver adds the
+// FP64 right-hand sides and solution and the reciprocal pivots
+__host__ __device__ inline int64_t point_smem_doubles(int NC, bool refine)
 {
     return 3 * NC + (3 * NC + 1) / 2 + 4 * NC + 4 * NC + 4 * NC + (int64_t)NC * (NC + 1) / 2 + 32 + 64 + 32 + 32 +
-           (NC + 1) / 2 + 2 + 2;
+           (NC + 1) / 2 + 2 + 2 + (refine ? 9 * NC : 0);
 }
 
-__device__ __forceinline__ PointSmem carve(double *base, int NC)
+// global scratch of one point group in the refined solver: the FP64 reduced
+// matrix S (packed lower triangle of order NC - 4)
+__host__ __device__ inline int64_t point_scratch_doubles(int NC)
+{
+    return (int64_t)(NC - 4) * (NC - 3) / 2;
+}
+
+__device__ __forceinline__ PointSmem carve(double *base, int NC, bool refine)
 {
     PointSmem w;
     double *p = base;
@@ -156,7 +289,14 @@ __device__ __forceinline__ PointSmem carve(double *base, int NC)
     w.redv = (float *)p; p += 32;
     w.redj = (int *)p; p += 32;
     w.r2o = (int *)p; p += (NC + 1) / 2;
-    w.piv = p;
+    w.piv = p; p += 2 + 2;
+    w.rhs = w.a = nullptr;
+    w.ivs = nullptr;
+    if (refine) {
+        w.rhs = p; p += 4 * NC;
+        w.a = p; p += 4 * NC;
+        w.ivs = (float2 *)p;
+    }
     return w;
 }
 
@@ -188,16 +328,6 @@ __device__ __forceinline__ double det3(double a, double b, double c, double d, d
     return a * fma(e, i, -f * h) - b * fma(d, i, -f * g) + c * fma(d, h, -e * g);
 }
 
-// position (i, j), i >= j, of linear index u of a packed lower triangle
-__device__ __forceinline__ void tri_decode(int u, int &i, int &j)
-{
-    int r = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
-    while ((r + 1) * (r + 2) / 2 <= u) r++;
-    while (r * (r + 1) / 2 > u) r--;
-    i = r;
-    j = u - r * (r + 1) / 2;
-}
-
 // Thread roles inside one point group of G warps.
 struct Group {
     int GT, gt, lane, wig, G, bar;
@@ -205,12 +335,18 @@ struct Group {
 
 // Shape functions of point p by one group (all G*32 threads of the group
 // call it; the phases are separated by the group's named barrier).
+//
+// REFINE selects the solver of step 7 onwards: false factors S in FP64;
+// true factors it in float-float arithmetic and recovers FP64 accuracy by
+// one step of iterative refinement with the residual in FP64 (Sg: the
+// group's global scratch, which holds S in FP64 for the residual).
+template <bool REFINE>
 __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries &ks, const PointSmem &W, const int NC,
                                             const Group &gr, const double *__restrict__ pts,
                                             const int32_t *__restrict__ inst_of, int shift,
                                             const InstGrid *__restrict__ ig, const int64_t *__restrict__ soff,
                                             const int32_t *__restrict__ sidx, const double *__restrict__ xyz,
-                                            double *__restrict__ phi, DevError *err)
+                                            double *__restrict__ phi, double *__restrict__ Sg, DevError *err)
 {
     const int GT = gr.GT, gt = gr.gt, lane = gr.lane, wig = gr.wig, G = gr.G, bar = gr.bar;
     const double c2 = ks.c2;
@@ -406,12 +542,16 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
     // 6. S = A_rr - Y C - C' Y' (packed lower triangle, rows 0..m-1),
     //    then the reduced right-hand sides as rows m..m+3 (entries
     //    j < m), so that the elimination below also performs the
-    //    forward substitution
+    //    forward substitution. The refined solver keeps S and the
+    //    right-hand sides in FP64 as well (S in the group's global scratch,
+    //    which stays in L2) for the residual of step 8.
+    float2 *SF = (float2 *)W.S;     // the triangle as float-float pairs (refined solver)
+    float2 *PF = (float2 *)W.piv;   // reciprocal of the next pivot (refined solver)
     {
         const int T = m * (m + 1) / 2;
         for (int u = gt; u < T; u += GT) {
             int i, j;
-            tri_decode(u, i, j);
+            tri_decode_fast(u, i, j);
             const int oi = W.r2o[i], oj = W.r2o[j];
             double a;
             if (i == j) {
@@ -425,8 +565,15 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
                 a = fma(-W.Y[k * NC + i], W.C[k * NC + j], a);
                 a = fma(-W.C[k * NC + i], W.Y[k * NC + j], a);
             }
-            W.S[u] = a;
-            if (u == 0) W.piv[0] = positive_normal(a) ? recip_nr(a) : 0.0;  // first pivot
+            if constexpr (REFINE) {
+                Sg[u] = a;
+                const float2 af = ff_from_f64(a);
+                SF[u] = af;
+                if (u == 0) PF[0] = ff_pivot_ok(af) ? ff_recip(af) : make_float2(0.0f, 0.0f);   // first pivot
+            } else {
+                W.S[u] = a;
+                if (u == 0) W.piv[0] = positive_normal(a) ? recip_nr(a) : 0.0;  // first pivot
+            }
         }
     }
     for (int t = gt; t < 4 * (m + 4); t += GT) {
@@ -438,7 +585,12 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
 #pragma unroll
             for (int k = 0; k < 4; k++) acc = fma(-W.C[k * NC + r], W.v[q * NC + pivot(k)], acc);
         }
-        if (r <= m + q) W.S[(m + q) * (m + q + 1) / 2 + r] = acc;
+        if constexpr (REFINE) {
+            if (r < m) W.rhs[q * NC + r] = acc;
+            if (r <= m + q) SF[(m + q) * (m + q + 1) / 2 + r] = ff_from_f64(acc);
+        } else {
+            if (r <= m + q) W.S[(m + q) * (m + q + 1) / 2 + r] = acc;
+        }
     }
     group_sync(bar, GT);
 
@@ -446,34 +598,65 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
     //    triangle; W.v holds the unscaled column of the current step.
     //    After step m-1 the rhs rows hold z = D^-1 L^-1 rhs.
     const int M2 = m + 4;
-    double *col = W.v;
     bool ok = true;
     //    The reciprocal of each pivot is computed once, by the thread
     //    that finishes the pivot (u == 0 of the previous update), and read
     //    from shared memory by the group: replicated in every warp it
     //    would cost each warp a full FP64 issue slot per instruction.
-    for (int k = 0; k < m; k++) {
-        const double iv = W.piv[0];
-        if (!(iv > 0.0)) { ok = false; break; }
-        for (int i = k + 1 + gt; i < M2; i += GT) {
-            const int ik = i * (i + 1) / 2 + k;
-            const double a = W.S[ik];
-            col[i] = a;
-            W.S[ik] = a * iv;
+    if constexpr (REFINE) {
+        //    Float-float elimination; the trailing-triangle index of each
+        //    update is decoded with the approximate square root (the exact
+        //    one would cost more than the update itself here).
+        float2 *col = (float2 *)W.v;
+        for (int k = 0; k < m; k++) {
+            const float2 iv = PF[0];
+            if (!(iv.x > 0.0f)) { ok = false; break; }
+            if (gt == 0) W.ivs[k] = iv;
+            for (int i = k + 1 + gt; i < M2; i += GT) {
+                const int ik = i * (i + 1) / 2 + k;
+                const float2 a = SF[ik];
+                col[i] = a;
+                SF[ik] = ff_mul(a, iv);
+            }
+            group_sync(bar, GT);
+            const int tk = M2 - k - 1;
+            const int T = tk * (tk + 1) / 2;
+            for (int u = gt; u < T; u += GT) {
+                int ri, rj;
+                tri_decode_fast(u, ri, rj);
+                const int i = k + 1 + ri, j = k + 1 + rj;
+                const int ib = i * (i + 1) / 2;
+                const float2 nv = ff_fnma(SF[ib + k], col[j], SF[ib + j]);
+                SF[ib + j] = nv;
+                if (u == 0 && k + 1 < m) PF[0] = ff_pivot_ok(nv) ? ff_recip(nv) : make_float2(0.0f, 0.0f);
+            }
+            group_sync(bar, GT);
         }
-        group_sync(bar, GT);
-        const int tk = M2 - k - 1;
-        const int T = tk * (tk + 1) / 2;
-        for (int u = gt; u < T; u += GT) {
-            int ri, rj;
-            tri_decode(u, ri, rj);
-            const int i = k + 1 + ri, j = k + 1 + rj;
-            const int ib = i * (i + 1) / 2;
-            const double nv = fma(-W.S[ib + k], col[j], W.S[ib + j]);
-            W.S[ib + j] = nv;
-            if (u == 0 && k + 1 < m) W.piv[0] = positive_normal(nv) ? recip_nr(nv) : 0.0;
+    } else {
+        double *col = W.v;
+        for (int k = 0; k < m; k++) {
+            const double iv = W.piv[0];
+            if (!(iv > 0.0)) { ok = false; break; }
+            for (int i = k + 1 + gt; i < M2; i += GT) {
+                const int ik = i * (i + 1) / 2 + k;
+                const double a = W.S[ik];
+                col[i] = a;
+                W.S[ik] = a * iv;
+            }
+            group_sync(bar, GT);
+            const int tk = M2 - k - 1;
+            const int T = tk * (tk + 1) / 2;
+            for (int u = gt; u < T; u += GT) {
+                int ri, rj;
+                tri_decode_fast(u, ri, rj);
+                const int i = k + 1 + ri, j = k + 1 + rj;
+                const int ib = i * (i + 1) / 2;
+                const double nv = fma(-W.S[ib + k], col[j], W.S[ib + j]);
+                W.S[ib + j] = nv;
+                if (u == 0 && k + 1 < m) W.piv[0] = positive_normal(nv) ? recip_nr(nv) : 0.0;
+            }
+            group_sync(bar, GT);
         }
-        group_sync(bar, GT);
     }
     if (!ok) {
         if (gt == 0) dev_fail(err, RPIM_E_SINGULAR, p);
@@ -483,15 +666,97 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
 
     // 8. L' a = z, column by column; threads over (row, rhs) pairs
     double *Z0 = W.S + (size_t)m * (m + 1) / 2;  // rhs row q starts at Z0 + q*m + q*(q+1)/2
-    for (int k = m - 1; k > 0; k--) {
-        const int kb = k * (k + 1) / 2;
-        for (int t = gt; t < 4 * k; t += GT) {
+    if constexpr (REFINE) {
+        float2 *Z0f = SF + (size_t)m * (m + 1) / 2;
+        for (int k = m - 1; k > 0; k--) {
+            const int kb = k * (k + 1) / 2;
+            for (int t = gt; t < 4 * k; t += GT) {
+                const int q = t & 3, i = t >> 2;
+                float2 *zq = Z0f + q * m + q * (q + 1) / 2;
+                zq[i] = ff_fnma(SF[kb + i], zq[k], zq[i]);
+            }
+            group_sync(bar, GT);
+        }
+        for (int t = gt; t < 4 * m; t += GT) {
             const int q = t & 3, i = t >> 2;
-            double *zq = Z0 + q * m + q * (q + 1) / 2;
-            zq[i] = fma(-W.S[kb + i], zq[k], zq[i]);
+            W.a[q * NC + i] = ff_to_f64(Z0f[q * m + q * (q + 1) / 2 + i]);
         }
         group_sync(bar, GT);
+        //    One step of iterative refinement: the residual rhs - S a in
+        //    FP64 (one thread per row, ascending column order), then the
+        //    correction from the float-float factors (L y = r, D z = y,
+        //    L' e = z) added to a in FP64.
+        float2 *R = (float2 *)W.v;   // [4][NC]
+        for (int i = gt; i < m; i += GT) {
+            double r0 = W.rhs[i], r1 = W.rhs[NC + i], r2 = W.rhs[2 * NC + i], r3 = W.rhs[3 * NC + i];
+            // row i of S: (i, j) for j <= i, then (j, i) for j > i (not
+            // unrolled: unrolling spills the kernel's registers)
+            const double *srow = Sg + i * (i + 1) / 2;
+#pragma unroll 1
+            for (int j = 0; j <= i; j++) {
+                const double sv = srow[j];
+                r0 = fma(-sv, W.a[j], r0);
+                r1 = fma(-sv, W.a[NC + j], r1);
+                r2 = fma(-sv, W.a[2 * NC + j], r2);
+                r3 = fma(-sv, W.a[3 * NC + j], r3);
+            }
+            int pos = (i + 1) * (i + 2) / 2 + i;   // (i + 1, i)
+#pragma unroll 1
+            for (int j = i + 1; j < m; j++) {
+                const double sv = Sg[pos];
+                pos += j + 1;
+                r0 = fma(-sv, W.a[j], r0);
+                r1 = fma(-sv, W.a[NC + j], r1);
+                r2 = fma(-sv, W.a[2 * NC + j], r2);
+                r3 = fma(-sv, W.a[3 * NC + j], r3);
+            }
+            R[i] = ff_from_f64(r0);
+            R[NC + i] = ff_from_f64(r1);
+            R[2 * NC + i] = ff_from_f64(r2);
+            R[3 * NC + i] = ff_from_f64(r3);
+        }
+        group_sync(bar, GT);
+        for (int k = 0; k + 1 < m; k++) {
+            for (int t = gt; t < 4 * (m - 1 - k); t += GT) {
+                const int q = t & 3, i = k + 1 + (t >> 2);
+                R[q * NC + i] = ff_fnma(SF[i * (i + 1) / 2 + k], R[q * NC + k], R[q * NC + i]);
+            }
+            group_sync(bar, GT);
+        }
+        for (int t = gt; t < 4 * m; t += GT) {
+            const int q = t & 3, i = t >> 2;
+            R[q * NC + i] = ff_mul(R[q * NC + i], W.ivs[i]);
+        }
+        group_sync(bar, GT);
+        for (int k = m - 1; k > 0; k--) {
+            const int kb = k * (k + 1) / 2;
+            for (int t = gt; t < 4 * k; t += GT) {
+                const int q = t & 3, i = t >> 2;
+                R[q * NC + i] = ff_fnma(SF[kb + i], R[q * NC + k], R[q * NC + i]);
+            }
+            group_sync(bar, GT);
+        }
+        for (int t = gt; t < 4 * m; t += GT) {
+            const int q = t & 3, i = t >> 2;
+            W.a[q * NC + i] += ff_to_f64(R[q * NC + i]);
+        }
+        group_sync(bar, GT);
+    } else {
+        for (int k = m - 1; k > 0; k--) {
+            const int kb = k * (k + 1) / 2;
+            for (int t = gt; t < 4 * k; t += GT) {
+                const int q = t & 3, i = t >> 2;
+                double *zq = Z0 + q * m + q * (q + 1) / 2;
+                zq[i] = fma(-W.S[kb + i], zq[k], zq[i]);
+            }
+            group_sync(bar, GT);
+        }
     }
+    // a_r of right-hand side q (r < m)
+    auto ar_of = [&](int q, int r) -> double {
+        if constexpr (REFINE) return W.a[q * NC + r];
+        else return Z0[q * m + q * (q + 1) / 2 + r];
+    };
 
     // 9. pivot values a_p = d - C a_r: 16 sums over the rest rows, by the
     //    group's first warp alone (lane-strided partial sums, then
@@ -505,7 +770,7 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
         for (int r = lane; r < m; r += 32) {
             double ar[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) ar[q] = Z0[q * m + q * (q + 1) / 2 + r];
+            for (int q = 0; q < 4; q++) ar[q] = ar_of(q, r);
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const double c = W.C[k * NC + r];
@@ -531,8 +796,8 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
     bool finite = true;
     for (int r = gt; r < m; r += GT) {
         const int j = W.r2o[r];
-        double2 lo2 = make_double2(Z0[r], Z0[m + 1 + r] * inv_h);
-        double2 hi2 = make_double2(Z0[2 * m + 3 + r] * inv_h, Z0[3 * m + 6 + r] * inv_h);
+        double2 lo2 = make_double2(ar_of(0, r), ar_of(1, r) * inv_h);
+        double2 hi2 = make_double2(ar_of(2, r) * inv_h, ar_of(3, r) * inv_h);
         finite &= isfinite(lo2.x) && isfinite(lo2.y) && isfinite(hi2.x) && isfinite(hi2.y);
         *(double2 *)(out + 4 * j) = lo2;
         *(double2 *)(out + 4 * j + 2) = hi2;
@@ -559,6 +824,10 @@ __global__ void recip_probe_kernel(int64_t n, const double *__restrict__ d, doub
 // One group of G warps per point. Every loop below is a flattened parallel
 // loop over the group's G*32 threads; the phases are separated by a named
 // barrier of the group. Groups of one block are independent.
+// scratch: the refined solver's FP64 copy of S, point_scratch_doubles(NC)
+// per point group, group g of block b at (b * ppb + g) (unused otherwise;
+// every block of this kernel works with the same NC and ppb).
+template <bool REFINE>
 __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double *__restrict__ pts,
                                                      const int32_t *__restrict__ inst_of, int shift,
                                                      const InstGrid *__restrict__ ig,
@@ -567,7 +836,8 @@ __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double
                                                      const int32_t *__restrict__ sidx,
                                                      const double *__restrict__ xyz,
                                                      const KernelSeries *__restrict__ ks_g,
-                                                     double *__restrict__ phi, int NC, int G, DevError *err)
+                                                     double *__restrict__ phi, int NC, int G,
+                                                     double *__restrict__ scratch, DevError *err)
 {
     extern __shared__ double dsm[];
     __shared__ KernelSeries ks;
@@ -583,13 +853,14 @@ __global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double
     const int lane = threadIdx.x & 31, wig = gt >> 5;
     const int ppb = blockDim.x / GT;
     const int bar = 1 + grp;
-    PointSmem W = carve(dsm + (size_t)grp * point_smem_doubles(NC), NC);
+    PointSmem W = carve(dsm + (size_t)grp * point_smem_doubles(NC, REFINE), NC, REFINE);
+    double *Sg = REFINE ? scratch + ((size_t)blockIdx.x * ppb + grp) * point_scratch_doubles(NC) : nullptr;
     const int64_t stride = (int64_t)gridDim.x * ppb;
 
     const Group gr{GT, gt, lane, wig, G, bar};
     for (int64_t pk = (int64_t)blockIdx.x * ppb + grp; pk < n_pts; pk += stride) {
         const int64_t p = order ? (int64_t)order[pk] : pk;
-        shape_point(p, ks, W, NC, gr, pts, inst_of, shift, ig, soff, sidx, xyz, phi, err);
+        shape_point<REFINE>(p, ks, W, NC, gr, pts, inst_of, shift, ig, soff, sidx, xyz, phi, Sg, err);
     }
 }
 
@@ -602,6 +873,7 @@ struct BucketPlan {
     int nb;
     int pad;
     long long total;                       // points of all buckets
+    long long block_scratch;               // refined solver: scratch doubles of one block (largest bucket)
     int NC[kMaxTileBuckets], G[kMaxTileBuckets], ppb[kMaxTileBuckets];
     long long start[kMaxTileBuckets];      // first position of the bucket in the order list
     long long count[kMaxTileBuckets];      // points of the bucket
@@ -616,6 +888,7 @@ struct BucketPlan {
 // and buffers change between them. Every value is computed by the same
 // thread-level formula as in shape_kernel, whatever the launch shape, so the
 // results are bitwise those of the per-bucket launches.
+template <bool REFINE>
 __global__ void __launch_bounds__(1024) shape_tiles_kernel(const BucketPlan plan, unsigned long long *counters,
                                                            const double *__restrict__ pts,
                                                            const int32_t *__restrict__ inst_of, int shift,
@@ -625,7 +898,8 @@ __global__ void __launch_bounds__(1024) shape_tiles_kernel(const BucketPlan plan
                                                            const int32_t *__restrict__ sidx,
                                                            const double *__restrict__ xyz,
                                                            const KernelSeries *__restrict__ ks_g,
-                                                           double *__restrict__ phi, DevError *err)
+                                                           double *__restrict__ phi, double *__restrict__ scratch,
+                                                           DevError *err)
 {
     extern __shared__ double dsm[];
     __shared__ KernelSeries ks;
@@ -638,6 +912,8 @@ __global__ void __launch_bounds__(1024) shape_tiles_kernel(const BucketPlan plan
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    // every block owns one fixed region of the scratch, sized for its largest
+    // bucket (blocks work on different buckets at the same time)
     for (int b = 0; b < plan.nb; b++) {
         const int G = plan.G[b], ppb = plan.ppb[b], NC = plan.NC[b];
         const int GT = G * 32;
@@ -645,7 +921,10 @@ __global__ void __launch_bounds__(1024) shape_tiles_kernel(const BucketPlan plan
         if (grp < ppb) {
             const int gt = threadIdx.x - grp * GT;
             const Group gr{GT, gt, lane, gt >> 5, G, 1 + grp};
-            const PointSmem W = carve(dsm + (size_t)grp * point_smem_doubles(NC), NC);
+            const PointSmem W = carve(dsm + (size_t)grp * point_smem_doubles(NC, REFINE), NC, REFINE);
+            double *Sg = REFINE ? scratch + (size_t)blockIdx.x * plan.block_scratch +
+                                      (size_t)grp * point_scratch_doubles(NC)
+                                : nullptr;
             for (;;) {
                 if (gt == 0) s_next[grp] = (long long)atomicAdd(&counters[b], 1ull);
                 group_sync(1 + grp, GT);
@@ -653,7 +932,7 @@ __global__ void __launch_bounds__(1024) shape_tiles_kernel(const BucketPlan plan
                 group_sync(1 + grp, GT);   // every thread holds pk before the next fetch
                 if (pk >= plan.count[b]) break;
                 const int64_t p = (int64_t)order[plan.start[b] + pk];
-                shape_point(p, ks, W, NC, gr, pts, inst_of, shift, ig, soff, sidx, xyz, phi, err);
+                shape_point<REFINE>(p, ks, W, NC, gr, pts, inst_of, shift, ig, soff, sidx, xyz, phi, Sg, err);
             }
         }
         __syncthreads();
@@ -670,45 +949,60 @@ struct ShapeCfg {
 };
 
 static std::mutex g_tune_mu;
-static ShapeCfg g_tuned[RPIM_MAX_SUPPORT + 1];
+static ShapeCfg g_tuned[2][RPIM_MAX_SUPPORT + 1];   // per solver
 
-static size_t point_bytes(int NC) { return (size_t)point_smem_doubles(NC) * sizeof(double); }
+static std::atomic<int> g_solver{RPIM_SOLVER_FP64};
+
+static bool refined() { return g_solver.load() == RPIM_SOLVER_REFINED; }
+
+// (every host path reads the solver once and passes it down, so that the
+// shared memory it sizes and the kernel it launches always agree)
+static size_t point_bytes(int NC, bool ref) { return (size_t)point_smem_doubles(NC, ref) * sizeof(double); }
 
 constexpr size_t kShapeSmemBudget = 216 * 1024;
 constexpr int kMaxGroupWarps = 16;   // warps per point group (argmax buffers hold 16)
 
-static bool cfg_valid(int NC, ShapeCfg c)
+static bool cfg_valid(int NC, ShapeCfg c, bool ref)
 {
     return c.G >= 1 && c.G <= kMaxGroupWarps && c.ppb >= 1 && c.ppb <= 15 && c.ppb * c.G * 32 <= 1024 &&
-           (size_t)c.ppb * point_bytes(NC) <= kShapeSmemBudget;
+           (size_t)c.ppb * point_bytes(NC, ref) <= kShapeSmemBudget;
 }
 
-static ShapeCfg default_cfg(int NC)
+static ShapeCfg default_cfg(int NC, bool ref)
 {
     ShapeCfg c;
-    c.ppb = (int)std::min<size_t>(15, kShapeSmemBudget / point_bytes(NC));  // points (groups) per block
+    c.ppb = (int)std::min<size_t>(15, kShapeSmemBudget / point_bytes(NC, ref));  // points (groups) per block
     c.G = std::max(1, std::min(c.ppb <= 2 ? 8 : 4, 32 / std::max(1, c.ppb)));   // warps per point
     return c;
 }
 
-static ShapeCfg shape_cfg(int NC)
+static ShapeCfg shape_cfg(int NC, bool ref)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    const ShapeCfg t = g_tuned[std::min(NC, RPIM_MAX_SUPPORT)];
-    return cfg_valid(NC, t) ? t : default_cfg(NC);
+    const ShapeCfg t = g_tuned[ref][std::min(NC, RPIM_MAX_SUPPORT)];
+    return cfg_valid(NC, t, ref) ? t : default_cfg(NC, ref);
 }
 
 static rpim_status launch_shape(rpim_pattern *p, int64_t n_pts, const double *pts, const int32_t *inst_of, int shift,
                                 const int32_t *order, const int64_t *soff, const int32_t *sidx, int NC, ShapeCfg c,
-                                double *phi, cudaStream_t s, const char *tag)
+                                bool ref, double *phi, cudaStream_t s, const char *tag)
 {
-    const size_t smem = (size_t)c.ppb * point_bytes(NC);
-    RPIM_CUDA(cudaFuncSetAttribute(shape_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = (size_t)c.ppb * point_bytes(NC, ref);
     int64_t blocks = std::min<int64_t>((int64_t)p->sm_count, (n_pts + c.ppb - 1) / c.ppb);
     if (blocks < 1) blocks = 1;
-    launch(tag, shape_kernel, (unsigned)blocks, c.ppb * c.G * 32, smem, s, n_pts, pts, inst_of, shift,
-           (const InstGrid *)p->ig, order, soff, sidx, (const double *)p->xyz, (const KernelSeries *)p->series, phi,
-           NC, c.G, p->err);
+    if (ref) {
+        if (blocks * c.ppb * point_scratch_doubles(NC) > p->shape_scratch_doubles)
+            return fail(RPIM_E_ARG, "shape scratch too small for the launch");
+        RPIM_CUDA(cudaFuncSetAttribute(shape_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        launch(tag, shape_kernel<true>, (unsigned)blocks, c.ppb * c.G * 32, smem, s, n_pts, pts, inst_of, shift,
+               (const InstGrid *)p->ig, order, soff, sidx, (const double *)p->xyz, (const KernelSeries *)p->series,
+               phi, NC, c.G, p->shape_scratch, p->err);
+    } else {
+        RPIM_CUDA(cudaFuncSetAttribute(shape_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        launch(tag, shape_kernel<false>, (unsigned)blocks, c.ppb * c.G * 32, smem, s, n_pts, pts, inst_of, shift,
+               (const InstGrid *)p->ig, order, soff, sidx, (const double *)p->xyz, (const KernelSeries *)p->series,
+               phi, NC, c.G, (double *)nullptr, p->err);
+    }
     RPIM_CUDA(cudaGetLastError());
     return RPIM_OK;
 }
@@ -722,8 +1016,9 @@ rpim_status shape_functions(rpim_pattern *p, int64_t n_pts, const double *pts, c
     if (p->shape_kind != RPIM_SHAPE_RPIM)   // MLS or Shepard
         return mls_shape_functions(p, n_pts, pts, inst_of, shift, order, soff, sidx, phi, s, tag);
     const int NC = std::max(8, (int)max_n);
-    if (point_bytes(NC) > kShapeSmemBudget) return fail(RPIM_E_SUPPORT, "support too large for shared memory");
-    return launch_shape(p, n_pts, pts, inst_of, shift, order, soff, sidx, NC, shape_cfg(NC), phi, s, tag);
+    const bool ref = refined();
+    if (point_bytes(NC, ref) > kShapeSmemBudget) return fail(RPIM_E_SUPPORT, "support too large for shared memory");
+    return launch_shape(p, n_pts, pts, inst_of, shift, order, soff, sidx, NC, shape_cfg(NC, ref), ref, phi, s, tag);
 }
 
 static std::atomic<int> g_persistent{1};
@@ -744,7 +1039,7 @@ static rpim_status shape_functions_buckets(rpim_pattern *p, double *phi, cudaStr
 // Plan of the persistent launch over the pattern's buckets (a sample of
 // `frac` of every bucket when tuning). Returns the shared memory and threads
 // per block and the largest number of blocks with work.
-static rpim_status bucket_plan(const rpim_pattern *p, double frac, BucketPlan *plan, size_t *smem_out,
+static rpim_status bucket_plan(const rpim_pattern *p, double frac, bool ref, BucketPlan *plan, size_t *smem_out,
                                int *threads_out, int64_t *blocks_out)
 {
     *plan = BucketPlan{};
@@ -757,8 +1052,8 @@ static rpim_status bucket_plan(const rpim_pattern *p, double frac, BucketPlan *p
         if (cnt > 0) {
             if (p->bucket_nc[b] > RPIM_MAX_SUPPORT) return fail(RPIM_E_SUPPORT, "support larger than RPIM_MAX_SUPPORT");
             const int NC = std::max(8, (int)p->bucket_nc[b]);
-            if (point_bytes(NC) > kShapeSmemBudget) return fail(RPIM_E_SUPPORT, "support too large for shared memory");
-            bs.push_back(B{NC, shape_cfg(NC), start, cnt});
+            if (point_bytes(NC, ref) > kShapeSmemBudget) return fail(RPIM_E_SUPPORT, "support too large for shared memory");
+            bs.push_back(B{NC, shape_cfg(NC, ref), start, cnt});
         }
         start += full;
     }
@@ -775,7 +1070,8 @@ static rpim_status bucket_plan(const rpim_pattern *p, double frac, BucketPlan *p
         plan->start[b] = bs[b].start;
         plan->count[b] = bs[b].count;
         plan->total += bs[b].count;
-        smem = std::max(smem, (size_t)bs[b].c.ppb * point_bytes(bs[b].NC));
+        smem = std::max(smem, (size_t)bs[b].c.ppb * point_bytes(bs[b].NC, ref));
+        plan->block_scratch = std::max<long long>(plan->block_scratch, (long long)bs[b].c.ppb * point_scratch_doubles(bs[b].NC));
         threads = std::max(threads, bs[b].c.ppb * bs[b].c.G * 32);
         blocks = std::max<int64_t>(blocks, (bs[b].count + bs[b].c.ppb - 1) / bs[b].c.ppb);
     }
@@ -791,18 +1087,22 @@ static rpim_status shape_functions_tiles(rpim_pattern *p, double *phi, cudaStrea
     size_t smem = 0;
     int threads = 0;
     int64_t need = 0;
-    RPIM_CHECK(bucket_plan(p, frac, &plan, &smem, &threads, &need));
+    const bool ref = refined();
+    RPIM_CHECK(bucket_plan(p, frac, ref, &plan, &smem, &threads, &need));
     if (plan.total == 0) return RPIM_OK;
     if (!p->tile_counter) RPIM_CHECK(dalloc(&p->tile_counter, kMaxTileBuckets, s));
     RPIM_CUDA(cudaMemsetAsync(p->tile_counter, 0, kMaxTileBuckets * sizeof(unsigned long long), s));
-    RPIM_CUDA(cudaFuncSetAttribute(shape_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = ref ? shape_tiles_kernel<true> : shape_tiles_kernel<false>;
+    RPIM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    RPIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shape_tiles_kernel, threads, smem));
+    RPIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)p->sm_count * std::max(1, per_sm), need));
-    launch("shape", shape_tiles_kernel, (unsigned)blocks, threads, smem, s, plan, p->tile_counter,
-           (const double *)p->pts, (const int32_t *)p->node_inst, 3, (const InstGrid *)p->ig,
-           (const int32_t *)p->bucket_order, (const int64_t *)p->soff, (const int32_t *)p->sidx,
-           (const double *)p->xyz, (const KernelSeries *)p->series, phi, p->err);
+    if (ref && blocks * plan.block_scratch > p->shape_scratch_doubles)
+        return fail(RPIM_E_ARG, "shape scratch too small for the launch");
+    launch("shape", kern, (unsigned)blocks, threads, smem, s, plan, p->tile_counter, (const double *)p->pts,
+           (const int32_t *)p->node_inst, 3, (const InstGrid *)p->ig, (const int32_t *)p->bucket_order,
+           (const int64_t *)p->soff, (const int32_t *)p->sidx, (const double *)p->xyz,
+           (const KernelSeries *)p->series, phi, ref ? p->shape_scratch : (double *)nullptr, p->err);
     RPIM_CUDA(cudaGetLastError());
     return RPIM_OK;
 }
@@ -817,21 +1117,22 @@ rpim_status shape_launch_key(const rpim_pattern *p, std::vector<unsigned char> *
         const unsigned char *c = (const unsigned char *)a;
         key->insert(key->end(), c, c + n);
     };
-    const int kind = p->shape_kind, sched = g_persistent.load();
+    const int kind = p->shape_kind, sched = g_persistent.load(), solver = g_solver.load();
     put(&kind, sizeof kind);
     put(&sched, sizeof sched);
+    put(&solver, sizeof solver);
     if (kind == RPIM_SHAPE_RPIM) {
         if (sched) {
             BucketPlan plan;
             size_t smem = 0;
             int threads = 0;
             int64_t blocks = 0;
-            RPIM_CHECK(bucket_plan(p, 1.0, &plan, &smem, &threads, &blocks));
+            RPIM_CHECK(bucket_plan(p, 1.0, solver == RPIM_SOLVER_REFINED, &plan, &smem, &threads, &blocks));
             put(&plan, sizeof plan);
         } else {
             for (size_t b = 0; b < p->bucket_count.size(); b++) {
                 const int NC = std::max(8, (int)p->bucket_nc[b]);
-                const ShapeCfg c = shape_cfg(NC);
+                const ShapeCfg c = shape_cfg(NC, solver == RPIM_SOLVER_REFINED);
                 put(&p->bucket_count[b], sizeof(int64_t));
                 put(&NC, sizeof NC);
                 put(&c, sizeof c);
@@ -874,24 +1175,26 @@ extern "C" rpim_status rpim_autotune_shape(rpim_pattern *p, int64_t max_points, 
     int nt = 0;
     int64_t start = 0;
     rpim_status st = RPIM_OK;
+    const bool ref = refined();
     for (size_t bk = 0; bk < p->bucket_count.size() && st == RPIM_OK; bk++) {
         const int64_t cnt = std::min<int64_t>(p->bucket_count[bk], max_points);
         const int NC = std::max(8, (int)p->bucket_nc[bk]);
         const int32_t *order = p->bucket_order + start;
         start += p->bucket_count[bk];
-        if (cnt == 0 || point_bytes(NC) > kShapeSmemBudget) continue;
-        ShapeCfg best = default_cfg(NC);
+        if (cnt == 0 || point_bytes(NC, ref) > kShapeSmemBudget) continue;
+        ShapeCfg best = default_cfg(NC, ref);
         float best_ms = 1e30f;
         for (int G : {1, 2, 3, 4, 6, 8, 12, 16})
             for (int ppb = 1; ppb <= 15 && st == RPIM_OK; ppb++) {
                 const ShapeCfg c{ppb, G};
-                if (!cfg_valid(NC, c)) continue;
+                if (!cfg_valid(NC, c, ref)) continue;
                 // skip launch shapes that cannot fill the SMs' warp slots
-                if (ppb * G < 4 && !(ppb == default_cfg(NC).ppb && G == default_cfg(NC).G)) continue;
+                if (ppb * G < 4 && !(ppb == default_cfg(NC, ref).ppb && G == default_cfg(NC, ref).G)) continue;
                 float ms = 1e30f;
                 for (int rep = 0; rep < 3 && st == RPIM_OK; rep++) {
                     if (cudaEventRecord(e0, s) != cudaSuccess) { st = fail(RPIM_E_CUDA, "tune: event"); break; }
-                    st = launch_shape(p, cnt, p->pts, p->node_inst, 3, order, p->soff, p->sidx, NC, c, p->phi, s, "tune");
+                    st = launch_shape(p, cnt, p->pts, p->node_inst, 3, order, p->soff, p->sidx, NC, c, ref, p->phi, s,
+                                      "tune");
                     if (st != RPIM_OK) break;
                     if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
                         st = fail(RPIM_E_CUDA, "tune: event");
@@ -906,7 +1209,7 @@ extern "C" rpim_status rpim_autotune_shape(rpim_pattern *p, int64_t max_points, 
         if (st != RPIM_OK) break;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tuned[std::min(NC, RPIM_MAX_SUPPORT)] = best;
+            g_tuned[ref][std::min(NC, RPIM_MAX_SUPPORT)] = best;
         }
         if (table && nt < 16) {
             table[3 * nt] = NC;
@@ -940,10 +1243,11 @@ extern "C" rpim_status rpim_autotune_set(int32_t max_support, int32_t warps_per_
 {
     const int NC = std::max(8, (int)max_support);
     const ShapeCfg c{points_per_block, warps_per_point};
-    if (max_support < 1 || max_support > RPIM_MAX_SUPPORT || !cfg_valid(NC, c))
+    const bool ref = refined();
+    if (max_support < 1 || max_support > RPIM_MAX_SUPPORT || !cfg_valid(NC, c, ref))
         return fail(RPIM_E_ARG, "launch shape not admissible for this support size");
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[NC] = c;
+    g_tuned[ref][NC] = c;
     return RPIM_OK;
 }
 
@@ -951,9 +1255,24 @@ extern "C" rpim_status rpim_autotune_reset(void)
 {
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        for (auto &c : g_tuned) c = ShapeCfg{};
+        for (auto &t : g_tuned)
+            for (auto &c : t) c = ShapeCfg{};
     }
     set_default_buckets({});
+    return RPIM_OK;
+}
+
+extern "C" rpim_status rpim_set_shape_solver(int32_t solver)
+{
+    if (solver != RPIM_SOLVER_FP64 && solver != RPIM_SOLVER_REFINED) return fail(RPIM_E_ARG, "unknown solver");
+    g_solver.store(solver);
+    return RPIM_OK;
+}
+
+extern "C" rpim_status rpim_get_shape_solver(int32_t *solver)
+{
+    if (!solver) return fail(RPIM_E_ARG, "null argument");
+    *solver = g_solver.load();
     return RPIM_OK;
 }
 
