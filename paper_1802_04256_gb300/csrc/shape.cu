@@ -237,25 +237,47 @@ __device__ __forceinline__ void series_A_dA(const KernelSeries &ks, double s, do
     dA = dv;
 }
 
+// Shared memory of one point group: fields at fixed offsets (in doubles)
+// from one base; each accessor computes its address where it is used, so
+// the group's sixteen arrays cost no registers between uses.
+//   xi   [3][NC]  local coordinates
+//   xf   [3][NC]  single-precision copy for the pivot search
+//   C    [4][NC]  C[k][r]
+//   Y    [4][NC]  A_rp then Y
+//   v    [4][NC]  v[rhs][j] (original order); column buffers later
+//   S    packed lower triangle of order NC: S, then 4 rhs rows (float-float
+//        pairs in the refined solver)
+//   M    [16] P_p^{-T}, row-major;  App [16];  red [4 * 16] partial sums of
+//        the pivot values;  redv/redj [4 passes][16 warps] argmax values and
+//        indices;  r2o [NC] rest index -> original index;  piv [16] pivot
+//        block of the next elimination step
+//   refined solver only: rhs [4][NC] reduced right-hand sides (FP64),
+//        a [4][NC] solution a_r (FP64), ivs [NC] reciprocal pivots
 struct PointSmem {
-    double *xi;     // [3][NC]
-    float *xf;      // [3][NC] single-precision copy for the pivot search
-    double *C;      // [4][NC]  C[k][r]
-    double *Y;      // [4][NC]  A_rp then Y
-    double *v;      // [4][NC]  v[rhs][j] (original order); column buffer later
-    double *S;      // packed lower triangle of order NC: S, then 4 rhs rows
-                    // (float-float pairs in the refined solver)
-    double *M;      // [16] P_p^{-T}, row-major
-    double *App;    // [16]
-    double *red;    // [4 * 16] per-warp partial sums of the pivot values
-    float *redv;    // [4 passes][16 warps] argmax values
-    int *redj;      // [4 passes][16 warps] argmax indices
-    int *r2o;       // [NC] rest index -> original index
-    double *piv;    // [2] reciprocal of the next LDL' pivot (0 when not positive)
-    // refined solver only
-    double *rhs;    // [4][NC] reduced right-hand sides (FP64)
-    double *a;      // [4][NC] solution a_r (FP64)
-    float2 *ivs;    // [NC] reciprocal pivots
+    double *base;
+    int NC;
+    __device__ __forceinline__ int64_t o_xf() const { return 3 * NC; }
+    __device__ __forceinline__ int64_t o_C() const { return o_xf() + (3 * NC + 1) / 2; }
+    __device__ __forceinline__ int64_t o_Y() const { return o_C() + 4 * NC; }
+    __device__ __forceinline__ int64_t o_v() const { return o_Y() + 4 * NC; }
+    __device__ __forceinline__ int64_t o_S() const { return o_v() + 4 * NC; }
+    __device__ __forceinline__ int64_t o_M() const { return o_S() + (int64_t)NC * (NC + 1) / 2; }
+    __device__ __forceinline__ double *xi() const { return base; }
+    __device__ __forceinline__ float *xf() const { return (float *)(base + o_xf()); }
+    __device__ __forceinline__ double *C() const { return base + o_C(); }
+    __device__ __forceinline__ double *Y() const { return base + o_Y(); }
+    __device__ __forceinline__ double *v() const { return base + o_v(); }
+    __device__ __forceinline__ double *S() const { return base + o_S(); }
+    __device__ __forceinline__ double *M() const { return base + o_M(); }
+    __device__ __forceinline__ double *App() const { return base + o_M() + 16; }
+    __device__ __forceinline__ double *red() const { return base + o_M() + 32; }
+    __device__ __forceinline__ float *redv() const { return (float *)(base + o_M() + 96); }
+    __device__ __forceinline__ int *redj() const { return (int *)(base + o_M() + 128); }
+    __device__ __forceinline__ int *r2o() const { return (int *)(base + o_M() + 160); }
+    __device__ __forceinline__ double *piv() const { return base + o_M() + 160 + (NC + 1) / 2; }
+    __device__ __forceinline__ double *rhs() const { return piv() + 16; }
+    __device__ __forceinline__ double *a() const { return rhs() + 4 * NC; }
+    __device__ __forceinline__ float2 *ivs() const { return (float2 *)(a() + 4 * NC); }
 };
 
 // shared memory of one point group (doubles); the refined solver adds the
@@ -263,7 +285,7 @@ struct PointSmem {
 __host__ __device__ inline int64_t point_smem_doubles(int NC, bool refine)
 {
     return 3 * NC + (3 * NC + 1) / 2 + 4 * NC + 4 * NC + 4 * NC + (int64_t)NC * (NC + 1) / 2 + 32 + 64 + 32 + 32 +
-           (NC + 1) / 2 + 2 + 2 + (refine ? 9 * NC : 0);
+           (NC + 1) / 2 + 16 + (refine ? 9 * NC : 0);
 }
 
 // global scratch of one point group in the refined solver: the FP64 reduced
@@ -273,30 +295,11 @@ __host__ __device__ inline int64_t point_scratch_doubles(int NC)
     return (int64_t)(NC - 4) * (NC - 3) / 2;
 }
 
-__device__ __forceinline__ PointSmem carve(double *base, int NC, bool refine)
+__device__ __forceinline__ PointSmem carve(double *base, int NC, bool)
 {
     PointSmem w;
-    double *p = base;
-    w.xi = p; p += 3 * NC;
-    w.xf = (float *)p; p += (3 * NC + 1) / 2;
-    w.C = p; p += 4 * NC;
-    w.Y = p; p += 4 * NC;
-    w.v = p; p += 4 * NC;
-    w.S = p; p += (int64_t)NC * (NC + 1) / 2;
-    w.M = p; p += 16;
-    w.App = p; p += 16;
-    w.red = p; p += 64;
-    w.redv = (float *)p; p += 32;
-    w.redj = (int *)p; p += 32;
-    w.r2o = (int *)p; p += (NC + 1) / 2;
-    w.piv = p; p += 2 + 2;
-    w.rhs = w.a = nullptr;
-    w.ivs = nullptr;
-    if (refine) {
-        w.rhs = p; p += 4 * NC;
-        w.a = p; p += 4 * NC;
-        w.ivs = (float2 *)p;
-    }
+    w.base = base;
+    w.NC = NC;
     return w;
 }
 
@@ -333,6 +336,151 @@ struct Group {
     int GT, gt, lane, wig, G, bar;
 };
 
+// columns per elimination step
+constexpr int kElimCols = 2;
+
+// Arithmetic of the elimination: FP64, or float-float pairs.
+struct F64Ops {
+    typedef double T;
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T fnma(T x, T y, T c) { return fma(-x, y, c); }   // c - x y
+    static __device__ __forceinline__ T inv_pivot(T d) { return positive_normal(d) ? recip_nr(d) : 0.0; }
+    static __device__ __forceinline__ bool usable(T iv) { return iv > 0.0; }
+};
+
+struct FFOps {
+    typedef float2 T;
+    static __device__ __forceinline__ T zero() { return make_float2(0.0f, 0.0f); }
+    static __device__ __forceinline__ T mul(T a, T b) { return ff_mul(a, b); }
+    static __device__ __forceinline__ T fnma(T x, T y, T c) { return ff_fnma(x, y, c); }
+    static __device__ __forceinline__ T inv_pivot(T d) { return ff_pivot_ok(d) ? ff_recip(d) : zero(); }
+    static __device__ __forceinline__ bool usable(T iv) { return iv.x > 0.0f; }
+};
+
+// Right-looking A = L D L' of the packed lower triangle A (order M2, in
+// place), the first m columns, B columns per step:
+//  - the B x B pivot block of the step is factored by one thread (lane 0 of
+//    the group's first warp) at the end of the previous step: reciprocal
+//    pivots piv[t] and the updated unscaled block entries piv[B + t(t-1)/2 + s]
+//    (t > s);
+//  - every row i below the block forms its B updated unscaled entries
+//    (col[t][i]) and their scaled values L_{i,k+t} (one thread per row);
+//  - every entry of the trailing triangle gets its B updates in one pass.
+// Each value is the same sequence of multiply-adds as in the elimination one
+// column at a time (same order), so B does not change the result; it divides
+// the barriers and index decodes by B. col: B arrays of NC values. ivs
+// (optional) receives 1/D of every column. Returns false (for the whole
+// group) at a pivot that is not positive.
+// The B x B pivot block of the step at column k (nb <= B columns) by one
+// thread: reciprocal pivots piv[t] and updated unscaled entries
+// piv[B + t(t-1)/2 + s] (t > s), each the multiply-add sequence of the
+// column-at-a-time elimination. Not inlined: one thread runs it per step,
+// and inlined its registers would be reserved by every thread.
+template <class Ops, int B>
+__device__ __noinline__ void pivot_block(const typename Ops::T *A, typename Ops::T *piv, int k, int nb)
+{
+    typedef typename Ops::T T;
+    T iv[B];
+#pragma unroll
+    for (int t = 0; t < B; t++) {
+        if (t < nb) {
+            const int rt = (k + t) * (k + t + 1) / 2 + k;   // row k + t, column k
+            T d = A[rt + t];
+#pragma unroll
+            for (int s = 0; s < B; s++) {
+                if (s < t) {
+                    // updated entry (k + t, k + s): the block's columns r < s first
+                    T c = A[rt + s];
+#pragma unroll
+                    for (int r = 0; r < B; r++)
+                        if (r < s) c = Ops::fnma(Ops::mul(piv[B + t * (t - 1) / 2 + r], iv[r]), piv[B + s * (s - 1) / 2 + r], c);
+                    piv[B + t * (t - 1) / 2 + s] = c;
+                    d = Ops::fnma(Ops::mul(c, iv[s]), c, d);
+                }
+            }
+            iv[t] = Ops::inv_pivot(d);
+            piv[t] = iv[t];
+        }
+    }
+}
+
+// Right-looking A = L D L' of the packed lower triangle A (order M2, in
+// place), the first m columns, B columns per step:
+//  - the B x B pivot block of the step is factored by one thread (lane 0 of
+//    the group's first warp) at the end of the previous step (pivot_block);
+//  - every row i below the block forms its B updated unscaled entries
+//    (col[t][i]) and their scaled values L_{i,k+t} (one thread per row);
+//  - every entry of the trailing triangle gets its B updates in one pass.
+// Each value is the same sequence of multiply-adds as in the elimination one
+// column at a time (same order), so B does not change the result; it divides
+// the barriers and index decodes by B. col: B arrays of NC values. ivs
+// (optional) receives 1/D of every column. Returns false (for the whole
+// group) at a pivot that is not positive.
+template <class Ops, int B>
+__device__ __forceinline__ bool eliminate(typename Ops::T *A, typename Ops::T *col, int NC, typename Ops::T *piv,
+                                          typename Ops::T *ivs, int m, int M2, const Group &gr)
+{
+    typedef typename Ops::T T;
+    const int GT = gr.GT, gt = gr.gt, bar = gr.bar;
+    if (gr.wig == 0 && gr.lane == 0) pivot_block<Ops, B>(A, piv, 0, min(B, m));
+    group_sync(bar, GT);
+    for (int k = 0; k < m; k += B) {
+        const int nb = min(B, m - k);
+        T iv[B];
+        bool ok = true;
+#pragma unroll
+        for (int t = 0; t < B; t++) {
+            iv[t] = t < nb ? piv[t] : Ops::zero();
+            if (t < nb) ok &= Ops::usable(iv[t]);
+        }
+        if (!ok) return false;   // (every thread read the same pivots)
+        if (ivs && gt == 0)
+            for (int t = 0; t < nb; t++) ivs[k + t] = iv[t];
+        // scale: rows i > k; a row inside the block has only the columns s < i - k
+#pragma unroll 1
+        for (int i = k + 1 + gt; i < M2; i += GT) {
+            const int ik = i * (i + 1) / 2 + k;
+            const int nt = min(nb, i - k);
+            T l[B];
+#pragma unroll
+            for (int t = 0; t < B; t++) {
+                if (t < nt) {
+                    T a = A[ik + t];
+#pragma unroll
+                    for (int s = 0; s < B; s++)
+                        if (s < t) a = Ops::fnma(l[s], piv[B + t * (t - 1) / 2 + s], a);
+                    col[t * NC + i] = a;
+                    l[t] = Ops::mul(a, iv[t]);
+                    A[ik + t] = l[t];
+                }
+            }
+        }
+        group_sync(bar, GT);
+        // trailing triangle: rows and columns >= k + nb
+        const int k1 = k + nb, tk = M2 - k1, T2 = tk * (tk + 1) / 2;
+#pragma unroll 1
+        for (int u = gt; u < T2; u += GT) {
+            int ri, rj;
+            tri_decode_fast(u, ri, rj);
+            const int i = k1 + ri, j = k1 + rj, ib = i * (i + 1) / 2;
+            T nv = A[ib + j];
+#pragma unroll
+            for (int t = 0; t < B; t++)
+                if (t < nb) nv = Ops::fnma(A[ib + k + t], col[t * NC + j], nv);
+            A[ib + j] = nv;
+        }
+        // the next pivot block: its entries (u < 10 above) were updated by
+        // lanes of the first warp
+        if (k1 < m && gr.wig == 0) {
+            __syncwarp();
+            if (gr.lane == 0) pivot_block<Ops, B>(A, piv, k1, min(B, m - k1));
+        }
+        group_sync(bar, GT);
+    }
+    return true;
+}
+
 // Shape functions of point p by one group (all G*32 threads of the group
 // call it; the phases are separated by the group's named barrier).
 //
@@ -365,31 +513,31 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
         const int64_t J = sidx[base + j];
         const double a = (xyz[3 * J] - gx) * inv_h, b = (xyz[3 * J + 1] - gy) * inv_h,
                      c = (xyz[3 * J + 2] - gz) * inv_h;
-        W.xi[j] = a;
-        W.xi[NC + j] = b;
-        W.xi[2 * NC + j] = c;
-        W.xf[j] = f32_from_f64(a);
-        W.xf[NC + j] = f32_from_f64(b);
-        W.xf[2 * NC + j] = f32_from_f64(c);
+        W.xi()[j] = a;
+        W.xi()[NC + j] = b;
+        W.xi()[2 * NC + j] = c;
+        W.xf()[j] = f32_from_f64(a);
+        W.xf()[NC + j] = f32_from_f64(b);
+        W.xf()[2 * NC + j] = f32_from_f64(c);
     }
     group_sync(bar, GT);
 
     // 2. greedy pivot tetrahedron (single precision is enough to choose);
     //    each pass: warp argmax, then the group combines the G warps in
     //    order
-    const float *X = W.xf, *Yc = W.xf + NC, *Z = W.xf + 2 * NC;
+    const float *X = W.xf(), *Yc = W.xf() + NC, *Z = W.xf() + 2 * NC;
     auto group_argmax = [&](float bv, int bj, int pass) {
         warp_argmax(bv, bj);
         if (lane == 0) {
-            W.redv[16 * pass + wig] = bv;
-            W.redj[16 * pass + wig] = bj;
+            W.redv()[16 * pass + wig] = bv;
+            W.redj()[16 * pass + wig] = bj;
         }
         group_sync(bar, GT);
-        float v = W.redv[16 * pass];
-        int j = W.redj[16 * pass];
+        float v = W.redv()[16 * pass];
+        int j = W.redj()[16 * pass];
         for (int w = 1; w < G; w++) {
-            const float ov = W.redv[16 * pass + w];
-            const int oj = W.redj[16 * pass + w];
+            const float ov = W.redv()[16 * pass + w];
+            const int oj = W.redj()[16 * pass + w];
             if (ov > v || (ov == v && oj < j)) { v = ov; j = oj; }
         }
         return ArgMax{v, j};
@@ -447,7 +595,7 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
     for (int j = gt; j < n; j += GT) {
         int less = (p0 < j) + (p1 < j) + (p2 < j) + (p3 < j);
         bool isp = j == p0 || j == p1 || j == p2 || j == p3;
-        if (!isp) W.r2o[j - less] = j;
+        if (!isp) W.r2o()[j - less] = j;
     }
     auto pivot = [&](int k) { return k == 0 ? p0 : k == 1 ? p1 : k == 2 ? p2 : p3; };
 
@@ -460,7 +608,7 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
         for (int r = 0; r < 4; r++) {
             if (r == ri) continue;
             const int pr = pivot(r);
-            const double row[4] = {1.0, W.xi[pr], W.xi[NC + pr], W.xi[2 * NC + pr]};
+            const double row[4] = {1.0, W.xi()[pr], W.xi()[NC + pr], W.xi()[2 * NC + pr]};
             int cc = 0;
             for (int c = 0; c < 4; c++)
                 if (c != cj) e[rr][cc++] = row[c];
@@ -468,13 +616,13 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
         }
         double cof = det3(e[0][0], e[0][1], e[0][2], e[1][0], e[1][1], e[1][2], e[2][0], e[2][1], e[2][2]);
         if ((ri + cj) & 1) cof = -cof;
-        const double prow = cj == 0 ? 1.0 : W.xi[(cj - 1) * NC + p0];
+        const double prow = cj == 0 ? 1.0 : W.xi()[(cj - 1) * NC + p0];
         double part = lane < 4 ? prow * cof : 0.0;
         part += __shfl_xor_sync(0xffffffffu, part, 1);
         part += __shfl_xor_sync(0xffffffffu, part, 2);
         const double det = __shfl_sync(0xffffffffu, part, 0);
         const double idet = recip_nr(det);
-        if (lane < 16) W.M[lane] = cof * idet;
+        if (lane < 16) W.M()[lane] = cof * idet;
     }
     group_sync(bar, GT);
 
@@ -484,25 +632,25 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
         const int ia = pivot(a), ib = pivot(b);
         double val = ks.diag;
         if (a != b) {
-            double dx = W.xi[ia] - W.xi[ib], dy = W.xi[NC + ia] - W.xi[NC + ib], dz = W.xi[2 * NC + ia] - W.xi[2 * NC + ib];
+            double dx = W.xi()[ia] - W.xi()[ib], dy = W.xi()[NC + ia] - W.xi()[NC + ib], dz = W.xi()[2 * NC + ia] - W.xi()[2 * NC + ib];
             val = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
         }
-        W.App[gt] = val;
+        W.App()[gt] = val;
     }
     for (int t = gt; t < 4 * m; t += GT) {
         const int r = t >> 2, k = t & 3;
-        const int j = W.r2o[r];
-        const double x0 = W.xi[j], x1 = W.xi[NC + j], x2 = W.xi[2 * NC + j];
-        W.C[k * NC + r] = fma(W.M[4 * k + 3], x2, fma(W.M[4 * k + 2], x1, fma(W.M[4 * k + 1], x0, W.M[4 * k])));
+        const int j = W.r2o()[r];
+        const double x0 = W.xi()[j], x1 = W.xi()[NC + j], x2 = W.xi()[2 * NC + j];
+        W.C()[k * NC + r] = fma(W.M()[4 * k + 3], x2, fma(W.M()[4 * k + 2], x1, fma(W.M()[4 * k + 1], x0, W.M()[4 * k])));
         const int ik = pivot(k);
-        double dx = x0 - W.xi[ik], dy = x1 - W.xi[NC + ik], dz = x2 - W.xi[2 * NC + ik];
-        W.Y[k * NC + r] = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
+        double dx = x0 - W.xi()[ik], dy = x1 - W.xi()[NC + ik], dz = x2 - W.xi()[2 * NC + ik];
+        W.Y()[k * NC + r] = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
     }
     group_sync(bar, GT);
 
     // 5. right-hand sides v = r - A_:p d  (d = columns of M), all nodes
     for (int j = gt; j < n; j += GT) {
-        const double x0 = W.xi[j], x1 = W.xi[NC + j], x2 = W.xi[2 * NC + j];
+        const double x0 = W.xi()[j], x1 = W.xi()[NC + j], x2 = W.xi()[2 * NC + j];
         double Aj, dAj;
         series_A_dA(ks, fma(x2, x2, fma(x1, x1, fma(x0, x0, c2))), Aj, dAj);
         const double m2 = -2.0 * dAj;
@@ -514,18 +662,18 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
             if (pivot(k) == j) kp = k;
         if (kp >= 0) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) Ajp[k] = W.App[4 * kp + k];
+            for (int k = 0; k < 4; k++) Ajp[k] = W.App()[4 * kp + k];
         } else {
             const int r = j - (p0 < j) - (p1 < j) - (p2 < j) - (p3 < j);
 #pragma unroll
-            for (int k = 0; k < 4; k++) Ajp[k] = W.Y[k * NC + r];
+            for (int k = 0; k < 4; k++) Ajp[k] = W.Y()[k * NC + r];
         }
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             double acc = rr[q];
 #pragma unroll
-            for (int k = 0; k < 4; k++) acc = fma(-Ajp[k], W.M[4 * k + q], acc);
-            W.v[q * NC + j] = acc;
+            for (int k = 0; k < 4; k++) acc = fma(-Ajp[k], W.M()[4 * k + q], acc);
+            W.v()[q * NC + j] = acc;
         }
     }
     group_sync(bar, GT);
@@ -534,8 +682,8 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
         const int r = t >> 2, k = t & 3;
         double acc = 0.0;
 #pragma unroll
-        for (int s2 = 0; s2 < 4; s2++) acc = fma(W.C[s2 * NC + r], W.App[4 * s2 + k], acc);
-        W.Y[k * NC + r] = fma(-0.5, acc, W.Y[k * NC + r]);  // each thread owns its element
+        for (int s2 = 0; s2 < 4; s2++) acc = fma(W.C()[s2 * NC + r], W.App()[4 * s2 + k], acc);
+        W.Y()[k * NC + r] = fma(-0.5, acc, W.Y()[k * NC + r]);  // each thread owns its element
     }
     group_sync(bar, GT);
 
@@ -545,34 +693,31 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
     //    forward substitution. The refined solver keeps S and the
     //    right-hand sides in FP64 as well (S in the group's global scratch,
     //    which stays in L2) for the residual of step 8.
-    float2 *SF = (float2 *)W.S;     // the triangle as float-float pairs (refined solver)
-    float2 *PF = (float2 *)W.piv;   // reciprocal of the next pivot (refined solver)
+    float2 *SF = (float2 *)W.S();     // the triangle as float-float pairs (refined solver)
+    float2 *PF = (float2 *)W.piv();   // reciprocal of the next pivot (refined solver)
     {
         const int T = m * (m + 1) / 2;
         for (int u = gt; u < T; u += GT) {
             int i, j;
             tri_decode_fast(u, i, j);
-            const int oi = W.r2o[i], oj = W.r2o[j];
+            const int oi = W.r2o()[i], oj = W.r2o()[j];
             double a;
             if (i == j) {
                 a = ks.diag;
             } else {
-                double dx = W.xi[oi] - W.xi[oj], dy = W.xi[NC + oi] - W.xi[NC + oj], dz = W.xi[2 * NC + oi] - W.xi[2 * NC + oj];
+                double dx = W.xi()[oi] - W.xi()[oj], dy = W.xi()[NC + oi] - W.xi()[NC + oj], dz = W.xi()[2 * NC + oi] - W.xi()[2 * NC + oj];
                 a = series_A(ks, fma(dz, dz, fma(dy, dy, fma(dx, dx, c2))));
             }
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                a = fma(-W.Y[k * NC + i], W.C[k * NC + j], a);
-                a = fma(-W.C[k * NC + i], W.Y[k * NC + j], a);
+                a = fma(-W.Y()[k * NC + i], W.C()[k * NC + j], a);
+                a = fma(-W.C()[k * NC + i], W.Y()[k * NC + j], a);
             }
             if constexpr (REFINE) {
                 Sg[u] = a;
-                const float2 af = ff_from_f64(a);
-                SF[u] = af;
-                if (u == 0) PF[0] = ff_pivot_ok(af) ? ff_recip(af) : make_float2(0.0f, 0.0f);   // first pivot
+                SF[u] = ff_from_f64(a);
             } else {
-                W.S[u] = a;
-                if (u == 0) W.piv[0] = positive_normal(a) ? recip_nr(a) : 0.0;  // first pivot
+                W.S()[u] = a;
             }
         }
     }
@@ -580,84 +725,33 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
         const int q = t / (m + 4), r = t - q * (m + 4);
         double acc = 0.0;
         if (r < m) {
-            const int j = W.r2o[r];
-            acc = W.v[q * NC + j];
+            const int j = W.r2o()[r];
+            acc = W.v()[q * NC + j];
 #pragma unroll
-            for (int k = 0; k < 4; k++) acc = fma(-W.C[k * NC + r], W.v[q * NC + pivot(k)], acc);
+            for (int k = 0; k < 4; k++) acc = fma(-W.C()[k * NC + r], W.v()[q * NC + pivot(k)], acc);
         }
         if constexpr (REFINE) {
-            if (r < m) W.rhs[q * NC + r] = acc;
+            if (r < m) W.rhs()[q * NC + r] = acc;
             if (r <= m + q) SF[(m + q) * (m + q + 1) / 2 + r] = ff_from_f64(acc);
         } else {
-            if (r <= m + q) W.S[(m + q) * (m + q + 1) / 2 + r] = acc;
+            if (r <= m + q) W.S()[(m + q) * (m + q + 1) / 2 + r] = acc;
         }
     }
     group_sync(bar, GT);
 
     // 7. S = L D L' (right-looking, packed, in place) on the order-(m+4)
-    //    triangle; W.v holds the unscaled column of the current step.
-    //    After step m-1 the rhs rows hold z = D^-1 L^-1 rhs.
+    //    triangle, kElimCols columns per step; W.v() holds the unscaled
+    //    columns of the current step. After the last step the rhs rows hold
+    //    z = D^-1 L^-1 rhs. The reciprocal pivots are computed once per
+    //    step, by one thread, and read from shared memory by the group:
+    //    replicated in every warp they would cost each warp a full FP64
+    //    issue slot per instruction.
     const int M2 = m + 4;
-    bool ok = true;
-    //    The reciprocal of each pivot is computed once, by the thread
-    //    that finishes the pivot (u == 0 of the previous update), and read
-    //    from shared memory by the group: replicated in every warp it
-    //    would cost each warp a full FP64 issue slot per instruction.
-    if constexpr (REFINE) {
-        //    Float-float elimination; the trailing-triangle index of each
-        //    update is decoded with the approximate square root (the exact
-        //    one would cost more than the update itself here).
-        float2 *col = (float2 *)W.v;
-        for (int k = 0; k < m; k++) {
-            const float2 iv = PF[0];
-            if (!(iv.x > 0.0f)) { ok = false; break; }
-            if (gt == 0) W.ivs[k] = iv;
-            for (int i = k + 1 + gt; i < M2; i += GT) {
-                const int ik = i * (i + 1) / 2 + k;
-                const float2 a = SF[ik];
-                col[i] = a;
-                SF[ik] = ff_mul(a, iv);
-            }
-            group_sync(bar, GT);
-            const int tk = M2 - k - 1;
-            const int T = tk * (tk + 1) / 2;
-            for (int u = gt; u < T; u += GT) {
-                int ri, rj;
-                tri_decode_fast(u, ri, rj);
-                const int i = k + 1 + ri, j = k + 1 + rj;
-                const int ib = i * (i + 1) / 2;
-                const float2 nv = ff_fnma(SF[ib + k], col[j], SF[ib + j]);
-                SF[ib + j] = nv;
-                if (u == 0 && k + 1 < m) PF[0] = ff_pivot_ok(nv) ? ff_recip(nv) : make_float2(0.0f, 0.0f);
-            }
-            group_sync(bar, GT);
-        }
-    } else {
-        double *col = W.v;
-        for (int k = 0; k < m; k++) {
-            const double iv = W.piv[0];
-            if (!(iv > 0.0)) { ok = false; break; }
-            for (int i = k + 1 + gt; i < M2; i += GT) {
-                const int ik = i * (i + 1) / 2 + k;
-                const double a = W.S[ik];
-                col[i] = a;
-                W.S[ik] = a * iv;
-            }
-            group_sync(bar, GT);
-            const int tk = M2 - k - 1;
-            const int T = tk * (tk + 1) / 2;
-            for (int u = gt; u < T; u += GT) {
-                int ri, rj;
-                tri_decode_fast(u, ri, rj);
-                const int i = k + 1 + ri, j = k + 1 + rj;
-                const int ib = i * (i + 1) / 2;
-                const double nv = fma(-W.S[ib + k], col[j], W.S[ib + j]);
-                W.S[ib + j] = nv;
-                if (u == 0 && k + 1 < m) W.piv[0] = positive_normal(nv) ? recip_nr(nv) : 0.0;
-            }
-            group_sync(bar, GT);
-        }
-    }
+    bool ok;
+    if constexpr (REFINE)
+        ok = eliminate<FFOps, kElimCols>(SF, (float2 *)W.v(), NC, PF, W.ivs(), m, M2, gr);
+    else
+        ok = eliminate<F64Ops, kElimCols>(W.S(), W.v(), NC, W.piv(), nullptr, m, M2, gr);
     if (!ok) {
         if (gt == 0) dev_fail(err, RPIM_E_SINGULAR, p);
         group_sync(bar, GT);
@@ -665,7 +759,7 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
     }
 
     // 8. L' a = z, column by column; threads over (row, rhs) pairs
-    double *Z0 = W.S + (size_t)m * (m + 1) / 2;  // rhs row q starts at Z0 + q*m + q*(q+1)/2
+    double *Z0 = W.S() + (size_t)m * (m + 1) / 2;  // rhs row q starts at Z0 + q*m + q*(q+1)/2
     if constexpr (REFINE) {
         float2 *Z0f = SF + (size_t)m * (m + 1) / 2;
         for (int k = m - 1; k > 0; k--) {
@@ -679,36 +773,36 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
         }
         for (int t = gt; t < 4 * m; t += GT) {
             const int q = t & 3, i = t >> 2;
-            W.a[q * NC + i] = ff_to_f64(Z0f[q * m + q * (q + 1) / 2 + i]);
+            W.a()[q * NC + i] = ff_to_f64(Z0f[q * m + q * (q + 1) / 2 + i]);
         }
         group_sync(bar, GT);
         //    One step of iterative refinement: the residual rhs - S a in
         //    FP64 (one thread per row, ascending column order), then the
         //    correction from the float-float factors (L y = r, D z = y,
         //    L' e = z) added to a in FP64.
-        float2 *R = (float2 *)W.v;   // [4][NC]
+        float2 *R = (float2 *)W.v();   // [4][NC]
         for (int i = gt; i < m; i += GT) {
-            double r0 = W.rhs[i], r1 = W.rhs[NC + i], r2 = W.rhs[2 * NC + i], r3 = W.rhs[3 * NC + i];
+            double r0 = W.rhs()[i], r1 = W.rhs()[NC + i], r2 = W.rhs()[2 * NC + i], r3 = W.rhs()[3 * NC + i];
             // row i of S: (i, j) for j <= i, then (j, i) for j > i (not
             // unrolled: unrolling spills the kernel's registers)
             const double *srow = Sg + i * (i + 1) / 2;
 #pragma unroll 1
             for (int j = 0; j <= i; j++) {
                 const double sv = srow[j];
-                r0 = fma(-sv, W.a[j], r0);
-                r1 = fma(-sv, W.a[NC + j], r1);
-                r2 = fma(-sv, W.a[2 * NC + j], r2);
-                r3 = fma(-sv, W.a[3 * NC + j], r3);
+                r0 = fma(-sv, W.a()[j], r0);
+                r1 = fma(-sv, W.a()[NC + j], r1);
+                r2 = fma(-sv, W.a()[2 * NC + j], r2);
+                r3 = fma(-sv, W.a()[3 * NC + j], r3);
             }
             int pos = (i + 1) * (i + 2) / 2 + i;   // (i + 1, i)
 #pragma unroll 1
             for (int j = i + 1; j < m; j++) {
                 const double sv = Sg[pos];
                 pos += j + 1;
-                r0 = fma(-sv, W.a[j], r0);
-                r1 = fma(-sv, W.a[NC + j], r1);
-                r2 = fma(-sv, W.a[2 * NC + j], r2);
-                r3 = fma(-sv, W.a[3 * NC + j], r3);
+                r0 = fma(-sv, W.a()[j], r0);
+                r1 = fma(-sv, W.a()[NC + j], r1);
+                r2 = fma(-sv, W.a()[2 * NC + j], r2);
+                r3 = fma(-sv, W.a()[3 * NC + j], r3);
             }
             R[i] = ff_from_f64(r0);
             R[NC + i] = ff_from_f64(r1);
@@ -725,7 +819,7 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
         }
         for (int t = gt; t < 4 * m; t += GT) {
             const int q = t & 3, i = t >> 2;
-            R[q * NC + i] = ff_mul(R[q * NC + i], W.ivs[i]);
+            R[q * NC + i] = ff_mul(R[q * NC + i], W.ivs()[i]);
         }
         group_sync(bar, GT);
         for (int k = m - 1; k > 0; k--) {
@@ -738,7 +832,7 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
         }
         for (int t = gt; t < 4 * m; t += GT) {
             const int q = t & 3, i = t >> 2;
-            W.a[q * NC + i] += ff_to_f64(R[q * NC + i]);
+            W.a()[q * NC + i] += ff_to_f64(R[q * NC + i]);
         }
         group_sync(bar, GT);
     } else {
@@ -747,14 +841,14 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
             for (int t = gt; t < 4 * k; t += GT) {
                 const int q = t & 3, i = t >> 2;
                 double *zq = Z0 + q * m + q * (q + 1) / 2;
-                zq[i] = fma(-W.S[kb + i], zq[k], zq[i]);
+                zq[i] = fma(-W.S()[kb + i], zq[k], zq[i]);
             }
             group_sync(bar, GT);
         }
     }
     // a_r of right-hand side q (r < m)
     auto ar_of = [&](int q, int r) -> double {
-        if constexpr (REFINE) return W.a[q * NC + r];
+        if constexpr (REFINE) return W.a()[q * NC + r];
         else return Z0[q * m + q * (q + 1) / 2 + r];
     };
 
@@ -773,7 +867,7 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
             for (int q = 0; q < 4; q++) ar[q] = ar_of(q, r);
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                const double c = W.C[k * NC + r];
+                const double c = W.C()[k * NC + r];
 #pragma unroll
                 for (int q = 0; q < 4; q++) v[4 * k + q] = fma(c, ar[q], v[4 * k + q]);
             }
@@ -789,13 +883,13 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
             }
         }
         v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-        if ((lane & 1) == 0) W.red[lane >> 1] = v[0];
+        if ((lane & 1) == 0) W.red()[lane >> 1] = v[0];
     }
 
     double *out = phi + 4 * base;
     bool finite = true;
     for (int r = gt; r < m; r += GT) {
-        const int j = W.r2o[r];
+        const int j = W.r2o()[r];
         double2 lo2 = make_double2(ar_of(0, r), ar_of(1, r) * inv_h);
         double2 hi2 = make_double2(ar_of(2, r) * inv_h, ar_of(3, r) * inv_h);
         finite &= isfinite(lo2.x) && isfinite(lo2.y) && isfinite(hi2.x) && isfinite(hi2.y);
@@ -805,7 +899,7 @@ __device__ __forceinline__ void shape_point(const int64_t p, const KernelSeries 
     group_sync(bar, GT);
     if (gt < 16) {
         const int k = gt >> 2, q = gt & 3;
-        double val = W.M[4 * k + q] - W.red[gt];
+        double val = W.M()[4 * k + q] - W.red()[gt];
         if (q) val *= inv_h;
         finite &= isfinite(val);
         out[4 * pivot(k) + q] = val;
