@@ -156,7 +156,11 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
             nloc = 0;
             __syncwarp();
         };
-        double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+        // body force f_I = b sum_g w_g phi_I(g): lane l sums the points
+        // tb + l of every prefetch, the lanes are combined at the end of the
+        // row (a fixed order); one FP64 add per point instead of three
+        // warp-wide multiply-adds per point
+        double fw = 0.0;
         for (int64_t tb = t0; tb < t1; tb += 32) {
             // prefetch: lane l loads the scalars of point tb + l
             int64_t pe = 0, pend = 0;
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                 pA0 = lw * pa.y; pA1 = lw * pb.x; pA2 = lw * pb.y;
                 pM0 = mw * pa.y; pM1 = mw * pb.x; pM2 = mw * pb.y;
                 pw = pa.x * wj[g];
+                if (body) fw += pw;
             }
             const int cnt = (int)min((int64_t)32, t1 - tb);
             for (int k = 0; k < cnt; k++) {
@@ -183,12 +188,6 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                     A0 = __shfl_sync(0xffffffffu, pA0, k);
                     A1 = __shfl_sync(0xffffffffu, pA1, k);
                     A2 = __shfl_sync(0xffffffffu, pA2, k);
-                }
-                const double w = __shfl_sync(0xffffffffu, pw, k);
-                if (body) {
-                    f0 = fma(w, b0, f0);
-                    f1 = fma(w, b1, f1);
-                    f2 = fma(w, b2, f2);
                 }
                 for (int64_t qb = e; qb < end; qb += 32) {
                     const int64_t q = qb + lane;
@@ -279,10 +278,14 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
 #pragma unroll
             for (int i = 0; i < 9; i++) o[i] = k[i];
         }
+        if (body) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) fw += __shfl_xor_sync(0xffffffffu, fw, o);
+        }
         if (lane == 0) {
-            f[3 * I] = f0;
-            f[3 * I + 1] = f1;
-            f[3 * I + 2] = f2;
+            f[3 * I] = fw * b0;
+            f[3 * I + 1] = fw * b1;
+            f[3 * I + 2] = fw * b2;
         }
         __syncwarp();
     }

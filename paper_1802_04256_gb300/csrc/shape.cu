@@ -339,9 +339,15 @@ struct Group {
 // columns per elimination step
 constexpr int kElimCols = 2;
 
+// threads per block of the shape kernels: the FP64 solver runs up to 1024
+// (64 registers a thread); the float-float solver, whose long dependent
+// FP32 chains need registers for overlap, up to 512 (128 registers)
+constexpr int kShapeMaxThreads[2] = {1024, 512};
+
 // Arithmetic of the elimination: FP64, or float-float pairs.
 struct F64Ops {
     typedef double T;
+    static constexpr int kUnroll = 1;   // trailing-update entries interleaved per thread
     static __device__ __forceinline__ T zero() { return 0.0; }
     static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
     static __device__ __forceinline__ T fnma(T x, T y, T c) { return fma(-x, y, c); }   // c - x y
@@ -351,6 +357,7 @@ struct F64Ops {
 
 struct FFOps {
     typedef float2 T;
+    static constexpr int kUnroll = 2;
     static __device__ __forceinline__ T zero() { return make_float2(0.0f, 0.0f); }
     static __device__ __forceinline__ T mul(T a, T b) { return ff_mul(a, b); }
     static __device__ __forceinline__ T fnma(T x, T y, T c) { return ff_fnma(x, y, c); }
@@ -459,7 +466,7 @@ __device__ __forceinline__ bool eliminate(typename Ops::T *A, typename Ops::T *c
         group_sync(bar, GT);
         // trailing triangle: rows and columns >= k + nb
         const int k1 = k + nb, tk = M2 - k1, T2 = tk * (tk + 1) / 2;
-#pragma unroll 1
+#pragma unroll (Ops::kUnroll)
         for (int u = gt; u < T2; u += GT) {
             int ri, rj;
             tri_decode_fast(u, ri, rj);
@@ -922,7 +929,7 @@ __global__ void recip_probe_kernel(int64_t n, const double *__restrict__ d, doub
 // per point group, group g of block b at (b * ppb + g) (unused otherwise;
 // every block of this kernel works with the same NC and ppb).
 template <bool REFINE>
-__global__ void __launch_bounds__(1024) shape_kernel(int64_t n_pts, const double *__restrict__ pts,
+__global__ void __launch_bounds__(kShapeMaxThreads[REFINE]) shape_kernel(int64_t n_pts, const double *__restrict__ pts,
                                                      const int32_t *__restrict__ inst_of, int shift,
                                                      const InstGrid *__restrict__ ig,
                                                      const int32_t *__restrict__ order,
@@ -983,7 +990,7 @@ struct BucketPlan {
 // thread-level formula as in shape_kernel, whatever the launch shape, so the
 // results are bitwise those of the per-bucket launches.
 template <bool REFINE>
-__global__ void __launch_bounds__(1024) shape_tiles_kernel(const BucketPlan plan, unsigned long long *counters,
+__global__ void __launch_bounds__(kShapeMaxThreads[REFINE]) shape_tiles_kernel(const BucketPlan plan, unsigned long long *counters,
                                                            const double *__restrict__ pts,
                                                            const int32_t *__restrict__ inst_of, int shift,
                                                            const InstGrid *__restrict__ ig,
@@ -1058,7 +1065,7 @@ constexpr int kMaxGroupWarps = 16;   // warps per point group (argmax buffers ho
 
 static bool cfg_valid(int NC, ShapeCfg c, bool ref)
 {
-    return c.G >= 1 && c.G <= kMaxGroupWarps && c.ppb >= 1 && c.ppb <= 15 && c.ppb * c.G * 32 <= 1024 &&
+    return c.G >= 1 && c.G <= kMaxGroupWarps && c.ppb >= 1 && c.ppb <= 15 && c.ppb * c.G * 32 <= kShapeMaxThreads[ref] &&
            (size_t)c.ppb * point_bytes(NC, ref) <= kShapeSmemBudget;
 }
 
@@ -1066,7 +1073,9 @@ static ShapeCfg default_cfg(int NC, bool ref)
 {
     ShapeCfg c;
     c.ppb = (int)std::min<size_t>(15, kShapeSmemBudget / point_bytes(NC, ref));  // points (groups) per block
-    c.G = std::max(1, std::min(c.ppb <= 2 ? 8 : 4, 32 / std::max(1, c.ppb)));   // warps per point
+    // warps per point: about 24 warps per block, at most 8 per point (the
+    // launch shapes the autotuner picked on supports of 40-130 nodes)
+    c.G = std::max(1, std::min(8, (ref ? 12 : 24) / std::max(1, c.ppb)));
     return c;
 }
 
@@ -1400,6 +1409,29 @@ extern "C" rpim_status rpim_autotune_buckets(rpim_pattern *p, int64_t max_points
         for (int v = std::max(8, (int)p->min_support + w - 1); v < (int)p->max_support; v += w) b.push_back(v);
         if (b.empty()) b.push_back((int32_t)p->max_support);
         if ((int)b.size() <= 31) cands.push_back(b);
+    }
+    {
+        // occupancy bounds: the largest support for which ppb point groups
+        // fit one block's shared memory, ppb = 1..15 (a bucket just below
+        // such a bound runs one more point per block than a bucket above it),
+        // alone and merged with the width-16 bounds
+        const bool ref = refined();
+        std::vector<int32_t> occ;
+        for (int ppb = 15; ppb >= 1; ppb--) {
+            int nc = 8;
+            while (nc + 1 <= RPIM_MAX_SUPPORT && (size_t)ppb * point_bytes(nc + 1, ref) <= kShapeSmemBudget) nc++;
+            if ((size_t)ppb * point_bytes(nc, ref) <= kShapeSmemBudget && nc > (int)p->min_support &&
+                nc < (int)p->max_support && (occ.empty() || nc > occ.back()))
+                occ.push_back(nc);
+        }
+        if (!occ.empty()) {
+            cands.push_back(occ);
+            std::vector<int32_t> merged = occ;
+            for (int v = std::max(8, (int)p->min_support + 15); v < (int)p->max_support; v += 16) merged.push_back(v);
+            std::sort(merged.begin(), merged.end());
+            merged.erase(std::unique(merged.begin(), merged.end()), merged.end());
+            if ((int)merged.size() <= 31) cands.push_back(merged);
+        }
     }
     const double frac = std::min(1.0, (double)max_points / (double)std::max<int64_t>(1, p->n_points));
     cudaEvent_t e0, e1;
