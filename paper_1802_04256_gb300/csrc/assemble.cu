@@ -178,9 +178,42 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                 if (body) fw += pw;
             }
             const int cnt = (int)min((int64_t)32, t1 - tb);
-            for (int k = 0; k < cnt; k++) {
-                const int64_t e = __shfl_sync(0xffffffffu, pe, k);
-                const int64_t end = __shfl_sync(0xffffffffu, pend, k);
+            // chunks of 32 support entries of the batch's points, walked in
+            // order; the slot and gradient of the next chunk are loaded
+            // while the current one is accumulated (the lookup chain
+            // sidx -> cell data -> slot table is the kernel's latency)
+            auto fetch = [&](int64_t qb_, int64_t qend_, int &slot_, double &d0_, double &d1_, double &d2_) {
+                const int64_t q = qb_ + lane;
+                slot_ = -1;
+                d0_ = d1_ = d2_ = 0.0;
+                if (q < qend_) {
+                    const int bi = run_bit(node_cpk, node_rank, sidx[q], cx, cy, cz, run_start[wi], run_pre[wi]);
+                    slot_ = bi >= 0 && bi < total ? tab[bi] : -1;
+                    if (slot_ < 0) dev_fail(err, RPIM_E_ARG, I);
+                    const double2 qa = *(const double2 *)(phi + 4 * q);
+                    const double2 qb2 = *(const double2 *)(phi + 4 * q + 2);
+                    d0_ = qa.y;
+                    d1_ = qb2.x;
+                    d2_ = qb2.y;
+                }
+            };
+            int k = 0;
+            int64_t qb = __shfl_sync(0xffffffffu, pe, 0), qend = __shfl_sync(0xffffffffu, pend, 0);
+            int slot;
+            double d0, d1, d2;
+            fetch(qb, qend, slot, d0, d1, d2);
+            while (k < cnt) {
+                // the next chunk: the rest of point k's support, or point k + 1
+                int nk = k;
+                int64_t nqb = qb + 32, nqend = qend;
+                if (nqb >= qend) {
+                    nk = k + 1;
+                    nqb = __shfl_sync(0xffffffffu, pe, nk & 31);
+                    nqend = __shfl_sync(0xffffffffu, pend, nk & 31);
+                }
+                int nslot = -1;
+                double n0 = 0.0, n1 = 0.0, n2 = 0.0;
+                if (nk < cnt) fetch(nqb, nqend, nslot, n0, n1, n2);
                 const double M0 = __shfl_sync(0xffffffffu, pM0, k), M1 = __shfl_sync(0xffffffffu, pM1, k),
                              M2 = __shfl_sync(0xffffffffu, pM2, k);
                 double A0 = 0.0, A1 = 0.0, A2 = 0.0;
@@ -189,18 +222,7 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                     A1 = __shfl_sync(0xffffffffu, pA1, k);
                     A2 = __shfl_sync(0xffffffffu, pA2, k);
                 }
-                for (int64_t qb = e; qb < end; qb += 32) {
-                    const int64_t q = qb + lane;
-                    int slot = -1;
-                    double d0 = 0.0, d1 = 0.0, d2 = 0.0;
-                    if (q < end) {
-                        const int bi = run_bit(node_cpk, node_rank, sidx[q], cx, cy, cz, run_start[wi], run_pre[wi]);
-                        slot = bi >= 0 && bi < total ? tab[bi] : -1;
-                        if (slot < 0) dev_fail(err, RPIM_E_ARG, I);
-                        const double2 qa = *(const double2 *)(phi + 4 * q);
-                        const double2 qb2 = *(const double2 *)(phi + 4 * q + 2);
-                        d0 = qa.y; d1 = qb2.x; d2 = qb2.y;
-                    }
+                {
                     // the block's place: in the cache (li >= 0), or to be
                     // brought in; blocks stay in K when the cache is full
                     int li = -1;
@@ -253,6 +275,13 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                     }
                     __syncwarp();   // cache map and entries visible to the next round's lanes
                 }
+                k = nk;
+                qb = nqb;
+                qend = nqend;
+                slot = nslot;
+                d0 = n0;
+                d1 = n1;
+                d2 = n2;
             }
         }
         flush();
