@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                                                      const int64_t *__restrict__ tent,
                                                      const int32_t *__restrict__ entry_pt,
                                                      const int64_t *__restrict__ soff,
-                                                     const int32_t *__restrict__ sidx,
+                                                     const uint2 *__restrict__ ecell,
                                                      const double *__restrict__ phi,
                                                      const double *__restrict__ lamw,
                                                      const double *__restrict__ wj,
@@ -118,7 +118,10 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
         const int U = (int)(rend - sd);
         const int32_t *ucols = cols + sd;
         double *Ku = K + 9 * sd;
-        for (int64_t i = lane; i < 9 * (int64_t)U; i += 32) Ku[i] = 0.0;
+        // without a cache every block is a running sum in K from zero; with
+        // one, a block's first update starts from zero itself (map -2)
+        if (C == 0)
+            for (int64_t i = lane; i < 9 * (int64_t)U; i += 32) Ku[i] = 0.0;
         const uint32_t ci = node_cpk[I];
         const int cx = (int)(ci & 0x7FF), cy = (int)((ci >> 11) & 0x7FF), cz = (int)(ci >> 22);
         const int total = cell_runs(ig[node_inst[I]], cell_start, cx, cy, cz, lane, run_start[wi], run_pre[wi]);
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
         }
         for (int i = lane; i < total; i += 32) tab[i] = -1;
         if (C > 0)
-            for (int i = lane; i < U; i += 32) lmap[i] = -1;
+            for (int i = lane; i < U; i += 32) lmap[i] = -2;
         __syncwarp();
         for (int s = lane; s < U; s += 32) {
             const int bi = run_bit(node_cpk, node_rank, ucols[s], cx, cy, cz, run_start[wi], run_pre[wi]);
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                 slot_ = -1;
                 d0_ = d1_ = d2_ = 0.0;
                 if (q < qend_) {
-                    const int bi = run_bit(node_cpk, node_rank, sidx[q], cx, cy, cz, run_start[wi], run_pre[wi]);
+                    const int bi = run_bit_cell(ecell[q], cx, cy, cz, run_start[wi], run_pre[wi]);
                     slot_ = bi >= 0 && bi < total ? tab[bi] : -1;
                     if (slot_ < 0) dev_fail(err, RPIM_E_ARG, I);
                     const double2 qa = *(const double2 *)(phi + 4 * q);
@@ -224,18 +227,22 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                 }
                 {
                     // the block's place: in the cache (li >= 0), or to be
-                    // brought in; blocks stay in K when the cache is full
-                    int li = -1;
+                    // brought in; blocks stay in K when the cache is full.
+                    // The map holds the cache index, -1 for a block whose
+                    // running sum is in K, -2 for a block not yet updated in
+                    // this row (its running sum is zero: no load)
+                    int li = -1, lv = -1;
                     bool fresh = false;
                     if (C > 0) {   // (C is uniform: without a cache every block stays in K)
-                        li = slot >= 0 ? (int)lmap[slot] : -1;
-                        unsigned need = __ballot_sync(0xffffffffu, slot >= 0 && li < 0);
+                        lv = slot >= 0 ? (int)lmap[slot] : -1;
+                        unsigned need = __ballot_sync(0xffffffffu, slot >= 0 && lv < 0);
                         if (need && nloc + __popc(need) > C) {
                             flush();
-                            li = slot >= 0 ? (int)lmap[slot] : -1;
-                            need = __ballot_sync(0xffffffffu, slot >= 0 && li < 0);
+                            lv = slot >= 0 ? (int)lmap[slot] : -1;
+                            need = __ballot_sync(0xffffffffu, slot >= 0 && lv < 0);
                         }
-                        if (slot >= 0 && li < 0) {
+                        li = lv >= 0 ? lv : -1;
+                        if (slot >= 0 && lv < 0) {
                             const int n = nloc + __popc(need & lt);
                             if (n < C) {
                                 li = n;
@@ -247,12 +254,19 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                         nloc = min(C, nloc + __popc(need));
                     }
                     if (slot >= 0) {
-                        // running sum of the block: from K when it enters the
-                        // cache or stays out of it, else from the cache
-                        const double *src = (li >= 0 && !fresh) ? cache + 9 * li : Ku + 9 * slot;
+                        // running sum of the block: zero at its first update,
+                        // from K when it enters the cache or stays out of it,
+                        // else from the cache
                         double o[9];
+                        if (lv == -2) {
 #pragma unroll
-                        for (int i = 0; i < 9; i++) o[i] = src[i];
+                            for (int i = 0; i < 9; i++) o[i] = 0.0;
+                            if (li < 0) lmap[slot] = -1;   // stays in K from now on
+                        } else {
+                            const double *src = (li >= 0 && !fresh) ? cache + 9 * li : Ku + 9 * slot;
+#pragma unroll
+                            for (int i = 0; i < 9; i++) o[i] = src[i];
+                        }
                         if (uni) {
                             o[0] = fma(M0, d0, o[0]); o[1] = fma(M0, d1, o[1]); o[2] = fma(M0, d2, o[2]);
                             o[3] = fma(M1, d0, o[3]); o[4] = fma(M1, d1, o[4]); o[5] = fma(M1, d2, o[5]);
@@ -290,8 +304,11 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
         for (int s = lane; s < U; s += 32) {
             double *o = Ku + 9 * s;
             double k[9];
+            // (every upper block of the pattern is updated by some point of
+            // the row; a block that was not would be zero)
+            const bool touched = C == 0 || lmap[s] != -2;
 #pragma unroll
-            for (int i = 0; i < 9; i++) k[i] = o[i];
+            for (int i = 0; i < 9; i++) k[i] = touched ? o[i] : 0.0;
             if (uni) {
                 const double tr = (k[0] + k[4]) + k[8];
                 double v[9];
@@ -520,7 +537,7 @@ static rpim_status assemble_issue(rpim_pattern *p, const double *E, const double
     if (nbits > 32767 || smem > 216 * 1024) return fail(RPIM_E_SUPPORT, "row slot table too large (too many nodes per cell)");
     RPIM_CUDA(cudaFuncSetAttribute(row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     launch("row", row_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, smem, s, p->n_nodes, p->toff,
-           p->tent, p->entry_pt, p->soff, p->sidx, p->phi, p->lamw, p->wj, nu, body, p->rowptr, p->cols, p->diag,
+           p->tent, p->entry_pt, p->soff, (const uint2 *)p->ecell, p->phi, p->lamw, p->wj, nu, body, p->rowptr, p->cols, p->diag,
            (const InstGrid *)p->ig, (const int32_t *)p->node_inst, (const int32_t *)p->cell_start,
            (const uint32_t *)p->node_cpk, (const int32_t *)p->node_rank, nbits, max_upper, C, rows_in_order(p), K, f,
            p->err);

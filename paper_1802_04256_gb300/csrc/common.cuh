@@ -141,6 +141,18 @@ __device__ __forceinline__ int run_bit(const uint32_t *node_cpk, const int32_t *
     return run_pre[r] + (node_rank[J] - run_start[r]);
 }
 
+// the same from a node's (packed cell, rank in cell) pair, as stored per
+// support entry (rpim_pattern::ecell)
+__device__ __forceinline__ int run_bit_cell(uint2 cj_rank, int cx, int cy, int cz, const int *run_start,
+                                            const int *run_pre)
+{
+    const uint32_t cj = cj_rank.x;
+    const int dx = (int)(cj & 0x7FF) - cx, dy = (int)((cj >> 11) & 0x7FF) - cy, dz = (int)(cj >> 22) - cz;
+    if (dx < -2 || dx > 2 || dy < -2 || dy > 2 || dz < -2 || dz > 2) return -1;
+    const int r = (dy + 2) + 5 * (dz + 2);
+    return run_pre[r] + ((int)cj_rank.y - run_start[r]);
+}
+
 // instance of point k of a list: inst_of[k >> shift], or 0 without a map
 __device__ __forceinline__ int instance_of(const int32_t *inst_of, int shift, int64_t k)
 {
@@ -201,6 +213,7 @@ struct rpim_pattern {
     int64_t *soff = nullptr;        // [n_points+1]
     int32_t *sidx = nullptr;        // [n_entries]
     int32_t *entry_pt = nullptr;    // [n_entries] point of each entry
+    uint2 *ecell = nullptr;         // [n_entries] (packed cell, rank in cell) of each entry's node
     // node -> entries incidence, ascending entry (hence ascending point)
     int64_t *toff = nullptr;        // [n_nodes+1]
     int64_t *tent = nullptr;        // [n_entries]

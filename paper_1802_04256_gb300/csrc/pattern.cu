@@ -396,6 +396,20 @@ rpim_status search_supports_into(rpim_pattern *p, int64_t n_pts, const double *p
     return RPIM_OK;
 }
 
+// (packed cell, rank in cell) of every support entry's node: the row-owner
+// kernels read it with the entry (one coalesced load) instead of gathering
+// node_cpk[J] and node_rank[J] behind the load of J
+__global__ void entry_cells_kernel(int64_t n_entries, const int32_t *__restrict__ sidx,
+                                   const uint32_t *__restrict__ node_cpk, const int32_t *__restrict__ node_rank,
+                                   uint2 *__restrict__ ecell)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_entries; e += stride) {
+        const int32_t J = sidx[e];
+        ecell[e] = make_uint2(node_cpk[J], (uint32_t)node_rank[J]);
+    }
+}
+
 __global__ void entry_points_kernel(int64_t n_pts, const int64_t *soff, int32_t *entry_pt)
 {
     const int lane = threadIdx.x & 31;
@@ -418,9 +432,9 @@ __global__ void entry_points_kernel(int64_t n_pts, const int64_t *soff, int32_t 
 // lanes, so that every lane has independent loads in flight (walking one
 // point at a time left most lanes idle behind a chain of dependent loads).
 __global__ void pattern_bits_kernel(int64_t n_nodes, const InstGrid *ig, const int32_t *node_inst,
-                                    const int32_t *cell_start, const uint32_t *node_cpk, const int32_t *node_rank,
+                                    const int32_t *cell_start, const uint32_t *node_cpk,
                                     const int64_t *toff, const int64_t *tent, const int32_t *entry_pt,
-                                    const int64_t *soff, const int32_t *sidx, int64_t *rowcnt, uint32_t *bm,
+                                    const int64_t *soff, const uint2 *ecell, int64_t *rowcnt, uint32_t *bm,
                                     int words, int *maxrow, const int32_t *order, DevError *err)
 {
     extern __shared__ uint32_t smem[];
@@ -478,17 +492,9 @@ __global__ void pattern_bits_kernel(int64_t n_nodes, const InstGrid *ig, const i
                 const int64_t sq = __shfl_sync(0xffffffffu, s0, q);
                 const int eq = __shfl_sync(0xffffffffu, excl, q);
                 if (e < tot) {
-                    const int32_t J = sidx[sq + (e - eq)];
-                    const uint32_t cj = node_cpk[J];
-                    const int dx = (int)(cj & 0x7FF) - cx, dy = (int)((cj >> 11) & 0x7FF) - cy,
-                              dz = (int)(cj >> 22) - cz;
-                    if (dx < -2 || dx > 2 || dy < -2 || dy > 2 || dz < -2 || dz > 2) {
-                        dev_fail(err, RPIM_E_ARG, I);
-                    } else {
-                        const int r = (dy + 2) + 5 * (dz + 2);
-                        const int bi = run_pre[w][r] + (node_rank[J] - run_start[w][r]);
-                        atomicOr(&bits[bi >> 5], 1u << (bi & 31));
-                    }
+                    const int bi = run_bit_cell(ecell[sq + (e - eq)], cx, cy, cz, run_start[w], run_pre[w]);
+                    if (bi < 0) dev_fail(err, RPIM_E_ARG, I);
+                    else atomicOr(&bits[bi >> 5], 1u << (bi & 31));
                 }
             }
         }
@@ -595,7 +601,7 @@ static void pattern_release(rpim_pattern *p)
     dfree(p->xyz, s); dfree(p->sorted_xyz, s); dfree(p->sorted_loc, s); dfree(p->sorted_ids, s); dfree(p->cell_start, s);
     dfree(p->node_cell, s); dfree(p->node_cpk, s); dfree(p->node_rank, s); dfree(p->pts, s); dfree(p->wj, s);
     dfree(p->row_order, s);
-    dfree(p->soff, s); dfree(p->sidx, s); dfree(p->entry_pt, s); dfree(p->toff, s);
+    dfree(p->soff, s); dfree(p->sidx, s); dfree(p->entry_pt, s); dfree(p->ecell, s); dfree(p->toff, s);
     dfree(p->tent, s); dfree(p->rowptr, s); dfree(p->cols, s); dfree(p->diag, s);
     dfree(p->phi, s); dfree(p->lamw, s); dfree(p->err, s); dfree(p->scal, s); dfree(p->series, s);
     dfree(p->ws.buf, s);
@@ -958,6 +964,9 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
                                &p->max_support, &p->min_support, s, "search"));
     RPIM_CHECK(dalloc(&p->entry_pt, p->n_entries, s));
     launch("entry_points", entry_points_kernel, grid_size(p->sm_count, 8, p->n_points * 32, 256), 256, 0, s, p->n_points, p->soff, p->entry_pt);
+    RPIM_CHECK(dalloc(&p->ecell, p->n_entries, s));
+    launch("entry_cells", entry_cells_kernel, grid_size(p->sm_count, 8, p->n_entries, 256), 256, 0, s, p->n_entries,
+           (const int32_t *)p->sidx, (const uint32_t *)p->node_cpk, (const int32_t *)p->node_rank, p->ecell);
     RPIM_CHECK(build_incidence(n, p->n_entries, p->sidx, &p->toff, &p->tent, &p->max_incident, s, p->sm_count));
 
     // support-size buckets
@@ -985,9 +994,9 @@ static rpim_status build(rpim_pattern *p, const double *xyz, const double *lo, c
             RPIM_CUDA(cudaFuncSetAttribute(pattern_bits_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         launch("pattern_count", pattern_bits_kernel, grid_size(p->sm_count, 4, n, wpb), wpb * 32, smem, s,
                n, (const InstGrid *)p->ig, (const int32_t *)p->node_inst, (const int32_t *)p->cell_start,
-               (const uint32_t *)p->node_cpk, (const int32_t *)p->node_rank, (const int64_t *)p->toff,
+               (const uint32_t *)p->node_cpk, (const int64_t *)p->toff,
                (const int64_t *)p->tent, (const int32_t *)p->entry_pt, (const int64_t *)p->soff,
-               (const int32_t *)p->sidx, p->rowptr, bm, words, dmax, rows_in_order(p), p->err);
+               (const uint2 *)p->ecell, p->rowptr, bm, words, dmax, rows_in_order(p), p->err);
         RPIM_CUDA(cudaGetLastError());
     }
     RPIM_CHECK(exclusive_scan(p->rowptr, n, tmp, s));
