@@ -59,10 +59,15 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t 
 // accumulators) 34 ms; 32 (a 64-register split into uniform and general
 // kernels) 94 ms, the L2 thrashing on 92 MB of blocks in flight. Per-point scalars
 // are prefetched 32 points at a time, one point per lane, and broadcast by
-// shuffles. The block slot of a column J is looked up in a per-warp shared
-// table indexed by J's position in the 25 cell runs around I (the same
-// positions as the pattern's bitmap), filled from the row's upper columns:
-// one table read per pair instead of a binary search over the row.
+// shuffles. A column J's block is found from J's position in the 25 cell
+// runs around I (the same positions as the pattern's bitmap, read per
+// support entry from the entry's cell record): the row's upper columns are
+// marked in a per-warp bitmap over these positions with the popcount before
+// each word, so J's rank among them (its local index) is one word, one
+// prefix and one popcount; a table maps local indices to the row's slots.
+// The tables take about a tenth of the shared memory of a slot per position,
+// which leaves room for a cache of up to 112 blocks per warp also where the
+// cells hold many nodes (the layered slope: 54).
 //
 // Uniform rows (all points of the row have the same nu, hence the same
 // kappa = lambda/mu = 2 nu / (1 - 2 nu)) accumulate only
@@ -94,15 +99,30 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
     extern __shared__ __align__(16) unsigned char row_smem[];
     __shared__ int run_start[8][25], run_pre[8][26];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    // per-warp shared memory: slot table | slot -> cache index | cache index
-    // -> slot | block cache [C][9]
-    const size_t tab_b = ((size_t)nbits * 2 + 15) & ~(size_t)15, map_b = ((size_t)max_upper + 15) & ~(size_t)15,
+    // per-warp shared memory: the row's upper columns as a bitmap over the
+    // positions of the 25 cell runs around I, with the popcount of the words
+    // before each word (a column's rank among the row's upper columns is its
+    // local index) | local index -> slot in the row | local index -> cache
+    // index | cache index -> local index | block cache [C][9]
+    const int nw = nbits >> 5;
+    const size_t bits_b = ((size_t)nw * 4 + 15) & ~(size_t)15, pre_b = ((size_t)nw * 2 + 15) & ~(size_t)15,
+                 l2s_b = ((size_t)max_upper * 2 + 15) & ~(size_t)15,
+                 map_b = C > 0 ? (((size_t)max_upper + 15) & ~(size_t)15) : 0,
                  cs_b = ((size_t)C * 2 + 15) & ~(size_t)15;
-    unsigned char *wbase = row_smem + (size_t)wi * (tab_b + map_b + cs_b + (size_t)C * 72);
-    int16_t *tab = (int16_t *)wbase;
-    int8_t *lmap = (int8_t *)(wbase + tab_b);
-    int16_t *cslot = (int16_t *)(wbase + tab_b + map_b);
-    double *cache = (double *)(wbase + tab_b + map_b + cs_b);
+    unsigned char *wbase = row_smem + (size_t)wi * (bits_b + pre_b + l2s_b + map_b + cs_b + (size_t)C * 72);
+    uint32_t *ubits = (uint32_t *)wbase;
+    uint16_t *upre = (uint16_t *)(wbase + bits_b);
+    int16_t *l2s = (int16_t *)(wbase + bits_b + pre_b);
+    int8_t *lmap = (int8_t *)(wbase + bits_b + pre_b + l2s_b);
+    int16_t *cslot = (int16_t *)(wbase + bits_b + pre_b + l2s_b + map_b);
+    double *cache = (double *)(wbase + bits_b + pre_b + l2s_b + map_b + cs_b);
+    // local index of the column at run position bi, or -1 if the row has no
+    // such upper column
+    auto local_of = [&](int bi, int total) -> int {
+        if (bi < 0 || bi >= total) return -1;
+        const uint32_t wv = ubits[bi >> 5], m = 1u << (bi & 31);
+        return (wv & m) ? (int)upre[bi >> 5] + __popc(wv & (m - 1u)) : -1;
+    };
     const unsigned lt = (1u << lane) - 1u;
     double b0 = 0.0, b1 = 0.0, b2 = 0.0;
     if (body) { b0 = body[0]; b1 = body[1]; b2 = body[2]; }
@@ -125,17 +145,48 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
         const uint32_t ci = node_cpk[I];
         const int cx = (int)(ci & 0x7FF), cy = (int)((ci >> 11) & 0x7FF), cz = (int)(ci >> 22);
         const int total = cell_runs(ig[node_inst[I]], cell_start, cx, cy, cz, lane, run_start[wi], run_pre[wi]);
-        if (total > nbits || (C > 0 && U > max_upper)) {
+        if (total > nbits || U > max_upper) {
             if (lane == 0) dev_fail(err, RPIM_E_ARG, I);
             continue;
         }
-        for (int i = lane; i < total; i += 32) tab[i] = -1;
+        const int nwr = (total + 31) >> 5;
+        for (int i = lane; i < nwr; i += 32) ubits[i] = 0u;
         if (C > 0)
             for (int i = lane; i < U; i += 32) lmap[i] = -2;
         __syncwarp();
+        bool bad = false;
         for (int s = lane; s < U; s += 32) {
             const int bi = run_bit(node_cpk, node_rank, ucols[s], cx, cy, cz, run_start[wi], run_pre[wi]);
-            if (bi >= 0 && bi < total) tab[bi] = (int16_t)s;
+            if (bi >= 0 && bi < total) atomicOr(&ubits[bi >> 5], 1u << (bi & 31));
+            else bad = true;
+        }
+        // (a column outside the runs cannot come from the pattern build; the
+        // row is skipped, so that every local index below has a slot)
+        if (__any_sync(0xffffffffu, bad)) {
+            if (lane == 0) dev_fail(err, RPIM_E_ARG, I);
+            continue;
+        }
+        __syncwarp();
+        {   // prefix popcounts: lane l takes words [l per, (l + 1) per)
+            const int per = (nwr + 31) >> 5, w0 = min(nwr, lane * per), w1 = min(nwr, w0 + per);
+            int cnt = 0;
+            for (int i = w0; i < w1; i++) cnt += __popc(ubits[i]);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            int run = incl - cnt;
+            for (int i = w0; i < w1; i++) {
+                upre[i] = (uint16_t)run;
+                run += __popc(ubits[i]);
+            }
+        }
+        __syncwarp();
+        for (int s = lane; s < U; s += 32) {
+            const int li = local_of(run_bit(node_cpk, node_rank, ucols[s], cx, cy, cz, run_start[wi], run_pre[wi]), total);
+            if (li >= 0) l2s[li] = (int16_t)s;
         }
         __syncwarp();
         // uniform Poisson ratio over the row's points?
@@ -149,12 +200,12 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
         // sum whether it lives in the cache or in K)
         auto flush = [&]() {
             for (int li = lane; li < nloc; li += 32) {
-                const int s = cslot[li];
+                const int lx = cslot[li];
                 const double *c = cache + 9 * li;
-                double *o = Ku + 9 * s;
+                double *o = Ku + 9 * (int)l2s[lx];
 #pragma unroll
                 for (int i = 0; i < 9; i++) o[i] = c[i];
-                lmap[s] = -1;
+                lmap[lx] = -1;
             }
             nloc = 0;
             __syncwarp();
@@ -182,16 +233,14 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
             }
             const int cnt = (int)min((int64_t)32, t1 - tb);
             // chunks of 32 support entries of the batch's points, walked in
-            // order; the slot and gradient of the next chunk are loaded
-            // while the current one is accumulated (the lookup chain
-            // sidx -> cell data -> slot table is the kernel's latency)
+            // order; the block (local index) and gradient of the next chunk
+            // are loaded while the current one is accumulated
             auto fetch = [&](int64_t qb_, int64_t qend_, int &slot_, double &d0_, double &d1_, double &d2_) {
                 const int64_t q = qb_ + lane;
                 slot_ = -1;
                 d0_ = d1_ = d2_ = 0.0;
                 if (q < qend_) {
-                    const int bi = run_bit_cell(ecell[q], cx, cy, cz, run_start[wi], run_pre[wi]);
-                    slot_ = bi >= 0 && bi < total ? tab[bi] : -1;
+                    slot_ = local_of(run_bit_cell(ecell[q], cx, cy, cz, run_start[wi], run_pre[wi]), total);
                     if (slot_ < 0) dev_fail(err, RPIM_E_ARG, I);
                     const double2 qa = *(const double2 *)(phi + 4 * q);
                     const double2 qb2 = *(const double2 *)(phi + 4 * q + 2);
@@ -263,7 +312,7 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                             for (int i = 0; i < 9; i++) o[i] = 0.0;
                             if (li < 0) lmap[slot] = -1;   // stays in K from now on
                         } else {
-                            const double *src = (li >= 0 && !fresh) ? cache + 9 * li : Ku + 9 * slot;
+                            const double *src = (li >= 0 && !fresh) ? cache + 9 * li : Ku + 9 * (int)l2s[slot];
 #pragma unroll
                             for (int i = 0; i < 9; i++) o[i] = src[i];
                         }
@@ -283,7 +332,7 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                             o[7] = fma(M1, d2, fma(A2, d1, o[7]));
                             o[8] = fma(M2, d2, fma(A2, d2, o[8] + md));
                         }
-                        double *dst = li >= 0 ? cache + 9 * li : Ku + 9 * slot;
+                        double *dst = li >= 0 ? cache + 9 * li : Ku + 9 * (int)l2s[slot];
 #pragma unroll
                         for (int i = 0; i < 9; i++) dst[i] = o[i];
                     }
@@ -301,12 +350,13 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
         flush();
         // finish the upper blocks
         const double kappa = 2.0 * nu0 / (1.0 - 2.0 * nu0);
-        for (int s = lane; s < U; s += 32) {
+        for (int lx = lane; lx < U; lx += 32) {
+            const int s = l2s[lx];
             double *o = Ku + 9 * s;
             double k[9];
             // (every upper block of the pattern is updated by some point of
             // the row; a block that was not would be zero)
-            const bool touched = C == 0 || lmap[s] != -2;
+            const bool touched = C == 0 || lmap[lx] != -2;
 #pragma unroll
             for (int i = 0; i < 9; i++) k[i] = touched ? o[i] : 0.0;
             if (uni) {
@@ -518,23 +568,24 @@ static rpim_status assemble_issue(rpim_pattern *p, const double *E, const double
 {
     launch("lame", lame_kernel, grid_size(p->sm_count, 4, p->n_points, 256), 256, 0, s, p->n_points, E, nu, p->wj, p->lamw, p->err);
     RPIM_CHECK(shape_functions_all(p, p->phi, s));
-    // per warp: the slot table (int16 per bitmap position), the block cache's
-    // map (int8 per upper block of the row) and the cache of C blocks; C is
-    // the largest of 64, 32, 0 that keeps two blocks of 8 warps per SM (with
-    // one block per SM the cache measured slower than none: 388 against
-    // 318 ms on 32 batched blocks with supports up to 180 nodes)
+    // per warp: the row's column bitmap over the cell-run positions with its
+    // word prefix counts, the local index -> slot table and, with a cache of
+    // C blocks, its maps (int8 per upper block of the row, so C <= 127); C is
+    // the largest multiple of 16 up to 112 that keeps two blocks of 8 warps
+    // per SM
     const int nbits = 32 * p->bit_words;
     const int max_row = std::max(1, p->max_row);
-    // per-warp bytes with a cache of c blocks (the map is needed only with a cache)
+    auto a16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     auto per_warp = [&](int c) {
-        return (((size_t)nbits * 2 + 15) & ~(size_t)15) + (c > 0 ? (((size_t)max_row + 15) & ~(size_t)15) : 0) +
-               (((size_t)c * 2 + 15) & ~(size_t)15) + (size_t)c * 72;
+        return a16((size_t)nbits / 8) + a16((size_t)nbits / 16) + a16((size_t)max_row * 2) +
+               (c > 0 ? a16((size_t)max_row) : 0) + a16((size_t)c * 2) + (size_t)c * 72;
     };
-    int C = 64;
-    while (C > 0 && 8 * per_warp(C) > 108 * 1024) C -= 32;
-    const int max_upper = C > 0 ? max_row : 0;
+    int C = 112;
+    while (C > 0 && 8 * per_warp(C) > 108 * 1024) C -= 16;
+    const int max_upper = max_row;
     const size_t smem = 8 * per_warp(C);
-    if (nbits > 32767 || smem > 216 * 1024) return fail(RPIM_E_SUPPORT, "row slot table too large (too many nodes per cell)");
+    if (max_row > 32767 || smem > 216 * 1024)
+        return fail(RPIM_E_SUPPORT, "row tables too large for shared memory (too many nodes per cell)");
     RPIM_CUDA(cudaFuncSetAttribute(row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     launch("row", row_kernel, grid_size(p->sm_count, 8, p->n_nodes * 32, 256), 256, smem, s, p->n_nodes, p->toff,
            p->tent, p->entry_pt, p->soff, (const uint2 *)p->ecell, p->phi, p->lamw, p->wj, nu, body, p->rowptr, p->cols, p->diag,
