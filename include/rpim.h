@@ -318,8 +318,9 @@ rpim_status rpim_pattern_copy_row_order(const rpim_pattern *pattern, int32_t *or
 
 /* Sets the launch shape for buckets whose largest support is max_support
  * (as rpim_autotune_shape would). Errors: RPIM_E_ARG when the shape is not
- * admissible (1-16 warps per point, 1-15 points per block, at most 1024
- * threads, the points' shared memory within 216 KB). */
+ * admissible (1-16 warps per point, 1-15 points per block, at most 768
+ * threads, 512 with the refined solver, the points' shared memory within
+ * 216 KB). */
 rpim_status rpim_autotune_set(int32_t max_support, int32_t warps_per_point, int32_t points_per_block);
 
 /* Forgets every tuned launch shape and the tuned bucket bounds (back to the

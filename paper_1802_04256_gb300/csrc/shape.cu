@@ -339,10 +339,12 @@ struct Group {
 // columns per elimination step
 constexpr int kElimCols = 2;
 
-// threads per block of the shape kernels: the FP64 solver runs up to 1024
-// (64 registers a thread); the float-float solver, whose long dependent
-// FP32 chains need registers for overlap, up to 512 (128 registers)
-constexpr int kShapeMaxThreads[2] = {1024, 512};
+// threads per block of the shape kernels: the FP64 solver runs up to 768
+// (80 registers a thread: at 1024 threads and 64 registers it spilled inside
+// the elimination, 1.3% slower on the layered slope, where the tuned shapes
+// use at most 768 threads anyway); the float-float solver, whose long
+// dependent FP32 chains need registers for overlap, up to 512 (128 registers)
+constexpr int kShapeMaxThreads[2] = {768, 512};
 
 // Arithmetic of the elimination: FP64, or float-float pairs.
 struct F64Ops {

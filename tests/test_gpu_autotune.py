@@ -68,7 +68,7 @@ def test_autotuner_picks_admissible_shapes_and_keeps_K(batch):
     print("tuned (largest support, warps per point, points per block):", table)
     assert len(table) >= 2
     for nc, G, ppb in table:
-        assert 1 <= G <= 16 and 1 <= ppb <= 15 and G * ppb * 32 <= 1024
+        assert 1 <= G <= 16 and 1 <= ppb <= 15 and G * ppb * 32 <= 768
     K, f = pat.assemble(E, nu)
     assert torch.equal(K, K0)
     assert torch.equal(f, f0)
@@ -78,6 +78,8 @@ def test_autotuner_picks_admissible_shapes_and_keeps_K(batch):
 def test_inadmissible_shape_rejected():
     with pytest.raises(R.RpimError):
         R.rpim_autotune_set(200, 4, 15)   # 1920 threads
+    with pytest.raises(R.RpimError):
+        R.rpim_autotune_set(60, 16, 2)    # 1024 threads: above the FP64 solver's 768
     with pytest.raises(R.RpimError):
         R.rpim_autotune_set(100, 17, 1)   # more warps than the argmax buffers hold
     with pytest.raises(R.RpimError):
