@@ -49,10 +49,11 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t 
 // point order). The running sums live in K (L2-resident read-modify-write)
 // or, while a run of consecutive points keeps touching them, in a per-warp
 // shared-memory cache of C blocks: a block enters the cache with its running
-// sum from K and is written back when the cache fills or the row ends.
-// Moving a sum between K and the cache is exact, so every block is the same
-// fused multiply-add sequence as without the cache (bitwise), with fewer
-// L2 round trips between consecutive points. The warps of a
+// sum from K (from zero at its first update in the row) and is written back
+// when the cache fills or the row ends. Moving a sum between K and the cache
+// is exact, so every block is the same fused multiply-add sequence as without
+// the cache (bitwise), with fewer L2 round trips between consecutive points.
+// The warps of a
 // wave keep their rows' upper blocks (about 19 KB a row on the cantilever)
 // in L2, so the number of resident warps is a trade: 16 per SM (2 blocks,
 // 100 registers) measured 27 ms on the cantilever; 8 (shared-memory
