@@ -232,15 +232,39 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                 pw = pa.x * wj[g];
                 if (body) fw += pw;
             }
-            const int cnt = (int)min((int64_t)32, t1 - tb);
-            // chunks of 32 support entries of the batch's points, walked in
-            // order; the block (local index) and gradient of the next chunk
-            // are loaded while the current one is accumulated
-            auto fetch = [&](int64_t qb_, int64_t qend_, int &slot_, double &d0_, double &d1_, double &d2_) {
-                const int64_t q = qb_ + lane;
+            // The (point, entry) pairs of the batch's points are walked flat
+            // in chunks of 32 lanes: a chunk may hold the end of one point's
+            // entries and the start of the next point's, so that the lanes
+            // stay busy where the supports' upper parts are short. Within a
+            // chunk a block can appear twice only for two different points;
+            // such a chunk is accumulated in rounds, one point at a time in
+            // ascending order, so every block keeps its ascending-point
+            // sequence of multiply-adds (bitwise the same K). The block
+            // (local index) and gradient of the next chunk are loaded while
+            // the current one is accumulated.
+            int len = 0;
+            if (tb + lane < t1) len = (int)(pend - pe);
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int excl = incl - len;   // lanes past the batch hold the total
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            auto fetch = [&](int f0_, int &kl_, int &slot_, double &d0_, double &d1_, double &d2_) {
+                const int f = f0_ + lane;
+                int kk = 0;   // last point of the batch whose entries start at or before f
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int ex = __shfl_sync(0xffffffffu, excl, kk + step);
+                    if (ex <= f) kk += step;
+                }
+                kl_ = kk;
+                const int64_t q = __shfl_sync(0xffffffffu, pe, kk) + (f - __shfl_sync(0xffffffffu, excl, kk));
                 slot_ = -1;
                 d0_ = d1_ = d2_ = 0.0;
-                if (q < qend_) {
+                if (f < tot) {
                     slot_ = local_of(run_bit_cell(ecell[q], cx, cy, cz, run_start[wi], run_pre[wi]), total);
                     if (slot_ < 0) dev_fail(err, RPIM_E_ARG, I);
                     const double2 qa = *(const double2 *)(phi + 4 * q);
@@ -250,98 +274,101 @@ __global__ void __launch_bounds__(256, 2) row_kernel(int64_t n_nodes, const int6
                     d2_ = qb2.y;
                 }
             };
-            int k = 0;
-            int64_t qb = __shfl_sync(0xffffffffu, pe, 0), qend = __shfl_sync(0xffffffffu, pend, 0);
-            int slot;
+            int kl, slot;
             double d0, d1, d2;
-            fetch(qb, qend, slot, d0, d1, d2);
-            while (k < cnt) {
-                // the next chunk: the rest of point k's support, or point k + 1
-                int nk = k;
-                int64_t nqb = qb + 32, nqend = qend;
-                if (nqb >= qend) {
-                    nk = k + 1;
-                    nqb = __shfl_sync(0xffffffffu, pe, nk & 31);
-                    nqend = __shfl_sync(0xffffffffu, pend, nk & 31);
-                }
-                int nslot = -1;
+            fetch(0, kl, slot, d0, d1, d2);
+            for (int f0 = 0; f0 < tot; f0 += 32) {
+                int nkl = 0, nslot = -1;
                 double n0 = 0.0, n1 = 0.0, n2 = 0.0;
-                if (nk < cnt) fetch(nqb, nqend, nslot, n0, n1, n2);
-                const double M0 = __shfl_sync(0xffffffffu, pM0, k), M1 = __shfl_sync(0xffffffffu, pM1, k),
-                             M2 = __shfl_sync(0xffffffffu, pM2, k);
+                if (f0 + 32 < tot) fetch(f0 + 32, nkl, nslot, n0, n1, n2);
+                const double M0 = __shfl_sync(0xffffffffu, pM0, kl), M1 = __shfl_sync(0xffffffffu, pM1, kl),
+                             M2 = __shfl_sync(0xffffffffu, pM2, kl);
                 double A0 = 0.0, A1 = 0.0, A2 = 0.0;
                 if (!uni) {
-                    A0 = __shfl_sync(0xffffffffu, pA0, k);
-                    A1 = __shfl_sync(0xffffffffu, pA1, k);
-                    A2 = __shfl_sync(0xffffffffu, pA2, k);
+                    A0 = __shfl_sync(0xffffffffu, pA0, kl);
+                    A1 = __shfl_sync(0xffffffffu, pA1, kl);
+                    A2 = __shfl_sync(0xffffffffu, pA2, kl);
                 }
-                {
-                    // the block's place: in the cache (li >= 0), or to be
-                    // brought in; blocks stay in K when the cache is full.
-                    // The map holds the cache index, -1 for a block whose
-                    // running sum is in K, -2 for a block not yet updated in
-                    // this row (its running sum is zero: no load)
-                    int li = -1, lv = -1;
-                    bool fresh = false;
-                    if (C > 0) {   // (C is uniform: without a cache every block stays in K)
-                        lv = slot >= 0 ? (int)lmap[slot] : -1;
-                        unsigned need = __ballot_sync(0xffffffffu, slot >= 0 && lv < 0);
-                        if (need && nloc + __popc(need) > C) {
-                            flush();
+                // accumulates the lane's entry into its block (slot < 0: none)
+                auto accumulate = [&](const int slot) {
+                    {
+                        // the block's place: in the cache (li >= 0), or to be
+                        // brought in; blocks stay in K when the cache is full.
+                        // The map holds the cache index, -1 for a block whose
+                        // running sum is in K, -2 for a block not yet updated in
+                        // this row (its running sum is zero: no load)
+                        int li = -1, lv = -1;
+                        bool fresh = false;
+                        if (C > 0) {   // (C is uniform: without a cache every block stays in K)
                             lv = slot >= 0 ? (int)lmap[slot] : -1;
-                            need = __ballot_sync(0xffffffffu, slot >= 0 && lv < 0);
-                        }
-                        li = lv >= 0 ? lv : -1;
-                        if (slot >= 0 && lv < 0) {
-                            const int n = nloc + __popc(need & lt);
-                            if (n < C) {
-                                li = n;
-                                lmap[slot] = (int8_t)n;
-                                cslot[n] = (int16_t)slot;
-                                fresh = true;
+                            unsigned need = __ballot_sync(0xffffffffu, slot >= 0 && lv < 0);
+                            if (need && nloc + __popc(need) > C) {
+                                flush();
+                                lv = slot >= 0 ? (int)lmap[slot] : -1;
+                                need = __ballot_sync(0xffffffffu, slot >= 0 && lv < 0);
                             }
+                            li = lv >= 0 ? lv : -1;
+                            if (slot >= 0 && lv < 0) {
+                                const int n = nloc + __popc(need & lt);
+                                if (n < C) {
+                                    li = n;
+                                    lmap[slot] = (int8_t)n;
+                                    cslot[n] = (int16_t)slot;
+                                    fresh = true;
+                                }
+                            }
+                            nloc = min(C, nloc + __popc(need));
                         }
-                        nloc = min(C, nloc + __popc(need));
+                        if (slot >= 0) {
+                            // running sum of the block: zero at its first update,
+                            // from K when it enters the cache or stays out of it,
+                            // else from the cache
+                            double o[9];
+                            if (lv == -2) {
+#pragma unroll
+                                for (int i = 0; i < 9; i++) o[i] = 0.0;
+                                if (li < 0) lmap[slot] = -1;   // stays in K from now on
+                            } else {
+                                const double *src = (li >= 0 && !fresh) ? cache + 9 * li : Ku + 9 * (int)l2s[slot];
+#pragma unroll
+                                for (int i = 0; i < 9; i++) o[i] = src[i];
+                            }
+                            if (uni) {
+                                o[0] = fma(M0, d0, o[0]); o[1] = fma(M0, d1, o[1]); o[2] = fma(M0, d2, o[2]);
+                                o[3] = fma(M1, d0, o[3]); o[4] = fma(M1, d1, o[4]); o[5] = fma(M1, d2, o[5]);
+                                o[6] = fma(M2, d0, o[6]); o[7] = fma(M2, d1, o[7]); o[8] = fma(M2, d2, o[8]);
+                            } else {
+                                const double md = fma(M2, d2, fma(M1, d1, M0 * d0));
+                                o[0] = fma(M0, d0, fma(A0, d0, o[0] + md));
+                                o[1] = fma(M1, d0, fma(A0, d1, o[1]));
+                                o[2] = fma(M2, d0, fma(A0, d2, o[2]));
+                                o[3] = fma(M0, d1, fma(A1, d0, o[3]));
+                                o[4] = fma(M1, d1, fma(A1, d1, o[4] + md));
+                                o[5] = fma(M2, d1, fma(A1, d2, o[5]));
+                                o[6] = fma(M0, d2, fma(A2, d0, o[6]));
+                                o[7] = fma(M1, d2, fma(A2, d1, o[7]));
+                                o[8] = fma(M2, d2, fma(A2, d2, o[8] + md));
+                            }
+                            double *dst = li >= 0 ? cache + 9 * li : Ku + 9 * (int)l2s[slot];
+#pragma unroll
+                            for (int i = 0; i < 9; i++) dst[i] = o[i];
+                        }
+                        __syncwarp();   // cache map and entries visible to the next round's lanes
                     }
-                    if (slot >= 0) {
-                        // running sum of the block: zero at its first update,
-                        // from K when it enters the cache or stays out of it,
-                        // else from the cache
-                        double o[9];
-                        if (lv == -2) {
-#pragma unroll
-                            for (int i = 0; i < 9; i++) o[i] = 0.0;
-                            if (li < 0) lmap[slot] = -1;   // stays in K from now on
-                        } else {
-                            const double *src = (li >= 0 && !fresh) ? cache + 9 * li : Ku + 9 * (int)l2s[slot];
-#pragma unroll
-                            for (int i = 0; i < 9; i++) o[i] = src[i];
-                        }
-                        if (uni) {
-                            o[0] = fma(M0, d0, o[0]); o[1] = fma(M0, d1, o[1]); o[2] = fma(M0, d2, o[2]);
-                            o[3] = fma(M1, d0, o[3]); o[4] = fma(M1, d1, o[4]); o[5] = fma(M1, d2, o[5]);
-                            o[6] = fma(M2, d0, o[6]); o[7] = fma(M2, d1, o[7]); o[8] = fma(M2, d2, o[8]);
-                        } else {
-                            const double md = fma(M2, d2, fma(M1, d1, M0 * d0));
-                            o[0] = fma(M0, d0, fma(A0, d0, o[0] + md));
-                            o[1] = fma(M1, d0, fma(A0, d1, o[1]));
-                            o[2] = fma(M2, d0, fma(A0, d2, o[2]));
-                            o[3] = fma(M0, d1, fma(A1, d0, o[3]));
-                            o[4] = fma(M1, d1, fma(A1, d1, o[4] + md));
-                            o[5] = fma(M2, d1, fma(A1, d2, o[5]));
-                            o[6] = fma(M0, d2, fma(A2, d0, o[6]));
-                            o[7] = fma(M1, d2, fma(A2, d1, o[7]));
-                            o[8] = fma(M2, d2, fma(A2, d2, o[8] + md));
-                        }
-                        double *dst = li >= 0 ? cache + 9 * li : Ku + 9 * (int)l2s[slot];
-#pragma unroll
-                        for (int i = 0; i < 9; i++) dst[i] = o[i];
-                    }
-                    __syncwarp();   // cache map and entries visible to the next round's lanes
+                };
+                const int kfirst = __shfl_sync(0xffffffffu, kl, 0);
+                const int klast = __shfl_sync(0xffffffffu, kl, min(31, tot - 1 - f0));
+                bool twice = false;
+                if (kfirst != klast) {
+                    const unsigned peers = __match_any_sync(0xffffffffu, slot >= 0 ? slot : -2 - lane);
+                    twice = __any_sync(0xffffffffu, __popc(peers) > 1);
                 }
-                k = nk;
-                qb = nqb;
-                qend = nqend;
+                if (!twice) {
+                    accumulate(slot);
+                } else {
+                    for (int kk = kfirst; kk <= klast; kk++) accumulate(kl == kk ? slot : -1);
+                }
+                kl = nkl;
                 slot = nslot;
                 d0 = n0;
                 d1 = n1;
