@@ -35,6 +35,8 @@ MUTANTS = {
     "traction_tangent_axes_swapped": ("const double U = x[ua], V = x[va];", "const double U = x[va], V = x[ua];"),
     "traction_gauss_point_off": ("x[va] = mv + hv * ((pt & 2) ? GAUSS2 : -GAUSS2);",
                                  "x[va] = mv + hv * ((pt & 2) ? 0.5 : -0.5);"),
+    "traction_v_offset_with_u_half_width": ("x[va] = mv + hv * ((pt & 2) ? GAUSS2 : -GAUSS2);",
+                                            "x[va] = mv + hu * ((pt & 2) ? GAUSS2 : -GAUSS2);"),
     "block_precond_diagonal_only": ("for (int b = 0; b < 3; b++) s += dinv[9 * I + 3 * a + b] * r[3 * I + b];",
                                     "for (int b = 0; b < 3; b++) s += dinv[9 * I + 4 * a] * r[3 * I + a];"),
     "block_inverse_wrong_row_op": ("for (int j = 0; j < 6; j++) m[i][j] -= l * m[k][j];",
@@ -79,6 +81,7 @@ def _pins(kind, cube):
     yield "stress", lambda: pins.test_stress_of_linear_fields_is_hookes_law(cube, kind)
     yield "traction", lambda: pins.test_traction_resultant_and_moment_are_the_exact_integrals(cube, kind)
     yield "block_pcg", lambda: pins.test_block_jacobi_pcg_is_exact_on_a_block_diagonal_matrix(cube, kind)
+    yield "symmetry", lambda: pins.check_cube_symmetries(kind)
 
 
 def _quad(kind, cube):
