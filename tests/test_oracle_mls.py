@@ -12,7 +12,8 @@ Against facts fixed by the mathematics, not by the oracle itself:
 * an extended-precision rerun (the 4x4 moment matrix is well conditioned in
   local coordinates, so FP64 agrees to ~1e-13);
 * K from MLS shape functions: symmetry, rigid-body modes, and the energy of
-  linear fields (the patch test in energy form);
+  linear fields (the patch test in energy form); stresses of linear fields
+  by Hooke's law;
 * planted mistakes in a copy of the oracle's MLS code break these pins.
 """
 import os
@@ -137,6 +138,17 @@ def check_K(p, kind):
 @pytest.mark.parametrize("kind", KINDS)
 def test_K_symmetry_rigid_modes_and_energy(cube, kind):
     check_K(cube, kind)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_stress_of_linear_fields_is_hookes_law(cube, kind):
+    """MLS with the linear basis reproduces u = A x and its gradient exactly,
+    so the stress of such a field at any point is Hooke's law of the
+    constant strain, as for RPIM: the same pin, with the stresses computed
+    from MLS shape functions."""
+    import test_oracle_pins as pins
+    with oracle.shape_kind("mls"):
+        pins.test_stress_of_linear_fields_is_hookes_law(cube, kind)
 
 
 def test_shape_kind_selection_is_scoped(cube):

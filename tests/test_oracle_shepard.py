@@ -13,6 +13,7 @@ Against facts fixed by the mathematics, not by the oracle itself:
 * derivatives against central differences;
 * an extended-precision rerun;
 * K: symmetric, rigid translations in its null space, rotations not;
+* stresses: zero for a rigid translation, not Hooke's law for a stretch;
 * planted mistakes in a copy of the oracle's Shepard code break these pins.
 """
 import os
@@ -122,6 +123,27 @@ def test_no_weight_is_singular():
     xyz = np.array([[0.0, 0.0, 0.0], [1.2, 0.0, 0.0]])
     with pytest.raises(oracle.OracleError):   # both nodes beyond the support radius 0.5
         oracle.shape_shepard(xyz, np.arange(2, dtype=np.int32), np.array([0.6, 0.0, 0.0]), 0.25, 2.0)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_stress_of_a_translation_is_zero_and_of_a_stretch_is_not_exact(cube, kind):
+    """Shepard functions sum to one, so their gradients sum to zero and a
+    rigid translation has zero strain and stress at every point (to
+    rounding); they do not reproduce linear fields, so a uniform stretch
+    does not give Hooke's law of its strain (what sets Shepard apart from
+    MLS and RPIM)."""
+    pts = cube.xyz[::7] * 0.9 + 0.05
+    E = np.full(len(pts), 1.0e4)
+    nu = np.full(len(pts), 0.3)
+    lam = E[0] * nu[0] / ((1 + nu[0]) * (1 - 2 * nu[0]))
+    with oracle.shape_kind("shepard"):
+        t = np.tile([0.3, -0.2, 0.5], cube.n_nodes)
+        sig = oracle.stress(cube.xyz, t, pts, E, nu, cube.alpha_s, cube.alpha_c, cube.q, cube.h, kind)
+        assert np.abs(sig).max() < 1e-12 * lam   # measured 2e-15 (f64), 1e-18 (ld)
+        u = (cube.xyz * [1.0e-3, 0.0, 0.0]).ravel()
+        sig = oracle.stress(cube.xyz, u, pts, E, nu, cube.alpha_s, cube.alpha_c, cube.q, cube.h, kind)
+    want_xx = (lam + E[0] / (1 + nu[0])) * 1.0e-3
+    assert np.abs(sig[:, 0] - want_xx).max() > 1e-3 * want_xx   # measured 44%
 
 
 @pytest.mark.parametrize("kind", KINDS)
